@@ -1,0 +1,229 @@
+"""FP64 CPU oracle for the FWI hot path (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+import this package.  The product path (``paper_1912_08063_gb300``) never does: it has
+no CPU fallback.  The oracle shares no code with the CUDA library; the two meet only at
+the seeded synthetic inputs (``paper_1912_08063_gb300.synth``), which carry none of the
+method's arithmetic.
+
+The arithmetic lives in ``fwi_oracle.c`` (plain C loops in double precision).  This
+module compiles it on first use with gcc and wraps it with ctypes; the wrappers only
+convert arrays.  See the C file's header for the equations each function follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fwi_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (gcc -O2 -fopenmp, no fast-math)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-fno-fast-math", "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            d = ctypes.c_double
+            i = ctypes.c_int
+            lib.oracle_fd_coeffs.argtypes = [i, P]
+            lib.oracle_fd_coeffs.restype = i
+            lib.oracle_cfl_number.argtypes = [i, i, P, d, d]
+            lib.oracle_cfl_number.restype = d
+            lib.oracle_laplacian.argtypes = [i, i64p, P, i, P, P]
+            lib.oracle_laplacian.restype = i
+            common = [i, i64p, P, P, d, i, i, i, d, d]
+            lib.oracle_forward.argtypes = common + [i, P, P, i, P, P, P]
+            lib.oracle_forward.restype = i
+            lib.oracle_misfit.argtypes = [P, P, ctypes.c_int64]
+            lib.oracle_misfit.restype = d
+            lib.oracle_gradient.argtypes = common + [i, P, P, i, P, P, P, P, P, P, i]
+            lib.oracle_gradient.restype = i
+            lib.oracle_source_adjoint.argtypes = common + [i, P, i, P, P, P]
+            lib.oracle_source_adjoint.restype = i
+            lib.oracle_model_fields.argtypes = [i, i64p, P, P, d, i, i, d, d, i64p, P, P, P]
+            lib.oracle_model_fields.restype = i
+            _lib = lib
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _shape3(ndim, shape):
+    shape = tuple(int(s) for s in shape)
+    if ndim == 2:
+        if len(shape) == 2:
+            shape = (shape[0], 1, shape[1])
+    if len(shape) != 3:
+        raise ValueError("shape must be (nz, nx) in 2-D or (nz, ny, nx) in 3-D")
+    return (ctypes.c_int64 * 3)(*shape), shape
+
+
+def _h3(ndim, h):
+    h = [float(x) for x in np.atleast_1d(h)]
+    if len(h) == 1:
+        h = h * 3
+    if ndim == 2 and len(h) == 2:
+        h = [h[0], 1.0, h[1]]
+    return _f64(h)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def order_to_radius(order: int) -> int:
+    """Stencil order 2M -> radius M (8th order: 4, 16th order: 8)."""
+    if order % 2 or not 2 <= order <= 16:
+        raise ValueError("order must be even, 2..16")
+    return order // 2
+
+
+def fd_coeffs(M: int) -> np.ndarray:
+    c = np.zeros(M + 1)
+    _check(_load().oracle_fd_coeffs(M, _ptr(c)), "fd_coeffs")
+    return c
+
+
+def cfl_number(ndim, M, h, vmax, dt) -> float:
+    return _load().oracle_cfl_number(ndim, M, _ptr(_h3(ndim, h)), float(vmax), float(dt))
+
+
+def laplacian(u, h, M):
+    """L u on a grid with zero outside (2-D arrays are (nz, nx), 3-D (nz, ny, nx))."""
+    u = _f64(u)
+    ndim = u.ndim
+    shp, _ = _shape3(ndim, u.shape)
+    out = np.empty_like(u)
+    _check(_load().oracle_laplacian(ndim, shp, _ptr(_h3(ndim, h)), M, _ptr(u), _ptr(out)),
+           "laplacian")
+    return out
+
+
+class Problem:
+    """Arguments shared by every oracle call (physical grid, numerics, acquisition)."""
+
+    def __init__(self, v, h, dt, nt, order=8, nb=20, r0=1e-3, vref=0.0,
+                 src=None, rec=None, wavelet=None):
+        self.v = _f64(v)
+        self.ndim = self.v.ndim
+        self.shape_c, self.shape = _shape3(self.ndim, self.v.shape)
+        self.h = _h3(self.ndim, h)
+        self.dt = float(dt)
+        self.nt = int(nt)
+        self.M = order_to_radius(order)
+        self.nb = int(nb)
+        self.r0 = float(r0)
+        self.vref = float(vref)
+        self.src = _i32(src).reshape(-1, 3)
+        self.nshots = self.src.shape[0]
+        rec = _i32(rec)
+        if rec.ndim == 2:
+            rec = np.broadcast_to(rec, (self.nshots,) + rec.shape)
+        self.rec = _i32(rec).reshape(self.nshots, -1, 3)
+        self.nrec = self.rec.shape[1]
+        w = _f64(wavelet)
+        if w.ndim == 1:
+            w = np.broadcast_to(w, (self.nshots, w.shape[0]))
+        self.wavelet = _f64(w).reshape(self.nshots, self.nt)
+
+    def _common(self, v=None):
+        v = self.v if v is None else _f64(v)
+        return [self.ndim, self.shape_c, _ptr(self.h), _ptr(v), self.dt, self.nt, self.M,
+                self.nb, self.r0, self.vref]
+
+    def computed_shape(self):
+        nb = self.nb
+        nz, ny, nx = self.shape
+        if self.ndim == 2:
+            return (nz + 2 * nb, nx + 2 * nb)
+        return (nz + 2 * nb, ny + 2 * nb, nx + 2 * nb)
+
+    def forward(self, v=None, wavelet=None, final=False):
+        """Traces [nshots][nt][nrec]; with final=True also (u^nt, u^{nt-1}) per shot."""
+        w = self.wavelet if wavelet is None else _f64(wavelet).reshape(self.nshots, self.nt)
+        tr = np.zeros((self.nshots, self.nt, self.nrec))
+        cs = self.computed_shape()
+        fin = np.zeros((self.nshots, 2) + cs) if final else None
+        rc = _load().oracle_forward(*self._common(v), self.nshots, _ptr(self.src), _ptr(w),
+                                    self.nrec, _ptr(self.rec), _ptr(tr), _ptr(fin))
+        _check(rc, "forward")
+        return (tr, fin) if final else tr
+
+    def gradient(self, dobs=None, v=None, adjsrc=None, seg=None, want_gW=False):
+        """(misfit, d misfit / d v on the physical grid[, d misfit / d W computed grid])."""
+        seg = seg or max(1, int(round(np.sqrt(self.nt))))
+        grad = np.zeros(self.shape if self.ndim == 3 else (self.shape[0], self.shape[2]))
+        gW = np.zeros(self.computed_shape()) if want_gW else None
+        phi = ctypes.c_double(0.0)
+        dobs_a = None if dobs is None else _f64(dobs)
+        adj_a = None if adjsrc is None else _f64(adjsrc)
+        if dobs_a is None and adj_a is None:
+            raise ValueError("need dobs or adjsrc")
+        rc = _load().oracle_gradient(*self._common(v), self.nshots, _ptr(self.src),
+                                     _ptr(self.wavelet), self.nrec, _ptr(self.rec),
+                                     _ptr(dobs_a), _ptr(adj_a), ctypes.byref(phi),
+                                     _ptr(grad), _ptr(gW), int(seg))
+        _check(rc, "gradient")
+        if want_gW:
+            return phi.value, grad, gW
+        return phi.value, grad
+
+    def source_adjoint(self, y):
+        y = _f64(y).reshape(self.nshots, self.nt, self.nrec)
+        x = np.zeros((self.nshots, self.nt))
+        rc = _load().oracle_source_adjoint(*self._common(), self.nshots, _ptr(self.src),
+                                           self.nrec, _ptr(self.rec), _ptr(y), _ptr(x))
+        _check(rc, "source_adjoint")
+        return x
+
+    def fields(self):
+        """(W, a+, a-) on the computed grid."""
+        cs = self.computed_shape()
+        W, ap, am = np.zeros(cs), np.zeros(cs), np.zeros(cs)
+        nc = (ctypes.c_int64 * 3)()
+        rc = _load().oracle_model_fields(self.ndim, self.shape_c, _ptr(self.h), _ptr(self.v),
+                                         self.dt, self.M, self.nb, self.r0, self.vref, nc,
+                                         _ptr(W), _ptr(ap), _ptr(am))
+        _check(rc, "model_fields")
+        return W, ap, am
+
+
+def misfit(dmod, dobs) -> float:
+    a, b = _f64(dmod), _f64(dobs)
+    return _load().oracle_misfit(_ptr(a), _ptr(b), a.size)

@@ -1,0 +1,519 @@
+/*
+ * FP64 CPU oracle for acoustic full-waveform inversion: forward modelling, exact
+ * discrete adjoint and the zero-lag imaging condition (velocity gradient).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or calls this
+ * file; only the tests, the package's smoke check and the CPU baseline of the bench
+ * do.  It shares no code, header, table or helper with the CUDA library: the
+ * finite-difference coefficients, the sponge profile, the CFL number and every
+ * update below are derived here again from their definitions.
+ *
+ * Every function is a plain loop over the grid in double precision, in the order the
+ * method states it, with no blocking, fusion or reordering beyond that.  OpenMP only
+ * splits the outermost grid loop.
+ *
+ * Sources of each definition ("HRI" = Huot et al., High-resolution imaging on TPUs):
+ *   - misfit  phi = || d_mod - d_obs ||_2^2                      HRI Sec. 3, Eq. 1
+ *   - wave equation  P_tt = v^2 lap(P) + s                       HRI Sec. 3, Eq. 2
+ *   - leapfrog update P^{n+1} = -P^{n-1} + 2P^n + v^2 dt^2 lap P^n + dt^2 s^n
+ *                                                                HRI Sec. 3, Eq. 3
+ *   - central stencils of order >= 8 (8th and 16th used)         HRI Sec. 3 (Fig. 3), Sec. 4
+ *   - the gradient of phi (named, not derived, in the paper)     HRI Sec. 1
+ * Readings where the paper is silent (all stated again where they are used):
+ *   - coefficients: Taylor (Fornberg) central second-derivative weights of radius M,
+ *     order 2M;
+ *   - absorbing boundary: a damped wave equation P_tt + eta P_t = v^2 lap P + s with a
+ *     quadratic sponge of nb cells padded outside the physical grid on every face,
+ *     centred in time, which reduces to Eq. 3 wherever eta = 0;
+ *   - outside the padded (computed) grid the field is zero (Dirichlet);
+ *   - source: dt^2 w[n] added at one node (Eq. 3's dt^2 s term), divided by the same
+ *     a+ factor as the rest of the update;
+ *   - receivers: sample n of a trace is the field after step n, u^{n+1};
+ *   - quiescent start u^{-1} = u^0 = 0;
+ *   - gradient: exact derivative of the discrete phi with respect to the physical
+ *     velocity grid, with the sponge strength held fixed; sponge cells take the
+ *     velocity of the nearest physical cell (edge replication), so their
+ *     contributions fold back onto that cell.
+ *
+ * Parity status: every function here is pinned by the CPU tests (coefficients by
+ * exact rational moment conditions, the Laplacian by its convergence order and
+ * modified-wavenumber symbol, time stepping by closed-box energy conservation and the
+ * homogeneous Green's function, the adjoint by dot-product tests and the gradient by
+ * central finite differences).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXM 8
+
+/* ------------------------------------------------------------------ coefficients */
+
+/* Central second-derivative weights of radius M (order 2M): the unique symmetric
+ * stencil that is exact for polynomials up to degree 2M+1.  Closed form
+ *   c_k = 2 (-1)^{k+1} (M!)^2 / (k^2 (M-k)! (M+k)!),  k = 1..M,
+ *   c_0 = -2 sum_k c_k.
+ * The factorials stay below 2^53 for M <= 8, so every factor is exact in double. */
+int oracle_fd_coeffs(int M, double *c)
+{
+    if (M < 1 || M > OR_MAXM) return -1;
+    double fM = 1.0;
+    for (int i = 2; i <= M; ++i) fM *= i;
+    double sum = 0.0;
+    for (int k = 1; k <= M; ++k) {
+        double fa = 1.0, fb = 1.0;
+        for (int i = 2; i <= M - k; ++i) fa *= i;
+        for (int i = 2; i <= M + k; ++i) fb *= i;
+        double sgn = (k % 2 == 1) ? 1.0 : -1.0;
+        c[k] = 2.0 * sgn * (fM / fa) * (fM / fb) / ((double)k * (double)k);
+        sum += c[k];
+    }
+    c[0] = -2.0 * sum;
+    return 0;
+}
+
+/* Stability number of the undamped leapfrog: the scheme is stable while
+ *   v_max dt sqrt(sum_axes S_M / h_a^2) / 2 < 1,
+ * where S_M = -(c_0 + 2 sum_k c_k cos(k pi)) is the largest eigenvalue magnitude of
+ * the 1-D stencil (its symbol at the Nyquist wavenumber). */
+double oracle_cfl_number(int ndim, int M, const double *h, double vmax, double dt)
+{
+    double c[OR_MAXM + 1];
+    if (oracle_fd_coeffs(M, c) != 0) return -1.0;
+    double S = -c[0];
+    for (int k = 1; k <= M; ++k) S -= 2.0 * c[k] * ((k % 2 == 0) ? 1.0 : -1.0);
+    double acc = S / (h[0] * h[0]) + S / (h[2] * h[2]);
+    if (ndim == 3) acc += S / (h[1] * h[1]);
+    return vmax * dt * sqrt(acc) / 2.0;
+}
+
+/* ------------------------------------------------------------------ grid */
+
+typedef struct {
+    int ndim, M, nb;
+    int64_t np[3];  /* physical extents (nz, ny, nx); ny = 1 in 2-D */
+    int64_t n[3];   /* computed (padded) extents */
+    int64_t ncell;
+    double h[3];
+    double dt;
+    double c[OR_MAXM + 1];
+    double *W;      /* v_c^2 dt^2 on the computed grid */
+    double *vc;     /* edge-replicated velocity */
+    double *ap, *am;/* a+ = 1 + eta dt / 2, a- = 1 - eta dt / 2 */
+} og_grid;
+
+static int64_t og_clamp(int64_t i, int64_t lo, int64_t hi)
+{
+    return i < lo ? lo : (i > hi ? hi : i);
+}
+
+/* depth of index i into the sponge of an axis of physical extent np, padded by nb */
+static double og_depth(int64_t i, int64_t np, int nb)
+{
+    if (i < nb) return (double)(nb - i);
+    if (i >= nb + np) return (double)(i - (nb + np - 1));
+    return 0.0;
+}
+
+static void og_free(og_grid *g)
+{
+    free(g->W); free(g->vc); free(g->ap); free(g->am);
+    g->W = g->vc = g->ap = g->am = NULL;
+}
+
+/* Builds the computed grid: pads v by nb cells on every face of every present axis by
+ * edge replication, W = v_c^2 dt^2, and the sponge
+ *   eta = sum_axes eta_max,a (depth_a / nb)^2,
+ *   eta_max,a = 3 vref ln(1/R0) / (2 nb h_a)
+ * (vref <= 0 means the largest velocity of the model). */
+static int og_build(og_grid *g, int ndim, const int64_t *shape, const double *h,
+                    const double *v, double dt, int M, int nb, double r0, double vref)
+{
+    memset(g, 0, sizeof(*g));
+    if (ndim != 2 && ndim != 3) return -1;
+    if (oracle_fd_coeffs(M, g->c) != 0) return -1;
+    g->ndim = ndim; g->M = M; g->nb = nb; g->dt = dt;
+    for (int a = 0; a < 3; ++a) { g->np[a] = shape[a]; g->h[a] = h[a]; }
+    if (ndim == 2) g->np[1] = 1;
+    g->n[0] = g->np[0] + 2 * nb;
+    g->n[1] = (ndim == 3) ? g->np[1] + 2 * nb : 1;
+    g->n[2] = g->np[2] + 2 * nb;
+    g->ncell = g->n[0] * g->n[1] * g->n[2];
+    g->W = malloc(sizeof(double) * g->ncell);
+    g->vc = malloc(sizeof(double) * g->ncell);
+    g->ap = malloc(sizeof(double) * g->ncell);
+    g->am = malloc(sizeof(double) * g->ncell);
+    if (!g->W || !g->vc || !g->ap || !g->am) { og_free(g); return -3; }
+
+    double vmax = 0.0;
+    int64_t nphys = g->np[0] * g->np[1] * g->np[2];
+    for (int64_t i = 0; i < nphys; ++i) if (v[i] > vmax) vmax = v[i];
+    if (vref <= 0.0) vref = vmax;
+    double emax[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < 3; ++a) {
+        if (a == 1 && ndim == 2) continue;
+        if (nb > 0) emax[a] = 3.0 * vref * log(1.0 / r0) / (2.0 * nb * h[a]);
+    }
+    int nby = (ndim == 3) ? nb : 0;
+    for (int64_t iz = 0; iz < g->n[0]; ++iz)
+        for (int64_t iy = 0; iy < g->n[1]; ++iy)
+            for (int64_t ix = 0; ix < g->n[2]; ++ix) {
+                int64_t pz = og_clamp(iz - nb, 0, g->np[0] - 1);
+                int64_t py = og_clamp(iy - nby, 0, g->np[1] - 1);
+                int64_t px = og_clamp(ix - nb, 0, g->np[2] - 1);
+                double vv = v[(pz * g->np[1] + py) * g->np[2] + px];
+                double eta = 0.0;
+                if (nb > 0) {
+                    double dz = og_depth(iz, g->np[0], nb) / nb;
+                    double dx = og_depth(ix, g->np[2], nb) / nb;
+                    eta += emax[0] * dz * dz + emax[2] * dx * dx;
+                    if (ndim == 3) {
+                        double dy = og_depth(iy, g->np[1], nb) / nb;
+                        eta += emax[1] * dy * dy;
+                    }
+                }
+                int64_t i = (iz * g->n[1] + iy) * g->n[2] + ix;
+                g->vc[i] = vv;
+                g->W[i] = vv * vv * dt * dt;
+                g->ap[i] = 1.0 + eta * dt / 2.0;
+                g->am[i] = 1.0 - eta * dt / 2.0;
+            }
+    return 0;
+}
+
+static int64_t og_index(const og_grid *g, const int32_t *p)
+{
+    int nby = (g->ndim == 3) ? g->nb : 0;
+    int64_t iz = p[0] + g->nb, iy = p[1] + nby, ix = p[2] + g->nb;
+    if (p[0] < 0 || p[0] >= g->np[0] || p[2] < 0 || p[2] >= g->np[2]) return -1;
+    if (g->ndim == 3 && (p[1] < 0 || p[1] >= g->np[1])) return -1;
+    if (g->ndim == 2 && p[1] != 0) return -1;
+    return (iz * g->n[1] + iy) * g->n[2] + ix;
+}
+
+/* ------------------------------------------------------------------ Laplacian */
+
+static double og_at(const og_grid *g, const double *u, int64_t iz, int64_t iy, int64_t ix)
+{
+    if (iz < 0 || iz >= g->n[0] || iy < 0 || iy >= g->n[1] || ix < 0 || ix >= g->n[2])
+        return 0.0;
+    return u[(iz * g->n[1] + iy) * g->n[2] + ix];
+}
+
+/* L u = sum over axes a of (1/h_a^2) sum_{k=-M..M} c_|k| u(shifted k cells along a),
+ * with u = 0 outside the computed grid (HRI Sec. 3: the Laplacian of Eq. 2-3 as a
+ * central stencil of order 2M). */
+static void og_laplacian(const og_grid *g, const double *u, double *out)
+{
+    const int M = g->M;
+    const double *c = g->c;
+    const double iz2 = 1.0 / (g->h[0] * g->h[0]);
+    const double iy2 = 1.0 / (g->h[1] * g->h[1]);
+    const double ix2 = 1.0 / (g->h[2] * g->h[2]);
+    #pragma omp parallel for schedule(static)
+    for (int64_t iz = 0; iz < g->n[0]; ++iz)
+        for (int64_t iy = 0; iy < g->n[1]; ++iy)
+            for (int64_t ix = 0; ix < g->n[2]; ++ix) {
+                double u0 = og_at(g, u, iz, iy, ix);
+                double sz = c[0] * u0, sx = c[0] * u0, sy = c[0] * u0;
+                for (int k = 1; k <= M; ++k) {
+                    sz += c[k] * (og_at(g, u, iz + k, iy, ix) + og_at(g, u, iz - k, iy, ix));
+                    sx += c[k] * (og_at(g, u, iz, iy, ix + k) + og_at(g, u, iz, iy, ix - k));
+                    if (g->ndim == 3)
+                        sy += c[k] * (og_at(g, u, iz, iy + k, ix) + og_at(g, u, iz, iy - k, ix));
+                }
+                double lap = sz * iz2 + sx * ix2;
+                if (g->ndim == 3) lap += sy * iy2;
+                out[(iz * g->n[1] + iy) * g->n[2] + ix] = lap;
+            }
+}
+
+/* The Laplacian alone, on a user grid with zero outside (no padding): for the tests of
+ * convergence order and modified wavenumber. */
+int oracle_laplacian(int ndim, const int64_t *shape, const double *h, int M,
+                     const double *u, double *out)
+{
+    og_grid g;
+    memset(&g, 0, sizeof(g));
+    if (ndim != 2 && ndim != 3) return -1;
+    if (oracle_fd_coeffs(M, g.c) != 0) return -1;
+    g.ndim = ndim; g.M = M;
+    for (int a = 0; a < 3; ++a) { g.n[a] = shape[a]; g.h[a] = h[a]; }
+    if (ndim == 2) g.n[1] = 1;
+    og_laplacian(&g, u, out);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ time stepping */
+
+/* One damped leapfrog step (Eq. 3 with the sponge reading):
+ *   a+ u^{n+1} = 2 u^n + W L u^n - a- u^{n-1} + dt^2 w[n] e_src
+ * lap is scratch of the grid's size. */
+static void og_step(const og_grid *g, const double *ucur, const double *uprev,
+                    double *unext, double *lap, int64_t src, double srcval)
+{
+    og_laplacian(g, ucur, lap);
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < g->ncell; ++i) {
+        double rhs = 2.0 * ucur[i] + g->W[i] * lap[i] - g->am[i] * uprev[i];
+        if (i == src) rhs += srcval;
+        unext[i] = rhs / g->ap[i];
+    }
+}
+
+typedef struct {
+    int nshots, nrec, nt;
+    const int32_t *src;     /* [nshots][3] */
+    const double *wavelet;  /* [nshots][nt] */
+    const int32_t *rec;     /* [nshots][nrec][3] */
+} og_acq;
+
+static int og_acq_index(const og_grid *g, const og_acq *q, int s, int64_t *src, int64_t *rec)
+{
+    *src = og_index(g, q->src + 3 * s);
+    if (*src < 0) return -1;
+    for (int r = 0; r < q->nrec; ++r) {
+        rec[r] = og_index(g, q->rec + 3 * ((int64_t)s * q->nrec + r));
+        if (rec[r] < 0) return -1;
+    }
+    return 0;
+}
+
+/* Forward modelling of every shot.  traces[s][n][r] = u^{n+1}(rec_r).  final_u, when
+ * given, receives per shot the last two states (u^nt, u^{nt-1}) on the computed grid. */
+int oracle_forward(int ndim, const int64_t *shape, const double *h, const double *v,
+                   double dt, int nt, int M, int nb, double r0, double vref,
+                   int nshots, const int32_t *src, const double *wavelet,
+                   int nrec, const int32_t *rec, double *traces, double *final_u)
+{
+    og_grid g;
+    int rc = og_build(&g, ndim, shape, h, v, dt, M, nb, r0, vref);
+    if (rc) return rc;
+    og_acq q = {nshots, nrec, nt, src, wavelet, rec};
+    double *a = calloc(g.ncell, sizeof(double));
+    double *b = calloc(g.ncell, sizeof(double));
+    double *c = calloc(g.ncell, sizeof(double));
+    double *lap = malloc(sizeof(double) * g.ncell);
+    int64_t *ri = malloc(sizeof(int64_t) * (nrec > 0 ? nrec : 1));
+    if (!a || !b || !c || !lap || !ri) { rc = -3; goto done; }
+    for (int s = 0; s < nshots; ++s) {
+        int64_t si;
+        if (og_acq_index(&g, &q, s, &si, ri)) { rc = -1; goto done; }
+        memset(a, 0, sizeof(double) * g.ncell);  /* u^{n-1} */
+        memset(b, 0, sizeof(double) * g.ncell);  /* u^n */
+        for (int n = 0; n < nt; ++n) {
+            double w = wavelet[(int64_t)s * nt + n];
+            og_step(&g, b, a, c, lap, si, dt * dt * w);
+            for (int r = 0; r < nrec; ++r)
+                traces[((int64_t)s * nt + n) * nrec + r] = c[ri[r]];
+            double *t = a; a = b; b = c; c = t;   /* (prev, cur) <- (cur, next) */
+        }
+        if (final_u) {
+            memcpy(final_u + (2 * (int64_t)s) * g.ncell, b, sizeof(double) * g.ncell);
+            memcpy(final_u + (2 * (int64_t)s + 1) * g.ncell, a, sizeof(double) * g.ncell);
+        }
+    }
+done:
+    free(a); free(b); free(c); free(lap); free(ri);
+    og_free(&g);
+    return rc;
+}
+
+double oracle_misfit(const double *dmod, const double *dobs, int64_t n)
+{
+    double phi = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double r = dmod[i] - dobs[i];
+        phi += r * r;   /* Eq. 1: squared L2 norm, no 1/2 and no dt weight */
+    }
+    return phi;
+}
+
+/* ------------------------------------------------------------------ adjoint */
+
+/* Exact discrete adjoint of the damped leapfrog.  Derivation (Lagrangian of the
+ * constraints a+ u^{m} - (2I + W L) u^{m-1} + a- u^{m-2} - dt^2 w[m-1] e_src = 0,
+ * m = 1..nt): with nu^{nt+1} = nu^{nt+2} = 0, for m = nt down to 1,
+ *   a+ nu^m = 2 nu^{m+1} + L (W nu^{m+1}) - a- nu^{m+2} + R^T q[m-1],
+ * where q[n] is the trace-space adjoint source (2 (d - d_obs) for Eq. 1).  L is
+ * symmetric and W diagonal, so the transposed step applies the stencil to W nu.
+ * Then   d phi / d W = sum_{m=1}^{nt} nu^{m+1} (L u^m)   (zero-lag imaging) and the
+ * wavelet sensitivity is  d / d w[n] = dt^2 nu^{n+1}(src).
+ *
+ * The forward history u^m, m = 1..nt-1, is needed in reverse order.  It is rebuilt
+ * segment by segment from exact double-precision checkpoints (u^{a}, u^{a-1}) taken
+ * every `seg` steps in a first forward sweep; recomputation repeats the same
+ * arithmetic, so every u^m equals the stored-history value bit for bit. */
+static int og_adjoint(const og_grid *g, const og_acq *q, int s, const double *adjsrc,
+                      double *gW, double *xadj, int seg)
+{
+    const int nt = q->nt, nrec = q->nrec;
+    const double dt = g->dt;
+    if (seg < 1) seg = 1;
+    int nseg = (nt + seg - 1) / seg;
+    int rc = 0;
+    int64_t si;
+    int64_t *ri = malloc(sizeof(int64_t) * (nrec > 0 ? nrec : 1));
+    double *ck = malloc(sizeof(double) * g->ncell * 2 * (size_t)nseg);
+    double *hist = malloc(sizeof(double) * g->ncell * (size_t)(seg + 2));
+    double *lap = malloc(sizeof(double) * g->ncell);
+    double *tmp = malloc(sizeof(double) * g->ncell);
+    double *n1 = calloc(g->ncell, sizeof(double));   /* nu^{m+1} */
+    double *n2 = calloc(g->ncell, sizeof(double));   /* nu^{m+2} */
+    double *n0 = calloc(g->ncell, sizeof(double));   /* nu^{m}   */
+    double *ua = calloc(g->ncell, sizeof(double));
+    double *ub = calloc(g->ncell, sizeof(double));
+    double *uc = calloc(g->ncell, sizeof(double));
+    if (!ri || !ck || !hist || !lap || !tmp || !n1 || !n2 || !n0 || !ua || !ub || !uc) {
+        rc = -3; goto done;
+    }
+    if (og_acq_index(g, q, s, &si, ri)) { rc = -1; goto done; }
+    const double *w = q->wavelet + (int64_t)s * nt;
+
+    /* forward sweep: checkpoint (u^{k seg}, u^{k seg - 1}) for k = 0..nseg-1 */
+    for (int n = 0; n < nt; ++n) {
+        if (n % seg == 0) {
+            int k = n / seg;
+            memcpy(ck + (2 * (size_t)k) * g->ncell, ub, sizeof(double) * g->ncell);
+            memcpy(ck + (2 * (size_t)k + 1) * g->ncell, ua, sizeof(double) * g->ncell);
+        }
+        og_step(g, ub, ua, uc, lap, si, dt * dt * w[n]);
+        double *t = ua; ua = ub; ub = uc; uc = t;
+    }
+
+    /* reverse sweep, one segment (a, a+seg] at a time, last segment first */
+    int m = nt;
+    for (int k = nseg - 1; k >= 0; --k) {
+        int a = k * seg;
+        int top = (a + seg < nt) ? a + seg : nt;
+        /* rebuild u^{a}, ..., u^{top} into hist[0..top-a] */
+        memcpy(hist, ck + (2 * (size_t)k) * g->ncell, sizeof(double) * g->ncell);
+        memcpy(ua, ck + (2 * (size_t)k + 1) * g->ncell, sizeof(double) * g->ncell);
+        for (int j = 1; j <= top - a; ++j) {
+            const double *cur = hist + (size_t)(j - 1) * g->ncell;
+            const double *prev = (j == 1) ? ua : hist + (size_t)(j - 2) * g->ncell;
+            og_step(g, cur, prev, hist + (size_t)j * g->ncell, lap, si,
+                    dt * dt * w[a + j - 1]);
+        }
+        for (; m > a; --m) {
+            /* nu^m from nu^{m+1}, nu^{m+2} and the adjoint source of sample m-1 */
+            #pragma omp parallel for schedule(static)
+            for (int64_t i = 0; i < g->ncell; ++i) tmp[i] = g->W[i] * n1[i];
+            og_laplacian(g, tmp, lap);
+            #pragma omp parallel for schedule(static)
+            for (int64_t i = 0; i < g->ncell; ++i)
+                n0[i] = 2.0 * n1[i] + lap[i] - g->am[i] * n2[i];
+            const double *qm = adjsrc + ((int64_t)s * nt + (m - 1)) * nrec;
+            for (int r = 0; r < nrec; ++r) n0[ri[r]] += qm[r];
+            #pragma omp parallel for schedule(static)
+            for (int64_t i = 0; i < g->ncell; ++i) n0[i] /= g->ap[i];
+            /* imaging: nu^{m+1} L u^m (nu^{nt+1} = 0 makes the m = nt term vanish) */
+            if (m < nt && gW) {
+                og_laplacian(g, hist + (size_t)(m - a) * g->ncell, lap);
+                #pragma omp parallel for schedule(static)
+                for (int64_t i = 0; i < g->ncell; ++i) gW[i] += n1[i] * lap[i];
+            }
+            if (xadj) xadj[(int64_t)s * nt + (m - 1)] = dt * dt * n0[si];
+            double *t = n2; n2 = n1; n1 = n0; n0 = t;
+        }
+    }
+done:
+    free(ri); free(ck); free(hist); free(lap); free(tmp);
+    free(n1); free(n2); free(n0); free(ua); free(ub); free(uc);
+    return rc;
+}
+
+/* Gradient of phi = sum_shots ||d_mod - d_obs||^2 with respect to the physical
+ * velocity grid.  adjsrc, when given ([nshots][nt][nrec]), replaces 2 (d - d_obs) as
+ * the adjoint source (then grad is J^T adjsrc, the Jacobian-transpose product, and
+ * dobs is not read).  gW_out, when given, receives d phi / d W on the computed grid
+ * (summed over shots).  seg is the checkpoint interval of the reverse sweep. */
+int oracle_gradient(int ndim, const int64_t *shape, const double *h, const double *v,
+                    double dt, int nt, int M, int nb, double r0, double vref,
+                    int nshots, const int32_t *src, const double *wavelet,
+                    int nrec, const int32_t *rec, const double *dobs,
+                    const double *adjsrc, double *misfit, double *grad,
+                    double *gW_out, int seg)
+{
+    og_grid g;
+    int rc = og_build(&g, ndim, shape, h, v, dt, M, nb, r0, vref);
+    if (rc) return rc;
+    og_acq q = {nshots, nrec, nt, src, wavelet, rec};
+    int64_t ntr = (int64_t)nshots * nt * nrec;
+    double *gW = calloc(g.ncell, sizeof(double));
+    double *res = NULL;
+    if (!gW) { rc = -3; goto done; }
+    if (!adjsrc) {
+        double *dmod = malloc(sizeof(double) * (ntr > 0 ? ntr : 1));
+        res = malloc(sizeof(double) * (ntr > 0 ? ntr : 1));
+        if (!dmod || !res) { free(dmod); rc = -3; goto done; }
+        rc = oracle_forward(ndim, shape, h, v, dt, nt, M, nb, r0, vref, nshots, src,
+                            wavelet, nrec, rec, dmod, NULL);
+        if (rc) { free(dmod); goto done; }
+        if (misfit) *misfit = oracle_misfit(dmod, dobs, ntr);
+        for (int64_t i = 0; i < ntr; ++i) res[i] = 2.0 * (dmod[i] - dobs[i]);
+        free(dmod);
+        adjsrc = res;
+    }
+    for (int s = 0; s < nshots; ++s) {
+        rc = og_adjoint(&g, &q, s, adjsrc, gW, NULL, seg);
+        if (rc) goto done;
+    }
+    if (gW_out) memcpy(gW_out, gW, sizeof(double) * g.ncell);
+    /* dW/dv_c = 2 v_c dt^2, then fold every computed cell onto the physical cell its
+     * velocity was replicated from (the transpose of the edge-replication padding). */
+    int64_t nphys = g.np[0] * g.np[1] * g.np[2];
+    memset(grad, 0, sizeof(double) * nphys);
+    int nby = (ndim == 3) ? nb : 0;
+    for (int64_t iz = 0; iz < g.n[0]; ++iz)
+        for (int64_t iy = 0; iy < g.n[1]; ++iy)
+            for (int64_t ix = 0; ix < g.n[2]; ++ix) {
+                int64_t i = (iz * g.n[1] + iy) * g.n[2] + ix;
+                int64_t pz = og_clamp(iz - nb, 0, g.np[0] - 1);
+                int64_t py = og_clamp(iy - nby, 0, g.np[1] - 1);
+                int64_t px = og_clamp(ix - nb, 0, g.np[2] - 1);
+                grad[(pz * g.np[1] + py) * g.np[2] + px] += 2.0 * g.vc[i] * dt * dt * gW[i];
+            }
+done:
+    free(gW); free(res);
+    og_free(&g);
+    return rc;
+}
+
+/* Adjoint of the linear map wavelet -> traces (F: w -> d at fixed v):
+ * x[s][n] = dt^2 nu^{n+1}(src_s), with y injected at the receivers. */
+int oracle_source_adjoint(int ndim, const int64_t *shape, const double *h, const double *v,
+                          double dt, int nt, int M, int nb, double r0, double vref,
+                          int nshots, const int32_t *src, int nrec, const int32_t *rec,
+                          const double *y, double *x)
+{
+    og_grid g;
+    int rc = og_build(&g, ndim, shape, h, v, dt, M, nb, r0, vref);
+    if (rc) return rc;
+    double *zero = calloc((size_t)nshots * nt, sizeof(double));
+    if (!zero) { og_free(&g); return -3; }
+    og_acq q = {nshots, nrec, nt, src, zero, rec};
+    for (int s = 0; s < nshots && rc == 0; ++s)
+        rc = og_adjoint(&g, &q, s, y, NULL, x, nt);
+    free(zero);
+    og_free(&g);
+    return rc;
+}
+
+/* Computed-grid extents and the W, a+ and a- fields the oracle uses (for the energy
+ * test and for reports). */
+int oracle_model_fields(int ndim, const int64_t *shape, const double *h, const double *v,
+                        double dt, int M, int nb, double r0, double vref,
+                        int64_t *ncomp, double *W, double *ap, double *am)
+{
+    og_grid g;
+    int rc = og_build(&g, ndim, shape, h, v, dt, M, nb, r0, vref);
+    if (rc) return rc;
+    for (int a = 0; a < 3; ++a) ncomp[a] = g.n[a];
+    if (W) memcpy(W, g.W, sizeof(double) * g.ncell);
+    if (ap) memcpy(ap, g.ap, sizeof(double) * g.ncell);
+    if (am) memcpy(am, g.am, sizeof(double) * g.ncell);
+    og_free(&g);
+    return 0;
+}
