@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Throughput of the FWI hot path on GB300: one step = one full misfit-gradient
+evaluation (forward sweep with receiver sampling, checkpoint encodes, L2 misfit,
+checkpointed reverse sweep with recomputation, adjoint steps with zero-lag imaging,
+FP64 gradient fold and finish) of a 3-D shot, through the library's C ABI.
+
+Metric: Gpts/s fwd+adjoint = computed grid points x time steps x shots / step time.
+Default workload: the 512^3 salt model (h 12.5 m, dt 0.6 ms, 4000 steps, 16th order,
+20-cell sponge, 256 x 256 receivers, FP16 checkpoints).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica of the workload (shots
+are independent units; the library has no multi-GPU path) and rank 0 prints one JSON
+line with the whole-job rate.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+HBM_FALLBACK_GBS = 6800.0
+BYTES_FWD = 16   # read u^n, u^{n-1}, W; write u^{n+1} (per point)
+BYTES_ADJ = 28   # + read u^m, read and write the FP32 gradient accumulator
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="salt_3d_512",
+                    choices=["salt_3d_512", "layered_3d_256"])
+    ap.add_argument("--nt", type=int, default=0, help="override the step count (short runs)")
+    ap.add_argument("--snap-budget-gb", type=float, default=64.0)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name, nt_override):
+    from paper_1912_08063_gb300 import synth
+    if name == "salt_3d_512":
+        w = synth.salt_3d(512)
+    else:
+        w = synth.layered_3d(256)
+    if nt_override:
+        w.nt = nt_override
+    return w
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1912_08063_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current
+    kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+        e = d[kernel]
+        if e.get("source_hash") == kernel_source_hash():
+            return float(e["bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, sample_n=192, sample_nt=10):
+    """The FP64 oracle, as it stands, on a bounded sample: a centred sample_n^3 crop of
+    the model (same spacing, order, sponge, dt), one misfit-gradient evaluation of
+    sample_nt steps.  Returns (Gpts/s, seconds, description, threads)."""
+    import oracle
+    n = w.shape[0]
+    c0 = (n - sample_n) // 2
+    sl = slice(c0, c0 + sample_n)
+    v = np.ascontiguousarray(w.v[sl, sl, sl], dtype=np.float64)
+    src = np.array([[10, sample_n // 2, sample_n // 2]], dtype=np.int32)
+    rec = np.array([[5, j, i] for j in range(0, sample_n, 8) for i in range(0, sample_n, 8)],
+                   dtype=np.int32)
+    wav = w.wavelets()[:1, :sample_nt]
+    p = oracle.Problem(v, w.h, w.dt, sample_nt, order=w.order, nb=w.nb, src=src, rec=rec,
+                       wavelet=wav)
+    dobs = np.zeros((1, sample_nt, rec.shape[0]))
+    oracle.build()
+    t0 = time.perf_counter()
+    p.gradient(dobs, seg=max(1, int(round(np.sqrt(sample_nt)))))
+    t = time.perf_counter() - t0
+    pts = 1
+    for s in p.computed_shape():
+        pts *= s
+    desc = (f"oracle misfit gradient on a centred {sample_n}^3 crop of the {n}^3 model "
+            f"({pts / 1e6:.1f} M computed points incl. sponge, order {w.order}, "
+            f"{sample_nt} steps); Gpts/s = points x steps / wall time")
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return pts * sample_nt / t / 1e9, t, desc, threads
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args.workload, args.nt)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        g, t, desc, threads = cpu_baseline(w)
+        if i >= args.warmup:
+            vals.append((g, t))
+    value = statistics.median(v for v, _ in vals)
+    ms = statistics.median(t for _, t in vals) * 1e3
+    line = {"impl": "reference", "metric": "Gpts/s fwd+adjoint", "value": value,
+            "unit": "Gpts/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "note": "bounded CPU sample, see cpu_baseline"},
+            "cpu_baseline": {"value": value, "unit": "Gpts/s", "cores": threads,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_1912_08063_gb300 import fwi
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = workload(args.workload, args.nt)
+    dev = torch.device("cuda", local)
+    budget = int(args.snap_budget_gb * (1 << 30))
+    model = fwi.FwiModel(torch.from_numpy(w.v).to(dev), w.h, w.dt, w.nt, order=w.order,
+                         nb=w.nb, snap_dtype=w.snap_dtype, snap_budget_bytes=budget,
+                         sponge_vref=4500.0, timing=True)
+    acq = fwi.Acquisition(w.src, w.rec)
+    wav = torch.from_numpy(w.wavelets()).to(dev)
+    # observed data from the perturbed model (input synthesis, untimed)
+    obs_model = fwi.FwiModel(torch.from_numpy(w.v_obs).to(dev), w.h, w.dt, w.nt,
+                             order=w.order, nb=w.nb, sponge_vref=4500.0)
+    dobs = obs_model.forward(acq, wav)
+    obs_model.close()
+    torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        phi, g = model.gradient(acq, wav, dobs)
+    torch.cuda.synchronize()
+    info0 = model.info()
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        phi, g = model.gradient(acq, wav, dobs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    info1 = model.info()
+
+    pts = info1["points"]
+    units = pts * w.nt * w.nshots
+    value = units * world / (ms * 1e-3) / 1e9
+    fwd_n = info1["fwd_step_launches"] - info0["fwd_step_launches"]
+    adj_n = info1["adj_step_launches"] - info0["adj_step_launches"]
+    fwd_ms = info1["fwd_step_ms"] - info0["fwd_step_ms"]
+    adj_ms = info1["adj_step_ms"] - info0["adj_step_ms"]
+    launches = (info1["kernel_launches"] - info0["kernel_launches"])
+    peak, peak_kind = measured_hbm()
+    if fwd_ms >= adj_ms:
+        kname, kbytes, kms, kn = "fwd_step_3d", BYTES_FWD * pts * w.nshots, fwd_ms, fwd_n
+    else:
+        kname, kbytes, kms, kn = "adj_step_3d", BYTES_ADJ * pts * w.nshots, adj_ms, adj_n
+    achieved = kbytes / (kms / kn * 1e-3) / 1e9 if kn else 0.0
+    roof = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": recorded_traffic(kname),
+            "algorithmic_bytes_per_launch": kbytes,
+            "fwd_step": {"launches": fwd_n, "avg_ms": fwd_ms / max(fwd_n, 1),
+                         "GB/s": BYTES_FWD * pts * w.nshots / (fwd_ms / max(fwd_n, 1) * 1e-3) / 1e9
+                         if fwd_n else None},
+            "adj_step": {"launches": adj_n, "avg_ms": adj_ms / max(adj_n, 1),
+                         "GB/s": BYTES_ADJ * pts * w.nshots / (adj_ms / max(adj_n, 1) * 1e-3) / 1e9
+                         if adj_n else None}}
+
+    # end to end through the C ABI with pinned host buffers, copies inside the timing
+    e2e = None
+    if not args.no_e2e:
+        v_h = torch.from_numpy(w.v).pin_memory()
+        wav_h = torch.from_numpy(w.wavelets()).pin_memory()
+        dobs_h = dobs.cpu().pin_memory()
+        grad_h = torch.empty(w.shape, dtype=torch.float32).pin_memory()
+        phi_h = np.zeros(1, dtype=np.float64)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            fwi.fwi_update_velocity(model.handle, v_h)
+            fwi.fwi_adjoint_gradient(model.handle, acq.c, wav_h, dobs_h, phi_h, grad_h)
+        te = (time.perf_counter() - t0) / args.e2e_steps
+        tt = torch.tensor([te], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt.item())
+        h2d = v_h.numel() * 4 + wav_h.numel() * 4 + dobs_h.numel() * 4
+        d2h = grad_h.numel() * 4 + 8
+        e2e = {"value": units * world / te / 1e9, "unit": "Gpts/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": te * 1e3, "misfit": float(phi_h[0])}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        g, tsec, desc, threads = cpu_baseline(w)
+        cpu = {"value": g, "unit": "Gpts/s", "cores": threads, "kind": "oracle",
+               "sample": desc, "seconds": round(tsec, 2)}
+
+    if rank == 0:
+        line = {"metric": "Gpts/s fwd+adjoint", "value": round(value, 3), "unit": "Gpts/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w.name, "grid": list(w.shape), "computed_points": pts,
+                           "order": w.order, "nt": w.nt, "shots": w.nshots,
+                           "receivers": w.nrec, "checkpoints": w.snap_dtype,
+                           "checkpoint_slots": info1["snap_slots"],
+                           "forward_steps_per_gradient": info1["last_forward_steps"],
+                           "adjoint_steps_per_gradient": info1["last_adjoint_steps"],
+                           "l2": "inputs larger than L2 (each field >= 100 MB)",
+                           "parallelism": f"replicas x{world}"},
+                "clocks": ck, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roof, "cpu_baseline": cpu, "misfit": float(phi.item())}
+        print(json.dumps(line), flush=True)
+    model.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

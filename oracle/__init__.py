@@ -67,6 +67,22 @@ def _load():
             lib.oracle_source_adjoint.restype = i
             lib.oracle_model_fields.argtypes = [i, i64p, P, P, d, i, i, d, d, i64p, P, P, P]
             lib.oracle_model_fields.restype = i
+            f = ctypes.c_float
+            u16 = ctypes.c_uint16
+            lib.oracle_snap_scale.argtypes = [f, i]
+            lib.oracle_snap_scale.restype = f
+            lib.oracle_f32_to_bf16.argtypes = [f]
+            lib.oracle_f32_to_bf16.restype = u16
+            lib.oracle_f32_to_f16.argtypes = [f]
+            lib.oracle_f32_to_f16.restype = u16
+            lib.oracle_bf16_to_f32.argtypes = [u16]
+            lib.oracle_bf16_to_f32.restype = f
+            lib.oracle_f16_to_f32.argtypes = [u16]
+            lib.oracle_f16_to_f32.restype = f
+            lib.oracle_snap_encode.argtypes = [P, P, ctypes.c_int64, i, P, P]
+            lib.oracle_snap_encode.restype = None
+            lib.oracle_snap_decode.argtypes = [P, f, ctypes.c_int64, i, P, P]
+            lib.oracle_snap_decode.restype = None
             _lib = lib
     return _lib
 
@@ -227,3 +243,42 @@ class Problem:
 def misfit(dmod, dobs) -> float:
     a, b = _f64(dmod), _f64(dobs)
     return _load().oracle_misfit(_ptr(a), _ptr(b), a.size)
+
+
+SNAP = {"fp32": 0, "bf16": 1, "fp16": 2}
+
+
+def snap_scale(maxabs: float, dtype: str) -> float:
+    return _load().oracle_snap_scale(float(maxabs), SNAP[dtype])
+
+
+def snap_encode(a, b, dtype: str):
+    """(codes uint16 [2][n], scale) of the checkpoint pair (a, b) (FP32 inputs)."""
+    a = np.ascontiguousarray(a, dtype=np.float32).ravel()
+    b = np.ascontiguousarray(b, dtype=np.float32).ravel()
+    code = np.zeros((2, a.size), dtype=np.uint16)
+    sc = ctypes.c_float(0.0)
+    _load().oracle_snap_encode(_ptr(a), _ptr(b), a.size, SNAP[dtype], _ptr(code),
+                               ctypes.byref(sc))
+    return code, sc.value
+
+
+def snap_decode(code, scale, dtype: str):
+    code = np.ascontiguousarray(code, dtype=np.uint16).reshape(2, -1)
+    n = code.shape[1]
+    a = np.zeros(n, dtype=np.float32)
+    b = np.zeros(n, dtype=np.float32)
+    _load().oracle_snap_decode(_ptr(code), float(scale), n, SNAP[dtype], _ptr(a), _ptr(b))
+    return a, b
+
+
+def f32_to_bf16(x) -> np.ndarray:
+    f = _load().oracle_f32_to_bf16
+    return np.array([f(float(v)) for v in np.asarray(x, dtype=np.float32).ravel()],
+                    dtype=np.uint16)
+
+
+def f32_to_f16(x) -> np.ndarray:
+    f = _load().oracle_f32_to_f16
+    return np.array([f(float(v)) for v in np.asarray(x, dtype=np.float32).ravel()],
+                    dtype=np.uint16)

@@ -517,3 +517,107 @@ int oracle_model_fields(int ndim, const int64_t *shape, const double *h, const d
     og_free(&g);
     return 0;
 }
+
+/* ------------------------------------------------------------------ checkpoint codec */
+
+/* Checkpoints of the reverse sweep (the paper only names the gradient, Sec. 1; the
+ * checkpoint format is a reading): the pair (u^n, u^{n-1}) is stored as 16-bit floats
+ * after scaling by s = 2^floor(log2(T / max|u^n, u^{n-1}|)), T = 2^14 for IEEE half and
+ * T = 1 for bfloat16, with round-to-nearest-even; s = 1 for an all-zero pair and NaN
+ * when the pair holds a non-finite value; floor(log2 .) is clamped to [-126, 127]. */
+float oracle_snap_scale(float maxabs, int dtype)
+{
+    if (dtype == 0 || maxabs == 0.0f) return 1.0f;
+    if (!isfinite(maxabs)) return NAN;
+    int texp = (dtype == 2) ? 14 : 0;
+    int ex;
+    double fr = frexp((double)maxabs, &ex);   /* maxabs = fr 2^ex, fr in [0.5, 1) */
+    /* log2(T / max) = texp - ex - log2(fr), -log2(fr) in (0, 1] */
+    int k = (fr == 0.5) ? texp - ex + 1 : texp - ex;
+    if (k < -126) k = -126;
+    if (k > 127) k = 127;
+    return (float)ldexp(1.0, k);
+}
+
+static uint32_t or_bits(float f) { uint32_t x; memcpy(&x, &f, 4); return x; }
+static float or_float(uint32_t x) { float f; memcpy(&f, &x, 4); return f; }
+
+/* float -> bfloat16, round to nearest, ties to even (NaN stays a quiet NaN) */
+uint16_t oracle_f32_to_bf16(float f)
+{
+    uint32_t x = or_bits(f);
+    if ((x & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((x >> 16) | 0x40u);
+    uint32_t lsb = (x >> 16) & 1u;
+    x += 0x7fffu + lsb;
+    return (uint16_t)(x >> 16);
+}
+
+float oracle_bf16_to_f32(uint16_t h) { return or_float((uint32_t)h << 16); }
+
+/* float -> IEEE binary16, round to nearest, ties to even, with subnormals, overflow to
+ * infinity and NaN kept */
+uint16_t oracle_f32_to_f16(float f)
+{
+    uint32_t x = or_bits(f);
+    uint32_t sign = (x >> 16) & 0x8000u;
+    uint32_t ax = x & 0x7fffffffu;
+    if (ax >= 0x7f800000u) return (uint16_t)(sign | (ax > 0x7f800000u ? 0x7e00u : 0x7c00u));
+    if (ax >= 0x477ff000u) return (uint16_t)(sign | 0x7c00u);   /* >= 65520: infinity */
+    if (ax >= 0x38800000u) {                                     /* >= 2^-14: normal */
+        uint32_t mant = ax & 0x7fffffu;
+        uint32_t e = (ax >> 23) - 127u + 15u;
+        uint32_t h = (e << 10) | (mant >> 13);
+        uint32_t rem = mant & 0x1fffu;
+        if (rem > 0x1000u || (rem == 0x1000u && (h & 1u))) h++;
+        return (uint16_t)(sign | h);
+    }
+    if (ax < 0x33000000u) return (uint16_t)sign;                 /* < 2^-25: zero */
+    /* subnormal result: count units of 2^-24 */
+    uint32_t m = (ax & 0x7fffffu) | 0x800000u;
+    int e = (int)(ax >> 23) - 127;                               /* -25 .. -15 */
+    int shift = -e - 1;                                          /* 14 .. 24 */
+    uint32_t q = m >> shift, rem = m & ((1u << shift) - 1u), half = 1u << (shift - 1);
+    if (rem > half || (rem == half && (q & 1u))) q++;
+    return (uint16_t)(sign | q);
+}
+
+float oracle_f16_to_f32(uint16_t h)
+{
+    uint32_t sign = ((uint32_t)h & 0x8000u) << 16;
+    uint32_t e = (h >> 10) & 0x1fu, m = h & 0x3ffu;
+    if (e == 0x1fu) return or_float(sign | 0x7f800000u | (m << 13));
+    if (e == 0) return (sign ? -1.0f : 1.0f) * (float)ldexp((double)m, -24);
+    return or_float(sign | ((e - 15u + 127u) << 23) | (m << 13));
+}
+
+/* Encode the pair (a, b) of n values: code[0..n) from a, code[n..2n) from b. */
+void oracle_snap_encode(const float *a, const float *b, int64_t n, int dtype,
+                        uint16_t *code, float *scale)
+{
+    float mx = 0.0f;
+    int bad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        float x = fabsf(a[i]), y = fabsf(b[i]);
+        if (!isfinite(x) || !isfinite(y)) bad = 1;
+        if (x > mx) mx = x;
+        if (y > mx) mx = y;
+    }
+    float s = bad ? NAN : oracle_snap_scale(mx, dtype);
+    *scale = s;
+    for (int64_t i = 0; i < n; ++i) {
+        float va = a[i] * s, vb = b[i] * s;   /* single-precision products, as stored */
+        code[i] = dtype == 2 ? oracle_f32_to_f16(va) : oracle_f32_to_bf16(va);
+        code[n + i] = dtype == 2 ? oracle_f32_to_f16(vb) : oracle_f32_to_bf16(vb);
+    }
+}
+
+void oracle_snap_decode(const uint16_t *code, float scale, int64_t n, int dtype,
+                        float *a, float *b)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        float va = dtype == 2 ? oracle_f16_to_f32(code[i]) : oracle_bf16_to_f32(code[i]);
+        float vb = dtype == 2 ? oracle_f16_to_f32(code[n + i]) : oracle_bf16_to_f32(code[n + i]);
+        a[i] = va / scale;
+        b[i] = vb / scale;
+    }
+}

@@ -1,0 +1,932 @@
+// C ABI of libfwi (include/fwi.h): model set-up, workspace, and the executors of the
+// forward sweep, the checkpointed reverse sweep (gradient) and the source adjoint.
+// Every step of the hot path runs in the library's CUDA kernels; this file only
+// validates arguments, owns device memory and orders launches on the caller's stream.
+#include "fwi.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fwi_internal.h"
+
+namespace fwi {
+std::vector<int32_t> revolve_actions(int32_t nsteps, int32_t nslots, int64_t *n_forward);
+}
+
+using namespace fwi;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define FWI_CU(call)                                                                     \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? FWI_ERR_OOM : FWI_ERR_CUDA,    \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));             \
+    } while (0)
+
+#define FWI_TRY(expr)             \
+    do {                          \
+        int rc_ = (expr);         \
+        if (rc_ != FWI_OK) return rc_; \
+    } while (0)
+
+// a kernel launch of the library, counted on the model
+#define FWI_LAUNCH(model, call)   \
+    do {                          \
+        ++(model)->launches;      \
+        FWI_CU(call);             \
+    } while (0)
+
+// ---------------------------------------------------------------- host numerics
+
+// Central second-derivative weights of radius M (order 2M), the symmetric stencil exact
+// on polynomials of degree <= 2M+1:  c_k = 2 (-1)^{k+1} (M!)^2 / (k^2 (M-k)! (M+k)!),
+// c_0 = -2 sum_k c_k  (Taylor weights; the paper uses stencils of order >= 8, Sec. 3).
+int host_coeffs(int M, double *c)
+{
+    if (M < 1 || M > kMaxM) return FWI_ERR_ARG;
+    double total = 0.0;
+    for (int k = 1; k <= M; ++k) {
+        // (M!)^2 / ((M-k)! (M+k)!) = prod_{i=1..k} (M - k + i) / (M + i)
+        double ratio = 1.0;
+        for (int i = 1; i <= k; ++i) ratio *= (double)(M - k + i) / (double)(M + i);
+        c[k] = ((k & 1) ? 2.0 : -2.0) * ratio / ((double)k * k);
+        total += c[k];
+    }
+    c[0] = -2.0 * total;
+    return FWI_OK;
+}
+
+// largest magnitude of the 1-D stencil's symbol (at the Nyquist wavenumber)
+double host_symbol_max(int M)
+{
+    double c[kMaxM + 1];
+    host_coeffs(M, c);
+    double s = c[0];
+    for (int k = 1; k <= M; ++k) s += 2.0 * c[k] * ((k & 1) ? -1.0 : 1.0);
+    return std::fabs(s);
+}
+
+double host_cfl(int ndim, int M, const float *h, double vmax, double dt)
+{
+    const double S = host_symbol_max(M);
+    double acc = S / ((double)h[0] * h[0]) + S / ((double)h[2] * h[2]);
+    if (ndim == 3) acc += S / ((double)h[1] * h[1]);
+    return vmax * dt * std::sqrt(acc) / 2.0;
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t want)
+    {
+        if (want <= bytes && p) return FWI_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        if (want == 0) return FWI_OK;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return fail(FWI_ERR_OOM, "cudaMalloc of " + std::to_string(want) + " bytes failed");
+        }
+        bytes = want;
+        return FWI_OK;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T> T *as() const { return (T *)p; }
+};
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+}  // namespace
+
+struct fwi_model {
+    int ndim = 0, M = 0, order = 0, nb = 0, nt = 0;
+    int64_t np[3] = {0, 0, 0};
+    float h[3] = {0, 0, 0};
+    float dt = 0;
+    fwi_opts opts{};
+    Geom g{};
+    Coefs co{};
+    float vmax = 0, vref = 0, cfl = 0, eta_max[3] = {0, 0, 0};
+    // model
+    DevBuf v, W, sig;   // sig: sig_z[nz] | sig_y[ny] | sig_x[nx]
+    // workspace
+    int cap_shots = 0, cap_nrec = 0;
+    DevBuf u[2], mu[2], g32, g64, traces, src_off, rec_off, inj, src_scale, maxbits, partials,
+        phi, snaps, scales;
+    DevBuf stage_in[3], stage_out[2];
+    int nslots = 0;
+    size_t slot_bytes = 0;
+    // cached geometry
+    std::vector<int32_t> geo_src, geo_rec;
+    int geo_shots = -1, geo_nrec = -1;
+    // cached schedule
+    int sched_nslots = -1;
+    std::vector<int32_t> sched;
+    int64_t sched_fwd = 0;
+    // status
+    unsigned *h_flag = nullptr, *d_flag = nullptr;
+    cudaStream_t last_stream = nullptr;
+    // stats of the last gradient call
+    int64_t st_fwd = 0, st_adj = 0, st_store = 0, st_restore = 0;
+    // launch count and kernel timing (opts.timing)
+    int64_t launches = 0;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_kind;   // per event pair: 0 forward step, 1 reverse step
+    size_t ev_used = 0;
+    int64_t t_fwd_n = 0, t_adj_n = 0;
+    double t_fwd_ms = 0.0, t_adj_ms = 0.0;
+
+    int64_t device_bytes() const
+    {
+        size_t b = v.bytes + W.bytes + sig.bytes + g32.bytes + g64.bytes + traces.bytes +
+                   src_off.bytes + rec_off.bytes + inj.bytes + src_scale.bytes + maxbits.bytes +
+                   partials.bytes + phi.bytes + snaps.bytes + scales.bytes;
+        for (int i = 0; i < 2; ++i) b += u[i].bytes + mu[i].bytes + stage_out[i].bytes;
+        for (int i = 0; i < 3; ++i) b += stage_in[i].bytes;
+        return (int64_t)b;
+    }
+};
+
+namespace {
+
+const float *sig_z(const fwi_model *m) { return m->sig.as<float>(); }
+const float *sig_y(const fwi_model *m) { return m->sig.as<float>() + m->g.nz; }
+const float *sig_x(const fwi_model *m) { return m->sig.as<float>() + m->g.nz + m->g.ny; }
+
+int check_status(fwi_model *m)
+{
+    if (m->h_flag && *(volatile unsigned *)m->h_flag)
+        return fail(FWI_ERR_UNSTABLE, "a wavefield became non-finite (latched device status)");
+    return FWI_OK;
+}
+
+// Copies a caller input (host or device) to the device; returns a device pointer.
+int stage_input(fwi_model *m, int slot, const void *src, size_t bytes, cudaStream_t s,
+                const void **dev)
+{
+    if (is_device_ptr(src)) {
+        *dev = src;
+        return FWI_OK;
+    }
+    FWI_TRY(m->stage_in[slot].ensure(bytes));
+    FWI_CU(cudaMemcpyAsync(m->stage_in[slot].p, src, bytes, cudaMemcpyHostToDevice, s));
+    *dev = m->stage_in[slot].p;
+    return FWI_OK;
+}
+
+// Device pointer an output can be written to: the caller's (device) or a staging buffer.
+int output_target(fwi_model *m, int slot, void *dst, size_t bytes, void **dev, bool *host)
+{
+    *host = !is_device_ptr(dst);
+    if (!*host) {
+        *dev = dst;
+        return FWI_OK;
+    }
+    FWI_TRY(m->stage_out[slot].ensure(bytes));
+    *dev = m->stage_out[slot].p;
+    return FWI_OK;
+}
+
+// Velocity-dependent state: copy v, largest velocity, sponge tables, CFL check, W.
+int set_velocity(fwi_model *m, const float *vp, cudaStream_t s)
+{
+    const int64_t nphys = m->np[0] * m->np[1] * m->np[2];
+    FWI_TRY(m->v.ensure(nphys * sizeof(float)));
+    FWI_CU(cudaMemcpyAsync(m->v.p, vp, nphys * sizeof(float), cudaMemcpyDefault, s));
+    // largest velocity through the codec's max|.| kernel (v > 0)
+    FWI_TRY(m->maxbits.ensure(64 * sizeof(unsigned)));
+    FWI_CU(cudaMemsetAsync(m->maxbits.p, 0, sizeof(unsigned), s));
+    FWI_LAUNCH(m, launch_maxabs(m->v.as<float>(), m->v.as<float>(), nphys, nphys, 1,
+                         m->maxbits.as<unsigned>(), s));
+    unsigned bits = 0;
+    FWI_CU(cudaMemcpyAsync(&bits, m->maxbits.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    FWI_CU(cudaStreamSynchronize(s));
+    float vmax;
+    std::memcpy(&vmax, &bits, sizeof(float));
+    if (!(vmax > 0.0f) || !std::isfinite(vmax))
+        return fail(FWI_ERR_ARG, "velocity must be finite and positive");
+    m->vmax = vmax;
+    m->vref = m->opts.sponge_vref > 0.0f ? m->opts.sponge_vref : vmax;
+    m->cfl = (float)host_cfl(m->ndim, m->M, m->h, vmax, m->dt);
+    if (!(m->cfl < 1.0f)) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf,
+                      "dt = %g s violates the stability limit: v_max dt sqrt(sum S/h^2)/2 = %g >= 1",
+                      (double)m->dt, (double)m->cfl);
+        return fail(FWI_ERR_CFL, buf);
+    }
+    // sponge: eta_a(i) = eta_max,a (depth_a(i)/nb)^2, eta_max,a = 3 vref ln(1/R0)/(2 nb h_a);
+    // the kernels read s = eta dt / 2 per axis
+    const int nb = m->nb;
+    const int ext[3] = {m->g.nz, m->g.ny, m->g.nx};
+    std::vector<float> sig(ext[0] + ext[1] + ext[2], 0.0f);
+    size_t base = 0;
+    for (int a = 0; a < 3; ++a) {
+        const bool present = !(a == 1 && m->ndim == 2);
+        double emax = 0.0;
+        if (present && nb > 0)
+            emax = 3.0 * m->vref * std::log(1.0 / m->opts.sponge_r0) / (2.0 * nb * m->h[a]);
+        m->eta_max[a] = (float)emax;
+        for (int i = 0; i < ext[a]; ++i) {
+            double d = 0.0;
+            if (present && nb > 0) {
+                if (i < nb) d = nb - i;
+                else if (i >= nb + m->np[a]) d = i - (nb + m->np[a] - 1);
+            }
+            const double eta = emax * (d / nb) * (d / nb);
+            sig[base + i] = (float)(0.5 * m->dt * (nb > 0 ? eta : 0.0));
+        }
+        base += ext[a];
+    }
+    FWI_TRY(m->sig.ensure(sig.size() * sizeof(float)));
+    FWI_CU(cudaMemcpyAsync(m->sig.p, sig.data(), sig.size() * sizeof(float),
+                           cudaMemcpyHostToDevice, s));
+    FWI_TRY(m->W.ensure(m->g.field * sizeof(float)));
+    FWI_CU(cudaMemsetAsync(m->W.p, 0, m->g.field * sizeof(float), s));
+    FWI_LAUNCH(m, launch_build_W(m->g, nb, m->np, m->v.as<float>(), m->dt, m->W.as<float>(), s));
+    FWI_CU(cudaStreamSynchronize(s));   // `sig` is a host temporary
+    return FWI_OK;
+}
+
+int validate_acq(const fwi_model *m, const fwi_acq *a)
+{
+    if (!a || a->nshots < 1 || a->nrec < 1 || !a->src || !a->rec)
+        return fail(FWI_ERR_ARG, "acquisition needs nshots >= 1, nrec >= 1, src and rec");
+    if ((int64_t)a->nshots * 65535 < a->nshots)
+        return fail(FWI_ERR_ARG, "too many shots");
+    auto inside = [&](const int32_t *p) {
+        if (p[0] < 0 || p[0] >= m->np[0] || p[2] < 0 || p[2] >= m->np[2]) return false;
+        if (m->ndim == 3) return p[1] >= 0 && p[1] < m->np[1];
+        return p[1] == 0;
+    };
+    for (int s = 0; s < a->nshots; ++s) {
+        if (!inside(a->src + 3 * s))
+            return fail(FWI_ERR_ARG, "source " + std::to_string(s) + " outside the grid");
+        for (int r = 0; r < a->nrec; ++r)
+            if (!inside(a->rec + 3 * ((int64_t)s * a->nrec + r)))
+                return fail(FWI_ERR_ARG, "receiver " + std::to_string(r) + " of shot " +
+                                             std::to_string(s) + " outside the grid");
+    }
+    return FWI_OK;
+}
+
+int64_t node_offset(const fwi_model *m, const int32_t *p)
+{
+    const int nby = m->ndim == 3 ? m->nb : 0;
+    return (int64_t)(p[0] + m->nb) * m->g.plane + (int64_t)(p[1] + nby) * m->g.px + (p[2] + m->nb);
+}
+
+// Per-shot buffers for `nshots` shots and `nrec` receivers; `grad` adds the reverse-sweep
+// fields.  Uploads the source/receiver offsets when the geometry changed.
+int ensure_workspace(fwi_model *m, const fwi_acq *a, bool grad, cudaStream_t s)
+{
+    const int ns = a->nshots, nr = a->nrec;
+    const size_t fb = (size_t)m->g.field * sizeof(float);
+    FWI_TRY(m->u[0].ensure(ns * fb));
+    FWI_TRY(m->u[1].ensure(ns * fb));
+    FWI_TRY(m->traces.ensure((size_t)ns * m->nt * nr * sizeof(float)));
+    FWI_TRY(m->src_off.ensure(ns * sizeof(int64_t)));
+    FWI_TRY(m->rec_off.ensure((size_t)ns * nr * sizeof(int64_t)));
+    FWI_TRY(m->inj.ensure((size_t)ns * nr * sizeof(float)));
+    FWI_TRY(m->src_scale.ensure(ns * sizeof(float)));
+    FWI_TRY(m->maxbits.ensure((ns > 64 ? ns : 64) * sizeof(unsigned)));
+    FWI_TRY(m->partials.ensure(1024 * sizeof(double)));
+    FWI_TRY(m->phi.ensure(sizeof(double)));
+    if (grad) {
+        FWI_TRY(m->mu[0].ensure(ns * fb));
+        FWI_TRY(m->mu[1].ensure(ns * fb));
+        FWI_TRY(m->g32.ensure(ns * fb));
+        FWI_TRY(m->g64.ensure(ns * 2 * fb));
+    }
+    if (ns > m->cap_shots) m->cap_shots = ns;
+    if (nr > m->cap_nrec) m->cap_nrec = nr;
+    const size_t nsrc = (size_t)ns * 3, nrec3 = (size_t)ns * nr * 3;
+    bool same = m->geo_shots == ns && m->geo_nrec == nr &&
+                std::memcmp(m->geo_src.data(), a->src, nsrc * sizeof(int32_t)) == 0 &&
+                std::memcmp(m->geo_rec.data(), a->rec, nrec3 * sizeof(int32_t)) == 0;
+    if (!same) {
+        std::vector<int64_t> so(ns), ro((size_t)ns * nr);
+        for (int i = 0; i < ns; ++i) so[i] = node_offset(m, a->src + 3 * i);
+        for (size_t i = 0; i < (size_t)ns * nr; ++i) ro[i] = node_offset(m, a->rec + 3 * i);
+        FWI_CU(cudaMemcpyAsync(m->src_off.p, so.data(), ns * sizeof(int64_t),
+                               cudaMemcpyHostToDevice, s));
+        FWI_CU(cudaMemcpyAsync(m->rec_off.p, ro.data(), ro.size() * sizeof(int64_t),
+                               cudaMemcpyHostToDevice, s));
+        FWI_CU(cudaStreamSynchronize(s));   // so / ro are host temporaries
+        m->geo_src.assign(a->src, a->src + nsrc);
+        m->geo_rec.assign(a->rec, a->rec + nrec3);
+        m->geo_shots = ns;
+        m->geo_nrec = nr;
+    }
+    return FWI_OK;
+}
+
+StepParams base_params(const fwi_model *m)
+{
+    StepParams p{};
+    p.g = m->g;
+    p.c = m->co;
+    p.W = m->W.as<float>();
+    p.sig_z = sig_z(m);
+    p.sig_y = sig_y(m);
+    p.sig_x = sig_x(m);
+    p.nt = m->nt;
+    p.dt2 = m->dt * m->dt;
+    return p;
+}
+
+// One time-step launch (kind 0: forward, 1: reverse); bracketed by CUDA events on the
+// launching stream when timing is on.
+int step_launch(fwi_model *m, const StepParams &p, int ns, bool img, int kind, cudaStream_t s)
+{
+    ++m->launches;
+    if (!m->opts.timing) {
+        FWI_CU(launch_step(p, ns, img, s));
+        return FWI_OK;
+    }
+    if (m->ev_used + 2 > m->ev.size()) {
+        for (int i = 0; i < 256; ++i) {
+            cudaEvent_t e;
+            FWI_CU(cudaEventCreate(&e));
+            m->ev.push_back(e);
+        }
+    }
+    FWI_CU(cudaEventRecord(m->ev[m->ev_used], s));
+    FWI_CU(launch_step(p, ns, img, s));
+    FWI_CU(cudaEventRecord(m->ev[m->ev_used + 1], s));
+    m->ev_used += 2;
+    m->ev_kind.push_back(kind);
+    return FWI_OK;
+}
+
+// Waits for the recorded events and adds their durations to the model's totals.
+int collect_timing(fwi_model *m)
+{
+    if (!m->opts.timing || m->ev_used == 0) return FWI_OK;
+    FWI_CU(cudaEventSynchronize(m->ev[m->ev_used - 1]));
+    for (size_t i = 0; i < m->ev_kind.size(); ++i) {
+        float ms = 0.0f;
+        FWI_CU(cudaEventElapsedTime(&ms, m->ev[2 * i], m->ev[2 * i + 1]));
+        if (m->ev_kind[i] == 0) {
+            m->t_fwd_ms += ms;
+            ++m->t_fwd_n;
+        } else {
+            m->t_adj_ms += ms;
+            ++m->t_adj_n;
+        }
+    }
+    m->ev_used = 0;
+    m->ev_kind.clear();
+    return FWI_OK;
+}
+
+int set_coefs(fwi_model *m)
+{
+    double c[kMaxM + 1];
+    FWI_TRY(host_coeffs(m->M, c));
+    const double iz = 1.0 / ((double)m->h[0] * m->h[0]);
+    const double iy = m->ndim == 3 ? 1.0 / ((double)m->h[1] * m->h[1]) : 0.0;
+    const double ix = 1.0 / ((double)m->h[2] * m->h[2]);
+    for (int k = 0; k <= kMaxM; ++k) {
+        const double ck = k <= m->M ? c[k] : 0.0;
+        m->co.cz[k] = (float)(ck * iz);
+        m->co.cy[k] = (float)(ck * iy);
+        m->co.cx[k] = (float)(ck * ix);
+    }
+    m->co.c0 = (float)(c[0] * (iz + iy + ix));
+    return FWI_OK;
+}
+
+// Forward sweep of nt steps from rest; traces to `tr` (device), or skipped when null.
+// On return u[cur] holds u^nt and u[1-cur] holds u^{nt-1}.
+int run_forward(fwi_model *m, int ns, int nr, const float *wav, float *tr, int *cur_out,
+                cudaStream_t s)
+{
+    const size_t fb = (size_t)m->g.field * sizeof(float);
+    FWI_CU(cudaMemsetAsync(m->u[0].p, 0, ns * fb, s));
+    FWI_CU(cudaMemsetAsync(m->u[1].p, 0, ns * fb, s));
+    StepParams p = base_params(m);
+    p.src_off = m->src_off.as<int64_t>();
+    p.wavelet = wav;
+    int cur = 0;
+    for (int n = 0; n < m->nt; ++n) {
+        p.cur = m->u[cur].as<float>();
+        p.prev = m->u[1 - cur].as<float>();
+        p.n = n;
+        FWI_TRY(step_launch(m, p, ns, false, 0, s));
+        if (tr)
+            FWI_LAUNCH(m, launch_sample(m->g, p.prev, m->rec_off.as<int64_t>(), ns, nr, m->nt, n, tr, s));
+        cur = 1 - cur;
+    }
+    *cur_out = cur;
+    return FWI_OK;
+}
+
+int finish_output(void *user, const void *dev, size_t bytes, bool host, cudaStream_t s)
+{
+    if (!user || !host) return FWI_OK;
+    FWI_CU(cudaMemcpyAsync(user, dev, bytes, cudaMemcpyDeviceToHost, s));
+    return FWI_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+const char *fwi_last_error(void) { return g_err.c_str(); }
+
+int fwi_fd_coeffs(int32_t order, double *c)
+{
+    if (!c || order % 2 || order < 2 || order > 2 * kMaxM)
+        return fail(FWI_ERR_ARG, "order must be even, 2..16");
+    return host_coeffs(order / 2, c);
+}
+
+double fwi_cfl_number(int32_t ndim, int32_t order, const float spacing[3], float vmax, float dt)
+{
+    if ((ndim != 2 && ndim != 3) || order % 2 || order < 2 || order > 2 * kMaxM || !spacing)
+        return -1.0;
+    return host_cfl(ndim, order / 2, spacing, vmax, dt);
+}
+
+int fwi_revolve_schedule(int32_t nsteps, int32_t nslots, int32_t *actions,
+                         int64_t max_actions, int64_t *n_actions, int64_t *n_forward)
+{
+    if (nsteps < 1 || nslots < 0) return fail(FWI_ERR_ARG, "nsteps >= 1 and nslots >= 0");
+    int64_t fwd = 0;
+    std::vector<int32_t> a = revolve_actions(nsteps, nslots, &fwd);
+    const int64_t na = (int64_t)a.size() / 2;
+    if (n_actions) *n_actions = na;
+    if (n_forward) *n_forward = fwd;
+    if (!actions) return FWI_OK;
+    if (na > max_actions) return fail(FWI_ERR_ARG, "max_actions too small");
+    std::memcpy(actions, a.data(), a.size() * sizeof(int32_t));
+    return FWI_OK;
+}
+
+int fwi_create_model(fwi_model **out, int32_t ndim, const int64_t shape[3],
+                     const float spacing[3], const float *vp, float dt, int32_t nt,
+                     const fwi_opts *opts, cudaStream_t stream)
+{
+    if (!out || !shape || !spacing || !vp) return fail(FWI_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (ndim != 2 && ndim != 3) return fail(FWI_ERR_ARG, "ndim must be 2 or 3");
+    if (shape[0] < 1 || shape[1] < 1 || shape[2] < 1 || (ndim == 2 && shape[1] != 1))
+        return fail(FWI_ERR_ARG, "shape must be positive (ny = 1 in 2-D)");
+    if (!(dt > 0.0f) || nt < 1) return fail(FWI_ERR_ARG, "dt > 0 and nt >= 1 required");
+    for (int a = 0; a < 3; ++a)
+        if ((a != 1 || ndim == 3) && !(spacing[a] > 0.0f))
+            return fail(FWI_ERR_ARG, "spacing must be positive");
+    fwi_opts o{};
+    if (opts) o = *opts;
+    if (o.order == 0) o.order = 8;
+    if (o.order != 8 && o.order != 16) return fail(FWI_ERR_ARG, "order must be 8 or 16");
+    if (o.nb == 0) o.nb = 20;
+    if (o.nb < 0) o.nb = 0;
+    if (o.snap_dtype < 0 || o.snap_dtype > 2) return fail(FWI_ERR_ARG, "bad snap_dtype");
+    if (o.fold_every <= 0) o.fold_every = 64;
+    if (!(o.sponge_r0 > 0.0f)) o.sponge_r0 = 1e-3f;
+    if (o.sponge_r0 >= 1.0f) return fail(FWI_ERR_ARG, "sponge_r0 must be in (0, 1)");
+
+    fwi_model *m = new fwi_model();
+    m->ndim = ndim;
+    m->order = o.order;
+    m->M = o.order / 2;
+    m->nb = o.nb;
+    m->nt = nt;
+    m->dt = dt;
+    m->opts = o;
+    for (int a = 0; a < 3; ++a) {
+        m->np[a] = shape[a];
+        m->h[a] = (a == 1 && ndim == 2) ? 1.0f : spacing[a];
+    }
+    Geom &g = m->g;
+    g.ndim = ndim;
+    g.M = m->M;
+    const int64_t nz = shape[0] + 2 * o.nb, ny = ndim == 3 ? shape[1] + 2 * o.nb : 1,
+                  nx = shape[2] + 2 * o.nb;
+    if (nz > (1 << 30) || ny > (1 << 30) || nx > (1 << 30)) {
+        delete m;
+        return fail(FWI_ERR_ARG, "grid too large");
+    }
+    g.nz = (int)nz;
+    g.ny = (int)ny;
+    g.nx = (int)nx;
+    g.px = (int)round_up(nx, 4);
+    g.plane = (int64_t)g.ny * g.px;
+    g.field = round_up((int64_t)g.nz * g.plane, 64);
+    int rc = set_coefs(m);
+    if (rc == FWI_OK) {
+        cudaError_t e = cudaHostAlloc((void **)&m->h_flag, sizeof(unsigned), cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&m->d_flag, m->h_flag, 0);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(FWI_ERR_CUDA, std::string("status word: ") + cudaGetErrorString(e));
+        } else {
+            *m->h_flag = 0;
+        }
+    }
+    if (rc == FWI_OK) rc = set_velocity(m, vp, stream);
+    if (rc != FWI_OK) {
+        std::string msg = g_err;
+        fwi_destroy(m);
+        g_err = msg;
+        return rc;
+    }
+    m->last_stream = stream;
+    *out = m;
+    return FWI_OK;
+}
+
+int fwi_update_velocity(fwi_model *m, const float *vp, cudaStream_t stream)
+{
+    if (!m || !vp) return fail(FWI_ERR_ARG, "null argument");
+    m->last_stream = stream;
+    return set_velocity(m, vp, stream);
+}
+
+int fwi_forward(fwi_model *m, const fwi_acq *acq, const float *wavelets, float *traces,
+                float *final_state, cudaStream_t s)
+{
+    if (!m || !wavelets) return fail(FWI_ERR_ARG, "null argument");
+    FWI_TRY(check_status(m));
+    FWI_TRY(validate_acq(m, acq));
+    m->last_stream = s;
+    const int ns = acq->nshots, nr = acq->nrec;
+    FWI_TRY(ensure_workspace(m, acq, false, s));
+    const void *wav;
+    FWI_TRY(stage_input(m, 0, wavelets, (size_t)ns * m->nt * sizeof(float), s, &wav));
+    void *trdev = nullptr;
+    bool trhost = false;
+    const size_t trbytes = (size_t)ns * m->nt * nr * sizeof(float);
+    if (traces) FWI_TRY(output_target(m, 0, traces, trbytes, &trdev, &trhost));
+    int cur = 0;
+    FWI_TRY(run_forward(m, ns, nr, (const float *)wav, (float *)trdev, &cur, s));
+    FWI_LAUNCH(m, launch_nonfinite_check(m->u[cur].as<float>(), (int64_t)ns * m->g.field, m->d_flag, s));
+    bool sync = trhost;
+    if (final_state) {
+        const bool fhost = !is_device_ptr(final_state);
+        const int64_t pts = (int64_t)m->g.nz * m->g.ny * m->g.nx;
+        for (int sh = 0; sh < ns; ++sh)
+            for (int k = 0; k < 2; ++k) {
+                const float *srcp = m->u[k == 0 ? cur : 1 - cur].as<float>() + (int64_t)sh * m->g.field;
+                float *dst = final_state + ((int64_t)sh * 2 + k) * pts;
+                FWI_CU(cudaMemcpy2DAsync(dst, m->g.nx * sizeof(float), srcp, m->g.px * sizeof(float),
+                                         m->g.nx * sizeof(float), (size_t)m->g.nz * m->g.ny,
+                                         fhost ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+            }
+        sync = sync || fhost;
+    }
+    FWI_TRY(finish_output(traces, trdev, trbytes, trhost, s));
+    if (sync) {
+        FWI_CU(cudaStreamSynchronize(s));
+        FWI_TRY(check_status(m));
+    }
+    FWI_TRY(collect_timing(m));
+    return FWI_OK;
+}
+
+int fwi_adjoint_gradient(fwi_model *m, const fwi_acq *acq, const float *wavelets,
+                         const float *d_obs, double *misfit, float *grad, double *grad64,
+                         cudaStream_t s)
+{
+    if (!m || !wavelets || !d_obs) return fail(FWI_ERR_ARG, "null argument");
+    FWI_TRY(check_status(m));
+    FWI_TRY(validate_acq(m, acq));
+    m->last_stream = s;
+    const int ns = acq->nshots, nr = acq->nrec, nt = m->nt;
+    FWI_TRY(ensure_workspace(m, acq, true, s));
+    const Geom &g = m->g;
+    const int64_t nfield = (int64_t)ns * g.field;
+    const size_t fb = (size_t)g.field * sizeof(float);
+
+    // checkpoint slots: as many as the budget holds, never more than nt
+    const int esz = m->opts.snap_dtype == FWI_SNAP_FP32 ? 4 : 2;
+    const size_t per_slot = (size_t)ns * 2 * g.field * esz;
+    int64_t budget = m->opts.snap_budget_bytes;
+    if (budget <= 0) {
+        size_t fr = 0, tot = 0;
+        FWI_CU(cudaMemGetInfo(&fr, &tot));
+        budget = (int64_t)(fr / 4);
+    }
+    int64_t slots = budget / (int64_t)per_slot;
+    if (slots > nt) slots = nt;
+    if (slots < 0) slots = 0;
+    if ((size_t)slots * per_slot > m->snaps.bytes) {
+        // shrink on failure rather than fail: fewer slots only cost recomputation
+        while (slots > 0 && m->snaps.ensure((size_t)slots * per_slot) != FWI_OK) slots /= 2;
+    }
+    FWI_TRY(m->scales.ensure((size_t)(slots > 0 ? slots : 1) * ns * sizeof(float)));
+    if (slots != m->sched_nslots) {
+        m->sched = revolve_actions(nt, (int32_t)slots, &m->sched_fwd);
+        m->sched_nslots = (int)slots;
+    }
+    m->nslots = (int)slots;
+    m->slot_bytes = per_slot;
+
+    const void *wav, *dobs;
+    FWI_TRY(stage_input(m, 0, wavelets, (size_t)ns * nt * sizeof(float), s, &wav));
+    FWI_TRY(stage_input(m, 1, d_obs, (size_t)ns * nt * nr * sizeof(float), s, &dobs));
+
+    // adjoint receiver injection factor 2 W / a+ (the adjoint source is 2 r for Eq. 1)
+    FWI_LAUNCH(m, launch_rec_scale(g, m->W.as<float>(), sig_z(m), sig_y(m), sig_x(m),
+                            m->rec_off.as<int64_t>(), ns * nr, 2.0f, 0, m->inj.as<float>(), s));
+    FWI_CU(cudaMemsetAsync(m->u[0].p, 0, ns * fb, s));
+    FWI_CU(cudaMemsetAsync(m->u[1].p, 0, ns * fb, s));
+    FWI_CU(cudaMemsetAsync(m->g32.p, 0, ns * fb, s));
+    FWI_CU(cudaMemsetAsync(m->g64.p, 0, ns * 2 * fb, s));
+
+    StepParams pf = base_params(m);
+    pf.src_off = m->src_off.as<int64_t>();
+    pf.wavelet = (const float *)wav;
+    StepParams pa = base_params(m);   // reverse sweep: no source, receivers injected after
+    float *tr = m->traces.as<float>();
+    float *res = tr;                  // residuals replace the traces in place
+    int cur = 0, mcur = 0;
+    int64_t step = 0, recorded = 0;
+    std::vector<int64_t> slot_step(slots > 0 ? slots : 1, -1);
+    bool first_adj = true;
+    int64_t nadj = 0, nfwd = 0, nstore = 0, nrestore = 0;
+    const char *codes = m->snaps.as<char>();
+
+    for (size_t i = 0; i + 1 < m->sched.size(); i += 2) {
+        const int kind = m->sched[i], arg = m->sched[i + 1];
+        if (kind == 1) {   // ADVANCE
+            for (int k = 0; k < arg; ++k) {
+                pf.cur = m->u[cur].as<float>();
+                pf.prev = m->u[1 - cur].as<float>();
+                pf.n = (int)step;
+                FWI_TRY(step_launch(m, pf, ns, false, 0, s));
+                if (step >= recorded) {
+                    FWI_LAUNCH(m, launch_sample(g, pf.prev, m->rec_off.as<int64_t>(), ns, nr, nt,
+                                         (int)step, tr, s));
+                    recorded = step + 1;
+                }
+                cur = 1 - cur;
+                ++step;
+                ++nfwd;
+            }
+        } else if (kind == 2) {   // STORE the pair (u^step, u^{step-1})
+            FWI_CU(cudaMemsetAsync(m->maxbits.p, 0, ns * sizeof(unsigned), s));
+            FWI_LAUNCH(m, launch_maxabs(m->u[cur].as<float>(), m->u[1 - cur].as<float>(), g.field,
+                                 g.field, ns, m->maxbits.as<unsigned>(), s));
+            FWI_LAUNCH(m, launch_encode(m->u[cur].as<float>(), m->u[1 - cur].as<float>(), g.field,
+                                 g.field, ns, m->opts.snap_dtype, m->maxbits.as<unsigned>(),
+                                 (void *)(codes + (size_t)arg * per_slot), 2 * g.field,
+                                 m->scales.as<float>() + (size_t)arg * ns, m->d_flag, s));
+            slot_step[arg] = step;
+            ++nstore;
+        } else if (kind == 3) {   // RESTORE
+            if (arg < 0) {
+                FWI_CU(cudaMemsetAsync(m->u[0].p, 0, ns * fb, s));
+                FWI_CU(cudaMemsetAsync(m->u[1].p, 0, ns * fb, s));
+                cur = 0;
+                step = 0;
+            } else {
+                FWI_LAUNCH(m, launch_decode(codes + (size_t)arg * per_slot, 2 * g.field,
+                                     m->scales.as<float>() + (size_t)arg * ns, g.field, g.field,
+                                     ns, m->opts.snap_dtype, m->u[cur].as<float>(),
+                                     m->u[1 - cur].as<float>(), s));
+                step = slot_step[arg];
+            }
+            ++nrestore;
+        } else if (kind == 4) {   // ADJOINT step m = arg, needs u^m = u[cur]
+            const int mm = arg;
+            if (step != mm) return fail(FWI_ERR_CUDA, "internal: checkpoint schedule out of step");
+            if (first_adj) {
+                ++m->launches;   // the misfit is two launches
+                FWI_LAUNCH(m, launch_misfit(tr, (const float *)dobs, res, (int64_t)ns * nt * nr,
+                                     m->partials.as<double>(), misfit_blocks((int64_t)ns * nt * nr),
+                                     m->phi.as<double>(), m->d_flag, s));
+                FWI_CU(cudaMemsetAsync(m->mu[0].p, 0, ns * fb, s));
+                FWI_CU(cudaMemsetAsync(m->mu[1].p, 0, ns * fb, s));
+                first_adj = false;
+            }
+            pa.cur = m->mu[mcur].as<float>();        // mu^{m+1}
+            pa.prev = m->mu[1 - mcur].as<float>();   // mu^{m+2} -> mu^m
+            const bool img = mm < nt;                // mu^{nt+1} = 0: no imaging at m = nt
+            pa.u_img = m->u[cur].as<float>();
+            pa.gacc = m->g32.as<float>();
+            FWI_TRY(step_launch(m, pa, ns, img, 1, s));
+            FWI_LAUNCH(m, launch_inject(g, pa.prev, m->rec_off.as<int64_t>(), m->inj.as<float>(), res,
+                                 ns, nr, nt, mm - 1, s));
+            mcur = 1 - mcur;
+            ++nadj;
+            if (nadj % m->opts.fold_every == 0)
+                FWI_LAUNCH(m, launch_fold(m->g32.as<float>(), m->g64.as<double>(), nfield, s));
+        }
+    }
+    FWI_LAUNCH(m, launch_fold(m->g32.as<float>(), m->g64.as<double>(), nfield, s));
+
+    const int64_t nphys = m->np[0] * m->np[1] * m->np[2];
+    void *g32dev = nullptr, *g64dev = nullptr;
+    bool g32host = false, g64host = false;
+    if (grad) FWI_TRY(output_target(m, 0, grad, nphys * sizeof(float), &g32dev, &g32host));
+    if (grad64) FWI_TRY(output_target(m, 1, grad64, nphys * sizeof(double), &g64dev, &g64host));
+    FWI_LAUNCH(m, launch_finish(g, m->nb, m->np, ns, m->g64.as<double>(), m->v.as<float>(),
+                         (float *)g32dev, (double *)g64dev, s));
+    FWI_TRY(finish_output(grad, g32dev, nphys * sizeof(float), g32host, s));
+    FWI_TRY(finish_output(grad64, g64dev, nphys * sizeof(double), g64host, s));
+    bool sync = g32host || g64host;
+    if (misfit) {
+        const bool mh = !is_device_ptr(misfit);
+        FWI_CU(cudaMemcpyAsync(misfit, m->phi.p, sizeof(double),
+                               mh ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+        sync = sync || mh;
+    }
+    m->st_fwd = nfwd;
+    m->st_adj = nadj;
+    m->st_store = nstore;
+    m->st_restore = nrestore;
+    if (sync) {
+        FWI_CU(cudaStreamSynchronize(s));
+        FWI_TRY(check_status(m));
+    }
+    FWI_TRY(collect_timing(m));
+    return FWI_OK;
+}
+
+int fwi_source_adjoint(fwi_model *m, const fwi_acq *acq, const float *y, float *x,
+                       cudaStream_t s)
+{
+    if (!m || !y || !x) return fail(FWI_ERR_ARG, "null argument");
+    FWI_TRY(check_status(m));
+    FWI_TRY(validate_acq(m, acq));
+    m->last_stream = s;
+    const int ns = acq->nshots, nr = acq->nrec, nt = m->nt;
+    FWI_TRY(ensure_workspace(m, acq, true, s));
+    const Geom &g = m->g;
+    const size_t fb = (size_t)g.field * sizeof(float);
+    const void *ydev;
+    FWI_TRY(stage_input(m, 0, y, (size_t)ns * nt * nr * sizeof(float), s, &ydev));
+    void *xdev;
+    bool xhost;
+    FWI_TRY(output_target(m, 0, x, (size_t)ns * nt * sizeof(float), &xdev, &xhost));
+    // injection W y / a+ at the receivers; read-out dt^2 mu / W at the source
+    FWI_LAUNCH(m, launch_rec_scale(g, m->W.as<float>(), sig_z(m), sig_y(m), sig_x(m),
+                            m->rec_off.as<int64_t>(), ns * nr, 1.0f, 0, m->inj.as<float>(), s));
+    FWI_LAUNCH(m, launch_rec_scale(g, m->W.as<float>(), sig_z(m), sig_y(m), sig_x(m),
+                            m->src_off.as<int64_t>(), ns, m->dt * m->dt, 1,
+                            m->src_scale.as<float>(), s));
+    FWI_CU(cudaMemsetAsync(m->mu[0].p, 0, ns * fb, s));
+    FWI_CU(cudaMemsetAsync(m->mu[1].p, 0, ns * fb, s));
+    StepParams pa = base_params(m);
+    int mcur = 0;
+    for (int mm = nt; mm >= 1; --mm) {
+        pa.cur = m->mu[mcur].as<float>();
+        pa.prev = m->mu[1 - mcur].as<float>();
+        FWI_TRY(step_launch(m, pa, ns, false, 1, s));
+        FWI_LAUNCH(m, launch_inject(g, pa.prev, m->rec_off.as<int64_t>(), m->inj.as<float>(),
+                             (const float *)ydev, ns, nr, nt, mm - 1, s));
+        FWI_LAUNCH(m, launch_gather_src(g, pa.prev, m->src_off.as<int64_t>(), m->src_scale.as<float>(),
+                                 ns, nt, mm - 1, (float *)xdev, s));
+        mcur = 1 - mcur;
+    }
+    FWI_TRY(finish_output(x, xdev, (size_t)ns * nt * sizeof(float), xhost, s));
+    if (xhost) FWI_CU(cudaStreamSynchronize(s));
+    FWI_TRY(collect_timing(m));
+    return FWI_OK;
+}
+
+int fwi_misfit(const float *d_mod, const float *d_obs, int64_t n, double *misfit_dev,
+               cudaStream_t s)
+{
+    if (!d_mod || !d_obs || !misfit_dev || n < 0) return fail(FWI_ERR_ARG, "bad argument");
+    const int nb = misfit_blocks(n);
+    double *part = nullptr;
+    FWI_CU(cudaMallocAsync((void **)&part, nb * sizeof(double), s));
+    cudaError_t e = launch_misfit(d_mod, d_obs, nullptr, n, part, nb, misfit_dev, nullptr, s);
+    cudaError_t e2 = cudaFreeAsync(part, s);
+    if (e != cudaSuccess) return fail(FWI_ERR_CUDA, std::string("misfit: ") + cudaGetErrorString(e));
+    if (e2 != cudaSuccess) return fail(FWI_ERR_CUDA, std::string("misfit free: ") + cudaGetErrorString(e2));
+    return FWI_OK;
+}
+
+int fwi_snapshot_encode(const float *a, const float *b, int64_t n, int32_t dtype, void *code,
+                        float *scale, cudaStream_t s)
+{
+    if (!a || !b || !code || !scale || n < 0 || dtype < 0 || dtype > 2)
+        return fail(FWI_ERR_ARG, "bad argument");
+    unsigned *mb = nullptr;
+    FWI_CU(cudaMallocAsync((void **)&mb, sizeof(unsigned), s));
+    FWI_CU(cudaMemsetAsync(mb, 0, sizeof(unsigned), s));
+    cudaError_t e = launch_maxabs(a, b, n, n, 1, mb, s);
+    if (e == cudaSuccess) e = launch_encode(a, b, n, n, 1, dtype, mb, code, 2 * n, scale, nullptr, s);
+    cudaError_t e2 = cudaFreeAsync(mb, s);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail(FWI_ERR_CUDA, std::string("encode: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return FWI_OK;
+}
+
+int fwi_snapshot_decode(const void *code, const float *scale, int64_t n, int32_t dtype, float *a,
+                        float *b, cudaStream_t s)
+{
+    if (!a || !b || !code || !scale || n < 0 || dtype < 0 || dtype > 2)
+        return fail(FWI_ERR_ARG, "bad argument");
+    FWI_CU(launch_decode(code, 2 * n, scale, n, n, 1, dtype, a, b, s));
+    return FWI_OK;
+}
+
+int fwi_model_info(const fwi_model *m, fwi_info *o)
+{
+    if (!m || !o) return fail(FWI_ERR_ARG, "null argument");
+    std::memset(o, 0, sizeof(*o));
+    o->ndim = m->ndim;
+    o->order = m->order;
+    o->nb = m->nb;
+    o->nt = m->nt;
+    for (int a = 0; a < 3; ++a) o->shape[a] = m->np[a];
+    o->computed[0] = m->g.nz;
+    o->computed[1] = m->g.ny;
+    o->computed[2] = m->g.nx;
+    o->pitch_x = m->g.px;
+    o->points = (int64_t)m->g.nz * m->g.ny * m->g.nx;
+    o->device_bytes = m->device_bytes();
+    o->snap_slots = m->nslots;
+    o->shots_capacity = m->cap_shots;
+    o->last_forward_steps = m->st_fwd;
+    o->last_adjoint_steps = m->st_adj;
+    o->last_snap_stores = m->st_store;
+    o->last_snap_restores = m->st_restore;
+    for (int a = 0; a < 3; ++a) o->sponge_eta_max[a] = m->eta_max[a];
+    o->cfl = m->cfl;
+    o->kernel_launches = m->launches;
+    o->fwd_step_launches = m->t_fwd_n;
+    o->adj_step_launches = m->t_adj_n;
+    o->fwd_step_ms = m->t_fwd_ms;
+    o->adj_step_ms = m->t_adj_ms;
+    return FWI_OK;
+}
+
+int fwi_sync_status(fwi_model *m)
+{
+    if (!m) return fail(FWI_ERR_ARG, "null argument");
+    FWI_CU(cudaStreamSynchronize(m->last_stream));
+    return check_status(m);
+}
+
+void fwi_destroy(fwi_model *m)
+{
+    if (!m) return;
+    if (m->last_stream) cudaStreamSynchronize(m->last_stream);
+    m->v.release();
+    m->W.release();
+    m->sig.release();
+    for (int i = 0; i < 2; ++i) {
+        m->u[i].release();
+        m->mu[i].release();
+        m->stage_out[i].release();
+    }
+    for (int i = 0; i < 3; ++i) m->stage_in[i].release();
+    m->g32.release();
+    m->g64.release();
+    m->traces.release();
+    m->src_off.release();
+    m->rec_off.release();
+    m->inj.release();
+    m->src_scale.release();
+    m->maxbits.release();
+    m->partials.release();
+    m->phi.release();
+    m->snaps.release();
+    m->scales.release();
+    if (m->h_flag) cudaFreeHost(m->h_flag);
+    for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
+    delete m;
+}
+
+}  // extern "C"

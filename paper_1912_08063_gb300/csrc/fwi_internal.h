@@ -1,0 +1,95 @@
+// Internal types shared by the CUDA kernels and the host executor of libfwi.
+// Nothing here is part of the C ABI (include/fwi.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fwi {
+
+constexpr int kMaxM = 8;   // stencil radius of the 16th-order Laplacian
+
+// Device layout of one shot's field on the computed grid (sponge included):
+// C-order [nz][ny][px] FP32, rows padded to px floats (a multiple of 4, so every row
+// starts on a 16-byte boundary), shots `field` floats apart (a multiple of 64).
+// Columns nx..px-1 are zero and never written.
+struct Geom {
+    int ndim;       // 2 or 3
+    int M;          // stencil radius
+    int nz, ny, nx; // computed extents (ny = 1 in 2-D)
+    int px;         // row pitch in floats
+    int64_t plane;  // ny * px
+    int64_t field;  // floats per shot
+};
+
+// Second-derivative weights c_k / h_a^2 per axis, k = 0..M, and the combined centre
+// weight c_0 * sum_a 1/h_a^2.
+struct Coefs {
+    float cz[kMaxM + 1];
+    float cy[kMaxM + 1];
+    float cx[kMaxM + 1];
+    float c0;
+};
+
+// One time step of the damped leapfrog on every shot of a batch:
+//   out = (2 cur + W (L cur) - (1 - s) prev + [dt^2 w[n] at the source]) / (1 + s),
+//   s = sig_z[z] + sig_y[y] + sig_x[x]  (= eta dt / 2),
+// written over `prev`.  With `u_img`/`gacc` set (imaging), additionally
+//   gacc += cur * (L u_img)
+// for the zero-lag imaging condition of the reverse sweep.
+struct StepParams {
+    Geom g;
+    Coefs c;
+    const float *cur;
+    float *prev;
+    const float *W;
+    const float *sig_z, *sig_y, *sig_x;
+    const int64_t *src_off;   // [nshots] offsets within a shot's field, or nullptr
+    const float *wavelet;     // [nshots][nt]
+    int nt, n;
+    float dt2;
+    const float *u_img;       // imaging only
+    float *gacc;              // imaging only: gradient accumulator
+    int zchunk;               // planes per CTA along z
+    int nzchunks;
+};
+
+cudaError_t launch_step(const StepParams &p, int nshots, bool imaging, cudaStream_t s);
+
+// ---- auxiliary kernels (k_aux.cu) ----
+cudaError_t launch_build_W(const Geom &g, int nb, const int64_t np[3], const float *v,
+                           float dt, float *W, cudaStream_t s);
+cudaError_t launch_sample(const Geom &g, const float *field, const int64_t *rec_off,
+                          int nshots, int nrec, int nt, int n, float *traces,
+                          cudaStream_t s);
+cudaError_t launch_inject(const Geom &g, float *field, const int64_t *rec_off,
+                          const float *scale, const float *q, int nshots, int nrec, int nt,
+                          int sample, cudaStream_t s);
+cudaError_t launch_gather_src(const Geom &g, const float *field, const int64_t *src_off,
+                              const float *src_scale, int nshots, int nt, int sample,
+                              float *x, cudaStream_t s);
+cudaError_t launch_rec_scale(const Geom &g, const float *W, const float *sig_z,
+                             const float *sig_y, const float *sig_x, const int64_t *off,
+                             int count, float factor, int mode, float *out, cudaStream_t s);
+// residual r = d - d_obs in place of d (when store_r) and block partials of sum r^2
+// (flag, when given, is raised if the sum is not finite)
+cudaError_t launch_misfit(const float *d, const float *dobs, float *r_out, int64_t n,
+                          double *partials, int nblocks, double *result, unsigned *flag,
+                          cudaStream_t s);
+int misfit_blocks(int64_t n);
+cudaError_t launch_maxabs(const float *a, const float *b, int64_t n, int64_t stride,
+                          int nshots, unsigned *maxbits, cudaStream_t s);
+cudaError_t launch_encode(const float *a, const float *b, int64_t n, int64_t stride,
+                          int nshots, int dtype, const unsigned *maxbits, void *code,
+                          int64_t code_stride, float *scale, unsigned *flag, cudaStream_t s);
+cudaError_t launch_decode(const void *code, int64_t code_stride, const float *scale,
+                          int64_t n, int64_t stride, int nshots, int dtype, float *a, float *b,
+                          cudaStream_t s);
+cudaError_t launch_fold(float *g32, double *g64, int64_t n, cudaStream_t s);
+cudaError_t launch_finish(const Geom &g, int nb, const int64_t np[3], int nshots,
+                          const double *g64, const float *v, float *grad32, double *grad64,
+                          cudaStream_t s);
+cudaError_t launch_nonfinite_check(const float *a, int64_t n, unsigned *flag,
+                                   cudaStream_t s);
+
+}  // namespace fwi

@@ -1,0 +1,403 @@
+// Auxiliary kernels of the FWI hot path: model set-up (W = v^2 dt^2 on the padded grid),
+// receiver sampling and adjoint injection, the FP64 misfit reduction (Eq. 1), the
+// checkpoint codec (BF16/FP16 with a per-checkpoint power-of-two scale), the FP32 -> FP64
+// gradient fold and the gradient finish (dW/dv and the fold of sponge cells).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "fwi_internal.h"
+
+namespace fwi {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+int blocks_for(int64_t n, int cap = 148 * 16)
+{
+    int64_t b = (n + kThreads - 1) / kThreads;
+    if (b < 1) b = 1;
+    return (int)(b > cap ? cap : b);
+}
+
+// ---------------------------------------------------------------- set-up
+
+// W[c] = (v[clamp(c - nb)] dt)^2 on the computed grid, zero in the row padding.
+__global__ void k_build_W(Geom g, int nb, int64_t npz, int64_t npy, int64_t npx,
+                          const float *__restrict__ v, double dt, float *__restrict__ W)
+{
+    const int64_t total = (int64_t)g.nz * g.plane;
+    const int nby = (g.ndim == 3) ? nb : 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t z = i / g.plane, r = i - z * g.plane;
+        const int64_t y = r / g.px, x = r - y * g.px;
+        float w = 0.0f;
+        if (x < g.nx) {
+            int64_t pz = min(max(z - nb, (int64_t)0), npz - 1);
+            int64_t py = min(max(y - nby, (int64_t)0), npy - 1);
+            int64_t pxx = min(max(x - nb, (int64_t)0), npx - 1);
+            double vv = v[(pz * npy + py) * npx + pxx];
+            w = (float)(vv * vv * dt * dt);
+        }
+        W[i] = w;
+    }
+}
+
+// out[i] = factor * W / (1 + s)  (mode 0: adjoint receiver injection of W R^T q / a+)
+// out[i] = factor / W            (mode 1: source read-out dt^2 mu / W)
+__global__ void k_rec_scale(Geom g, const float *__restrict__ W, const float *__restrict__ sz,
+                            const float *__restrict__ sy, const float *__restrict__ sx,
+                            const int64_t *__restrict__ off, int count, float factor, int mode,
+                            float *__restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int64_t o = off[i];
+    const int64_t z = o / g.plane, r = o - z * g.plane;
+    const int64_t y = r / g.px, x = r - y * g.px;
+    const float w = W[o];
+    if (mode == 0) {
+        const float s = sz[z] + sy[y] + sx[x];
+        out[i] = factor * w / (1.0f + s);
+    } else {
+        out[i] = factor / w;
+    }
+}
+
+// ---------------------------------------------------------------- receivers
+
+__global__ void k_sample(int64_t fs, const float *__restrict__ f, const int64_t *__restrict__ off,
+                         int nshots, int nrec, int nt, int n, float *__restrict__ traces)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nshots * nrec) return;
+    const int s = i / nrec, r = i - s * nrec;
+    traces[((int64_t)s * nt + n) * nrec + r] = f[(int64_t)s * fs + off[i]];
+}
+
+__global__ void k_inject(int64_t fs, float *__restrict__ f, const int64_t *__restrict__ off,
+                         const float *__restrict__ scale, const float *__restrict__ q,
+                         int nshots, int nrec, int nt, int sample)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nshots * nrec) return;
+    const int s = i / nrec, r = i - s * nrec;
+    atomicAdd(f + (int64_t)s * fs + off[i], scale[i] * q[((int64_t)s * nt + sample) * nrec + r]);
+}
+
+__global__ void k_gather_src(int64_t fs, const float *__restrict__ f,
+                             const int64_t *__restrict__ off, const float *__restrict__ sc,
+                             int nshots, int nt, int sample, float *__restrict__ x)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nshots) return;
+    x[(int64_t)s * nt + sample] = f[(int64_t)s * fs + off[s]] * sc[s];
+}
+
+// ---------------------------------------------------------------- misfit (Eq. 1)
+
+__device__ double block_sum(double v)
+{
+    __shared__ double part[kThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) part[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (wid == 0) {
+        t = lane < kThreads / 32 ? part[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    }
+    return t;  // valid in thread 0
+}
+
+// Fixed-order partial sums: thread t of block b adds samples b*T + t + k*(B*T), k = 0.. in
+// order, then a fixed tree.  The grid size depends only on n, so the result is
+// reproducible bit for bit.
+__global__ void k_misfit_partial(const float *__restrict__ d, const float *__restrict__ dobs,
+                                 float *__restrict__ r_out, int64_t n, double *__restrict__ part)
+{
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kThreads) {
+        const float r = d[i] - dobs[i];
+        if (r_out) r_out[i] = r;
+        acc += (double)r * (double)r;
+    }
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void k_sum_partials(const double *__restrict__ part, int nb, double *__restrict__ out,
+                               unsigned *flag)
+{
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += kThreads) acc += part[i];
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) {
+        out[0] = t;
+        if (flag && !isfinite(t)) atomicOr(flag, 1u);
+    }
+}
+
+// ---------------------------------------------------------------- checkpoint codec
+
+__device__ __forceinline__ unsigned absbits(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+
+__global__ void k_maxabs(const float *__restrict__ a, const float *__restrict__ b, int64_t n,
+                         int64_t stride, unsigned *__restrict__ out)
+{
+    const int s = blockIdx.y;
+    const float *pa = a + s * stride, *pb = b + s * stride;
+    unsigned m = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, max(absbits(pa[i]), absbits(pb[i])));
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out + s, m);
+}
+
+// s = 2^floor(log2(T / max)) with T = 2^texp, from the bit pattern of max (exact
+// integer arithmetic); NaN for a non-finite max, 1 for an all-zero pair.
+__device__ float snap_scale(unsigned mb, int dtype)
+{
+    if (dtype == 0 || mb == 0u) return 1.0f;
+    if (mb >= 0x7f800000u) return __int_as_float(0x7fc00000);
+    const int texp = (dtype == 2) ? 14 : 0;
+    const unsigned e = mb >> 23, mant = mb & 0x7fffffu;
+    int E;
+    bool frac;
+    if (e > 0) {
+        E = (int)e - 127;
+        frac = mant != 0u;
+    } else {
+        E = (31 - __clz((int)mant)) - 149;
+        frac = (mant & (mant - 1u)) != 0u;
+    }
+    int k = texp - E - (frac ? 1 : 0);
+    k = max(-126, min(127, k));
+    return __int_as_float((k + 127) << 23);
+}
+
+__global__ void k_encode(const float *__restrict__ a, const float *__restrict__ b, int64_t n,
+                         int64_t stride, int dtype, const unsigned *__restrict__ maxbits,
+                         void *__restrict__ code, int64_t cstride, float *__restrict__ scale,
+                         unsigned *flag)
+{
+    const int s = blockIdx.y;
+    const float sc = snap_scale(maxbits[s], dtype);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        scale[s] = sc;
+        if (flag && maxbits[s] >= 0x7f800000u) atomicOr(flag, 1u);
+    }
+    const float *pa = a + s * stride, *pb = b + s * stride;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float va = pa[i], vb = pb[i];
+        if (dtype == 0) {
+            float *c = (float *)code + s * cstride;
+            c[i] = va;
+            c[n + i] = vb;
+        } else if (dtype == 1) {
+            __nv_bfloat16 *c = (__nv_bfloat16 *)code + s * cstride;
+            c[i] = __float2bfloat16_rn(va * sc);
+            c[n + i] = __float2bfloat16_rn(vb * sc);
+        } else {
+            __half *c = (__half *)code + s * cstride;
+            c[i] = __float2half_rn(va * sc);
+            c[n + i] = __float2half_rn(vb * sc);
+        }
+    }
+}
+
+__global__ void k_decode(const void *__restrict__ code, int64_t cstride,
+                         const float *__restrict__ scale, int64_t n, int64_t stride, int dtype,
+                         float *__restrict__ a, float *__restrict__ b)
+{
+    const int s = blockIdx.y;
+    const float sc = scale[s];
+    float *pa = a + s * stride, *pb = b + s * stride;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (dtype == 0) {
+            const float *c = (const float *)code + s * cstride;
+            pa[i] = c[i];
+            pb[i] = c[n + i];
+        } else if (dtype == 1) {
+            const __nv_bfloat16 *c = (const __nv_bfloat16 *)code + s * cstride;
+            pa[i] = __bfloat162float(c[i]) / sc;
+            pb[i] = __bfloat162float(c[n + i]) / sc;
+        } else {
+            const __half *c = (const __half *)code + s * cstride;
+            pa[i] = __half2float(c[i]) / sc;
+            pb[i] = __half2float(c[n + i]) / sc;
+        }
+    }
+}
+
+__global__ void k_nonfinite(const float *__restrict__ a, int64_t n, unsigned *flag)
+{
+    unsigned bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        bad |= absbits(a[i]) >= 0x7f800000u;
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && bad) atomicOr(flag, 1u);
+}
+
+// ---------------------------------------------------------------- gradient
+
+__global__ void k_fold(float *__restrict__ g32, double *__restrict__ g64, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        g64[i] += (double)g32[i];
+        g32[i] = 0.0f;
+    }
+}
+
+// grad(p) = (2 / v(p)) * sum_shots sum_{computed cells c replicated from p} g_mu(c),
+// where g_mu = sum_m mu^{m+1} L u^m and mu = W nu (so dphi/dW = g_mu / W and
+// dphi/dv = 2 v dt^2 dphi/dW = 2 g_mu / v).
+__global__ void k_finish(Geom g, int nb, int64_t npz, int64_t npy, int64_t npx, int nshots,
+                         const double *__restrict__ g64, const float *__restrict__ v,
+                         float *__restrict__ grad32, double *__restrict__ grad64)
+{
+    const int64_t nphys = npz * npy * npx;
+    const int nby = (g.ndim == 3) ? nb : 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nphys;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pz = i / (npy * npx), r = i - pz * npy * npx;
+        const int64_t py = r / npx, pxx = r - py * npx;
+        const int64_t z0 = pz == 0 ? 0 : pz + nb, z1 = pz == npz - 1 ? pz + 2 * nb : pz + nb;
+        const int64_t y0 = py == 0 ? 0 : py + nby, y1 = py == npy - 1 ? py + 2 * nby : py + nby;
+        const int64_t x0 = pxx == 0 ? 0 : pxx + nb, x1 = pxx == npx - 1 ? pxx + 2 * nb : pxx + nb;
+        double acc = 0.0;
+        for (int s = 0; s < nshots; ++s) {
+            const double *gs = g64 + (int64_t)s * g.field;
+            for (int64_t cz = z0; cz <= z1; ++cz)
+                for (int64_t cy = y0; cy <= y1; ++cy)
+                    for (int64_t cx = x0; cx <= x1; ++cx)
+                        acc += gs[cz * g.plane + cy * g.px + cx];
+        }
+        const double out = acc * 2.0 / (double)v[i];
+        if (grad32) grad32[i] = (float)out;
+        if (grad64) grad64[i] = out;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+
+cudaError_t launch_build_W(const Geom &g, int nb, const int64_t np[3], const float *v,
+                           float dt, float *W, cudaStream_t s)
+{
+    k_build_W<<<blocks_for((int64_t)g.nz * g.plane), kThreads, 0, s>>>(g, nb, np[0], np[1],
+                                                                      np[2], v, dt, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample(const Geom &g, const float *field, const int64_t *rec_off,
+                          int nshots, int nrec, int nt, int n, float *traces, cudaStream_t s)
+{
+    int cnt = nshots * nrec;
+    k_sample<<<(cnt + kThreads - 1) / kThreads, kThreads, 0, s>>>(g.field, field, rec_off,
+                                                                 nshots, nrec, nt, n, traces);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject(const Geom &g, float *field, const int64_t *rec_off,
+                          const float *scale, const float *q, int nshots, int nrec, int nt,
+                          int sample, cudaStream_t s)
+{
+    int cnt = nshots * nrec;
+    k_inject<<<(cnt + kThreads - 1) / kThreads, kThreads, 0, s>>>(g.field, field, rec_off,
+                                                                 scale, q, nshots, nrec, nt,
+                                                                 sample);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_src(const Geom &g, const float *field, const int64_t *src_off,
+                              const float *src_scale, int nshots, int nt, int sample,
+                              float *x, cudaStream_t s)
+{
+    k_gather_src<<<(nshots + 63) / 64, 64, 0, s>>>(g.field, field, src_off, src_scale, nshots,
+                                                   nt, sample, x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rec_scale(const Geom &g, const float *W, const float *sig_z,
+                             const float *sig_y, const float *sig_x, const int64_t *off,
+                             int count, float factor, int mode, float *out, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    k_rec_scale<<<(count + kThreads - 1) / kThreads, kThreads, 0, s>>>(g, W, sig_z, sig_y,
+                                                                      sig_x, off, count,
+                                                                      factor, mode, out);
+    return cudaGetLastError();
+}
+
+int misfit_blocks(int64_t n) { return blocks_for(n, 1024); }
+
+cudaError_t launch_misfit(const float *d, const float *dobs, float *r_out, int64_t n,
+                          double *partials, int nblocks, double *result, unsigned *flag,
+                          cudaStream_t s)
+{
+    k_misfit_partial<<<nblocks, kThreads, 0, s>>>(d, dobs, r_out, n, partials);
+    k_sum_partials<<<1, kThreads, 0, s>>>(partials, nblocks, result, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_maxabs(const float *a, const float *b, int64_t n, int64_t stride,
+                          int nshots, unsigned *maxbits, cudaStream_t s)
+{
+    dim3 grid(blocks_for(n, 152 * 8), nshots);
+    k_maxabs<<<grid, kThreads, 0, s>>>(a, b, n, stride, maxbits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encode(const float *a, const float *b, int64_t n, int64_t stride,
+                          int nshots, int dtype, const unsigned *maxbits, void *code,
+                          int64_t code_stride, float *scale, unsigned *flag, cudaStream_t s)
+{
+    dim3 grid(blocks_for(n, 152 * 8), nshots);
+    k_encode<<<grid, kThreads, 0, s>>>(a, b, n, stride, dtype, maxbits, code, code_stride,
+                                       scale, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode(const void *code, int64_t code_stride, const float *scale,
+                          int64_t n, int64_t stride, int nshots, int dtype, float *a, float *b,
+                          cudaStream_t s)
+{
+    dim3 grid(blocks_for(n, 152 * 8), nshots);
+    k_decode<<<grid, kThreads, 0, s>>>(code, code_stride, scale, n, stride, dtype, a, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold(float *g32, double *g64, int64_t n, cudaStream_t s)
+{
+    k_fold<<<blocks_for(n, 152 * 8), kThreads, 0, s>>>(g32, g64, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const Geom &g, int nb, const int64_t np[3], int nshots,
+                          const double *g64, const float *v, float *grad32, double *grad64,
+                          cudaStream_t s)
+{
+    k_finish<<<blocks_for(np[0] * np[1] * np[2], 152 * 8), kThreads, 0, s>>>(
+        g, nb, np[0], np[1], np[2], nshots, g64, v, grad32, grad64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nonfinite_check(const float *a, int64_t n, unsigned *flag, cudaStream_t s)
+{
+    k_nonfinite<<<blocks_for(n, 152 * 4), kThreads, 0, s>>>(a, n, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace fwi

@@ -1,0 +1,255 @@
+"""GPU parity: the CUDA path (called through the C ABI) against the FP64 oracle on the
+same seeded inputs.  Bars: traces and final wavefields rel-L2 <= 1e-4; gradients
+rel-L2 <= 1e-3 with FP32 checkpoints and <= 1e-2 with BF16/FP16 checkpoints; codec
+bit-exact; misfit rel <= 1e-6."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_08063_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_FWD = 1e-4
+TOL_GRAD32 = 1e-3
+TOL_GRAD16 = 1e-2
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def fwi():
+    from paper_1912_08063_gb300 import fwi as f
+    return f
+
+
+def make_pair(w, vref=4600.0, snap="fp32", budget=0, nb=None, v=None):
+    f = fwi()
+    nb = w.nb if nb is None else nb
+    v = w.v if v is None else v
+    m = f.FwiModel(torch.from_numpy(np.ascontiguousarray(v)).cuda(), w.h, w.dt, w.nt,
+                   order=w.order, nb=nb, sponge_vref=vref, snap_dtype=snap,
+                   snap_budget_bytes=budget)
+    p = oracle.Problem(v, w.h, w.dt, w.nt, order=w.order, nb=nb, vref=vref, src=w.src,
+                       rec=w.rec, wavelet=w.wavelets())
+    return m, p, f.Acquisition(w.src, w.rec)
+
+
+def gpu_forward(m, acq, w, final=True):
+    wav = torch.from_numpy(w.wavelets()).cuda()
+    out = m.forward(acq, wav, final_state=final)
+    if final:
+        return out[0].cpu().numpy(), out[1].cpu().numpy()
+    return out.cpu().numpy()
+
+
+# ------------------------------------------------------------------ forward
+
+def test_forward_two_layer_2d():
+    """2-D two-layer model, 201 x 201, 8th order, dt 1 ms, 500 steps, 15 Hz Ricker."""
+    w = synth.two_layer_2d()
+    m, p, acq = make_pair(w)
+    tr, fin = gpu_forward(m, acq, w)
+    rtr, rfin = p.forward(final=True)
+    e_tr, e_fin = rel(tr, rtr), rel(fin.reshape(rfin.shape), rfin)
+    print(f"two_layer_2d: traces {e_tr:.2e} final {e_fin:.2e}")
+    assert e_tr <= TOL_FWD and e_fin <= TOL_FWD
+
+
+CASES = [
+    # ndim, physical shape, order, nb — ragged sizes that span several tiles
+    (2, (37, 45), 8, 6),
+    (2, (19, 300), 16, 5),
+    (2, (70, 131), 8, 0),
+    (3, (23, 17, 41), 8, 4),
+    (3, (15, 21, 29), 16, 3),
+    (3, (9, 40, 33), 8, 0),
+    (3, (6, 5, 7), 16, 0),        # grid smaller than the stencil radius
+]
+
+
+@pytest.mark.parametrize("ndim,shape,order,nb", CASES)
+def test_forward_random_models(ndim, shape, order, nb):
+    rng = np.random.default_rng(hash((ndim, shape, order)) & 0xffff)
+    w = synth.random_small(rng, ndim, shape, nt=50, order=order, nb=nb, nrec=11)
+    # receivers on the grid corners and on tile edges too
+    extra = [[0, 0, 0], [shape[0] - 1, 0 if ndim == 2 else shape[1] - 1, shape[-1] - 1]]
+    if shape[-1] > 32:
+        extra.append([shape[0] // 2, 0 if ndim == 2 else shape[1] // 2, 31 - nb if nb < 31 else 0])
+    w.rec = np.concatenate([w.rec, np.array(extra, dtype=np.int32)], 0)
+    m, p, acq = make_pair(w)
+    tr, fin = gpu_forward(m, acq, w)
+    rtr, rfin = p.forward(final=True)
+    e_tr, e_fin = rel(tr, rtr), rel(fin.reshape(rfin.shape), rfin)
+    assert e_tr <= TOL_FWD and e_fin <= TOL_FWD, (e_tr, e_fin)
+
+
+def test_forward_batched_shots_2d():
+    w = synth.faulted_2d(nz=60, nx=160, nt=120, nshots=5)
+    w.nb = 8
+    m, p, acq = make_pair(w)
+    tr, fin = gpu_forward(m, acq, w)
+    rtr, rfin = p.forward(final=True)
+    assert rel(tr, rtr) <= TOL_FWD and rel(fin.reshape(rfin.shape), rfin) <= TOL_FWD
+
+
+def test_forward_single_step_and_host_buffers():
+    """nt = 1 (one update from rest: only the source node is non-zero) through host
+    (numpy) buffers."""
+    f = fwi()
+    rng = np.random.default_rng(4)
+    w = synth.random_small(rng, 3, (11, 12, 13), nt=1, nb=2, nrec=4)
+    m = f.FwiModel(w.v, w.h, w.dt, w.nt, order=8, nb=w.nb, sponge_vref=4600.0)
+    acq = f.Acquisition(w.src, w.rec)
+    tr = np.zeros((1, 1, w.nrec), dtype=np.float32)
+    f.fwi_forward(m.handle, acq.c, w.wavelets(), tr)
+    p = oracle.Problem(w.v, w.h, w.dt, 1, order=8, nb=w.nb, vref=4600.0, src=w.src,
+                       rec=w.rec, wavelet=w.wavelets())
+    assert rel(tr, p.forward()) <= TOL_FWD or np.abs(p.forward()).max() == 0
+
+
+# ------------------------------------------------------------------ misfit and codec
+
+def test_misfit_matches_oracle():
+    f = fwi()
+    rng = np.random.default_rng(8)
+    for n in (1, 1000, 123457, 3_000_001):
+        a = rng.standard_normal(n).astype(np.float32)
+        b = (a + 1e-3 * rng.standard_normal(n)).astype(np.float32)
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+        f.fwi_misfit(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), n, out)
+        # the oracle takes the FP32 residual the kernel forms, then sums in FP64
+        r = (a - b).astype(np.float64)
+        ref = oracle.misfit(r, np.zeros_like(r))
+        # same terms, different FP64 summation order: |error| <= n eps sum|terms|
+        assert abs(out.item() - ref) <= n * 2.0 ** -52 * ref
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp16"])
+def test_codec_bit_exact(dtype):
+    f = fwi()
+    rng = np.random.default_rng(9)
+    n = 100_003
+    a = (rng.standard_normal(n) * 10.0 ** rng.uniform(-9, -3, n)).astype(np.float32)
+    b = (rng.standard_normal(n) * 1e-6).astype(np.float32)
+    a[:5] = [0.0, -0.0, 1e-30, -2.0 ** -20, 3.3e-3]
+    code = torch.zeros(2 * n, dtype=torch.int16, device="cuda")
+    sc = torch.zeros(1, dtype=torch.float32, device="cuda")
+    ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    dt_id = {"bf16": 1, "fp16": 2}[dtype]
+    f.fwi_snapshot_encode(ta, tb, n, dt_id, code, sc)
+    rcode, rs = oracle.snap_encode(a, b, dtype)
+    assert sc.item() == rs
+    assert np.array_equal(code.cpu().numpy().view(np.uint16).reshape(2, n), rcode)
+    da, db = torch.empty_like(ta), torch.empty_like(tb)
+    f.fwi_snapshot_decode(code, sc, n, dt_id, da, db)
+    ra, rb = oracle.snap_decode(rcode, rs, dtype)
+    assert np.array_equal(da.cpu().numpy(), ra) and np.array_equal(db.cpu().numpy(), rb)
+
+
+# ------------------------------------------------------------------ adjoint and gradient
+
+@pytest.mark.parametrize("ndim,shape,order", [(2, (30, 41), 8), (3, (13, 14, 19), 16)])
+def test_source_dot_product_gpu(ndim, shape, order):
+    """<F x, y> = <x, F* y> for the GPU forward and GPU source adjoint (FP32 arithmetic,
+    FP64 dots)."""
+    rng = np.random.default_rng(12)
+    w = synth.random_small(rng, ndim, shape, nt=60, order=order, nb=5, nrec=9)
+    f = fwi()
+    m, p, acq = make_pair(w)
+    x = rng.standard_normal((1, w.nt)).astype(np.float32)
+    y = rng.standard_normal((1, w.nt, w.nrec)).astype(np.float32)
+    Fx = m.forward(acq, torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
+    Fty = m.source_adjoint(acq, torch.from_numpy(y).cuda()).cpu().numpy().astype(np.float64)
+    lhs, rhs = np.sum(Fx * y), np.sum(x * Fty)
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs)), (lhs, rhs)
+    # and the GPU source adjoint against the oracle's
+    ref = p.source_adjoint(y.astype(np.float64))
+    assert rel(Fty, ref) <= TOL_FWD
+
+
+def _grad_case(ndim, shape, order, nt=70, nb=5, seed=13, nshots=1):
+    rng = np.random.default_rng(seed)
+    w = synth.random_small(rng, ndim, shape, nt=nt, order=order, nb=nb, nrec=12)
+    if nshots > 1:
+        src = np.repeat(w.src, nshots, 0)
+        src[:, -1] = rng.integers(0, shape[-1], nshots)
+        w.src = src
+    vobs = (w.v * (1.0 + 0.05 * synth.gaussian_random_field(rng, w.v.shape, w.h, 40.0, 1.0)))
+    p_obs = oracle.Problem(vobs, w.h, w.dt, w.nt, order=order, nb=nb, vref=4600.0,
+                           src=w.src, rec=w.rec, wavelet=w.wavelets())
+    dobs = p_obs.forward().astype(np.float32)
+    return w, dobs
+
+
+@pytest.mark.parametrize("ndim,shape,order,nshots", [
+    (2, (33, 47), 8, 1), (2, (29, 38), 16, 3), (3, (14, 17, 21), 8, 1), (3, (12, 13, 15), 16, 2)])
+def test_gradient_fp32_checkpoints(ndim, shape, order, nshots):
+    w, dobs = _grad_case(ndim, shape, order, nshots=nshots)
+    m, p, acq = make_pair(w, snap="fp32")
+    phi, g = m.gradient(acq, torch.from_numpy(w.wavelets()).cuda(), torch.from_numpy(dobs).cuda())
+    rphi, rg = p.gradient(dobs.astype(np.float64))
+    e = rel(g.cpu().numpy(), rg)
+    print(f"grad fp32 {ndim}d o{order}: rel-L2 {e:.2e}, misfit rel {abs(phi.item()-rphi)/rphi:.2e}")
+    assert e <= TOL_GRAD32
+    assert abs(phi.item() - rphi) <= 1e-4 * rphi
+
+
+def test_gradient_independent_of_checkpoint_budget_fp32():
+    """With FP32 checkpoints restores are exact, so every budget (no checkpoint, a few,
+    one per step) gives the same gradient bit for bit."""
+    w, dobs = _grad_case(2, (25, 31), 8, nt=40)
+    grads = []
+    for budget in (0, 1, 3 * 2 * 4 * (41 * 44 + 64), 10 ** 9):
+        m, p, acq = make_pair(w, snap="fp32", budget=budget if budget else 1)
+        _, g = m.gradient(acq, torch.from_numpy(w.wavelets()).cuda(), torch.from_numpy(dobs).cuda())
+        grads.append(g.cpu().numpy())
+        info = m.info()
+        assert info["last_adjoint_steps"] == w.nt
+    for g in grads[1:]:
+        assert np.array_equal(g, grads[0])
+
+
+@pytest.mark.parametrize("snap", ["bf16", "fp16"])
+@pytest.mark.parametrize("ndim,shape,order", [(2, (40, 52), 8), (3, (15, 16, 18), 16)])
+def test_gradient_16bit_checkpoints(snap, ndim, shape, order):
+    w, dobs = _grad_case(ndim, shape, order, nt=90)
+    probe, _, _ = make_pair(w, snap=snap, budget=1)
+    pitch, comp = probe.info()["pitch_x"], probe.info()["computed"]
+    field = -(-comp[0] * comp[1] * pitch // 64) * 64
+    m, p, acq = make_pair(w, snap=snap, budget=8 * 2 * 2 * field)   # eight checkpoints
+    _, g = m.gradient(acq, torch.from_numpy(w.wavelets()).cuda(), torch.from_numpy(dobs).cuda())
+    info = m.info()
+    assert 0 < info["snap_slots"] < w.nt    # recomputation really happened
+    rphi, rg = p.gradient(dobs.astype(np.float64))
+    e = rel(g.cpu().numpy(), rg)
+    print(f"grad {snap} {ndim}d: rel-L2 {e:.2e} slots {info['snap_slots']}")
+    assert e <= TOL_GRAD16
+
+
+# ------------------------------------------------------------------ errors
+
+def test_errors_are_reported():
+    f = fwi()
+    rng = np.random.default_rng(3)
+    w = synth.random_small(rng, 2, (20, 20), nt=10, nb=3)
+    with pytest.raises(f.FwiError) as e:
+        f.FwiModel(torch.from_numpy(w.v).cuda(), w.h, w.dt * 3.0, w.nt, nb=3)
+    assert e.value.code == f.FWI_ERR_CFL
+    m, _, _ = make_pair(w)
+    bad = f.Acquisition([[25, 0, 3]], w.rec)
+    with pytest.raises(f.FwiError) as e:
+        m.forward(bad, torch.from_numpy(w.wavelets()).cuda())
+    assert e.value.code == f.FWI_ERR_ARG
+    # a host-poisoned wavelet drives the wavefield non-finite: latched and reported
+    wav = w.wavelets().copy()
+    wav[0, 2] = np.inf
+    acq = f.Acquisition(w.src, w.rec)
+    m.forward(acq, torch.from_numpy(wav).cuda())
+    with pytest.raises(f.FwiError) as e:
+        f.fwi_sync_status(m.handle)
+    assert e.value.code == f.FWI_ERR_UNSTABLE
