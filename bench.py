@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--workload", default="salt_3d_512",
                     choices=["salt_3d_512", "layered_3d_256"])
     ap.add_argument("--nt", type=int, default=0, help="override the step count (short runs)")
+    ap.add_argument("--n", type=int, default=0,
+                    help="grid size of a scaled twin of the workload (profiling runs)")
     ap.add_argument("--snap-budget-gb", type=float, default=64.0)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
@@ -53,12 +55,12 @@ def parse():
     return ap.parse_args()
 
 
-def workload(name, nt_override):
+def workload(name, nt_override, n=0):
     from paper_1912_08063_gb300 import synth
     if name == "salt_3d_512":
-        w = synth.salt_3d(512)
+        w = synth.salt_3d(n or 512)
     else:
-        w = synth.layered_3d(256)
+        w = synth.layered_3d(n or 256)
     if nt_override:
         w.nt = nt_override
     return w
@@ -148,12 +150,13 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_baseline(w, sample_n=192, sample_nt=10):
+def cpu_baseline(w, sample_n=320, sample_nt=30):
     """The FP64 oracle, as it stands, on a bounded sample: a centred sample_n^3 crop of
     the model (same spacing, order, sponge, dt), one misfit-gradient evaluation of
     sample_nt steps.  Returns (Gpts/s, seconds, description, threads)."""
     import oracle
     n = w.shape[0]
+    sample_n = min(sample_n, n)
     c0 = (n - sample_n) // 2
     sl = slice(c0, c0 + sample_n)
     v = np.ascontiguousarray(w.v[sl, sl, sl], dtype=np.float64)
@@ -182,7 +185,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = workload(args.workload, args.nt)
+    w = workload(args.workload, args.nt, args.n)
     vals = []
     for i in range(args.warmup + args.steps):
         g, t, desc, threads = cpu_baseline(w)
@@ -223,7 +226,7 @@ def main():
         if world > 1:
             dist.barrier()
 
-    w = workload(args.workload, args.nt)
+    w = workload(args.workload, args.nt, args.n)
     dev = torch.device("cuda", local)
     budget = int(args.snap_budget_gb * (1 << 30))
     model = fwi.FwiModel(torch.from_numpy(w.v).to(dev), w.h, w.dt, w.nt, order=w.order,

@@ -149,15 +149,17 @@ int fwi_source_adjoint(fwi_model *m, const fwi_acq *acq, const float *y, float *
 int fwi_misfit(const float *d_mod, const float *d_obs, int64_t n, double *misfit_dev,
                cudaStream_t stream);
 
-/* Checkpoint codec (device pointers).  Encode the pair (a, b) of n FP32 values into
- * 16-bit codes (FWI_SNAP_BF16 / FWI_SNAP_FP16, round to nearest even) after scaling by
- * s = 2^floor(log2(T / max|a,b|)), T = 2^14 for FP16 and 1 for BF16 (s = 1 when the
- * pair is all zero); code holds [2][n] 16-bit values, scale[0] receives s.  FWI_SNAP_FP32
- * copies the values (s = 1).  Non-finite input sets scale[0] to NaN and returns
- * FWI_OK (the codes are then unspecified). */
+/* Checkpoint codec (device pointers) for a state pair (a, b) = (u^n, u^{n-1}) of n FP32
+ * values.  FWI_SNAP_BF16 / FWI_SNAP_FP16 store the components a and d = a - b as 16-bit
+ * codes (round to nearest even), each after scaling by its own
+ * s = 2^floor(log2(T / max|component|)), T = 2^14 for FP16 and 1 for BF16 (s = 1 for an
+ * all-zero component): code holds [2][n] 16-bit values, scale[0..1] receive (s_a, s_d).
+ * FWI_SNAP_FP32 copies a and b ([2][n] FP32, scales 1).  Non-finite input sets the
+ * scales to NaN and returns FWI_OK (the codes are then unspecified).  Allocates two
+ * words of stream-ordered scratch. */
 int fwi_snapshot_encode(const float *a, const float *b, int64_t n, int32_t dtype,
                         void *code, float *scale, cudaStream_t stream);
-/* Inverse of fwi_snapshot_encode: a = code[0] / s, b = code[1] / s. */
+/* Inverse of fwi_snapshot_encode: a = code[0] / s_a, b = a - code[1] / s_d. */
 int fwi_snapshot_decode(const void *code, const float *scale, int64_t n, int32_t dtype,
                         float *a, float *b, cudaStream_t stream);
 

@@ -81,7 +81,7 @@ def _load():
             lib.oracle_f16_to_f32.restype = f
             lib.oracle_snap_encode.argtypes = [P, P, ctypes.c_int64, i, P, P]
             lib.oracle_snap_encode.restype = None
-            lib.oracle_snap_decode.argtypes = [P, f, ctypes.c_int64, i, P, P]
+            lib.oracle_snap_decode.argtypes = [P, P, ctypes.c_int64, i, P, P]
             lib.oracle_snap_decode.restype = None
             _lib = lib
     return _lib
@@ -253,22 +253,23 @@ def snap_scale(maxabs: float, dtype: str) -> float:
 
 
 def snap_encode(a, b, dtype: str):
-    """(codes uint16 [2][n], scale) of the checkpoint pair (a, b) (FP32 inputs)."""
+    """(codes uint16 [2][n], scales float32 [2]) of the checkpoint pair (a, b): the
+    components a and a - b, each with its own power-of-two scale."""
     a = np.ascontiguousarray(a, dtype=np.float32).ravel()
     b = np.ascontiguousarray(b, dtype=np.float32).ravel()
     code = np.zeros((2, a.size), dtype=np.uint16)
-    sc = ctypes.c_float(0.0)
-    _load().oracle_snap_encode(_ptr(a), _ptr(b), a.size, SNAP[dtype], _ptr(code),
-                               ctypes.byref(sc))
-    return code, sc.value
+    sc = np.zeros(2, dtype=np.float32)
+    _load().oracle_snap_encode(_ptr(a), _ptr(b), a.size, SNAP[dtype], _ptr(code), _ptr(sc))
+    return code, sc
 
 
-def snap_decode(code, scale, dtype: str):
+def snap_decode(code, scales, dtype: str):
     code = np.ascontiguousarray(code, dtype=np.uint16).reshape(2, -1)
+    sc = np.ascontiguousarray(scales, dtype=np.float32).reshape(2)
     n = code.shape[1]
     a = np.zeros(n, dtype=np.float32)
     b = np.zeros(n, dtype=np.float32)
-    _load().oracle_snap_decode(_ptr(code), float(scale), n, SNAP[dtype], _ptr(a), _ptr(b))
+    _load().oracle_snap_decode(_ptr(code), _ptr(sc), n, SNAP[dtype], _ptr(a), _ptr(b))
     return a, b
 
 

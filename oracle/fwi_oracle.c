@@ -521,10 +521,14 @@ int oracle_model_fields(int ndim, const int64_t *shape, const double *h, const d
 /* ------------------------------------------------------------------ checkpoint codec */
 
 /* Checkpoints of the reverse sweep (the paper only names the gradient, Sec. 1; the
- * checkpoint format is a reading): the pair (u^n, u^{n-1}) is stored as 16-bit floats
- * after scaling by s = 2^floor(log2(T / max|u^n, u^{n-1}|)), T = 2^14 for IEEE half and
- * T = 1 for bfloat16, with round-to-nearest-even; s = 1 for an all-zero pair and NaN
- * when the pair holds a non-finite value; floor(log2 .) is clamped to [-126, 127]. */
+ * checkpoint format is a reading): the state pair (u^n, u^{n-1}) is stored as the two
+ * components a = u^n and d = u^n - u^{n-1} (single-precision difference), each as 16-bit
+ * floats after scaling by its own s = 2^floor(log2(T / max|component|)), T = 2^14 for
+ * IEEE half and T = 1 for bfloat16, with round-to-nearest-even; s = 1 for an all-zero
+ * component and NaN when the pair holds a non-finite value; floor(log2 .) is clamped to
+ * [-126, 127].  Decoding returns a and a - d.  Storing the difference keeps the part of
+ * the state that drives the time stepping (u^n - u^{n-1}, about omega dt of u) to the
+ * format's relative precision, instead of to that of u. */
 float oracle_snap_scale(float maxabs, int dtype)
 {
     if (dtype == 0 || maxabs == 0.0f) return 1.0f;
@@ -590,34 +594,38 @@ float oracle_f16_to_f32(uint16_t h)
     return or_float(sign | ((e - 15u + 127u) << 23) | (m << 13));
 }
 
-/* Encode the pair (a, b) of n values: code[0..n) from a, code[n..2n) from b. */
+/* Encode the pair (a, b) of n values: code[0..n) from a with scale[0], code[n..2n) from
+ * d = a - b with scale[1]. */
 void oracle_snap_encode(const float *a, const float *b, int64_t n, int dtype,
                         uint16_t *code, float *scale)
 {
-    float mx = 0.0f;
+    float ma = 0.0f, md = 0.0f;
     int bad = 0;
     for (int64_t i = 0; i < n; ++i) {
-        float x = fabsf(a[i]), y = fabsf(b[i]);
-        if (!isfinite(x) || !isfinite(y)) bad = 1;
-        if (x > mx) mx = x;
-        if (y > mx) mx = y;
+        float d = a[i] - b[i];
+        if (!isfinite(a[i]) || !isfinite(b[i])) bad = 1;
+        if (fabsf(a[i]) > ma) ma = fabsf(a[i]);
+        if (fabsf(d) > md) md = fabsf(d);
     }
-    float s = bad ? NAN : oracle_snap_scale(mx, dtype);
-    *scale = s;
+    float sa = bad ? NAN : oracle_snap_scale(ma, dtype);
+    float sd = bad ? NAN : oracle_snap_scale(md, dtype);
+    scale[0] = sa;
+    scale[1] = sd;
     for (int64_t i = 0; i < n; ++i) {
-        float va = a[i] * s, vb = b[i] * s;   /* single-precision products, as stored */
+        float va = a[i] * sa;                 /* single-precision products, as stored */
+        float vd = (a[i] - b[i]) * sd;
         code[i] = dtype == 2 ? oracle_f32_to_f16(va) : oracle_f32_to_bf16(va);
-        code[n + i] = dtype == 2 ? oracle_f32_to_f16(vb) : oracle_f32_to_bf16(vb);
+        code[n + i] = dtype == 2 ? oracle_f32_to_f16(vd) : oracle_f32_to_bf16(vd);
     }
 }
 
-void oracle_snap_decode(const uint16_t *code, float scale, int64_t n, int dtype,
+void oracle_snap_decode(const uint16_t *code, const float *scale, int64_t n, int dtype,
                         float *a, float *b)
 {
     for (int64_t i = 0; i < n; ++i) {
         float va = dtype == 2 ? oracle_f16_to_f32(code[i]) : oracle_bf16_to_f32(code[i]);
-        float vb = dtype == 2 ? oracle_f16_to_f32(code[n + i]) : oracle_bf16_to_f32(code[n + i]);
-        a[i] = va / scale;
-        b[i] = vb / scale;
+        float vd = dtype == 2 ? oracle_f16_to_f32(code[n + i]) : oracle_bf16_to_f32(code[n + i]);
+        a[i] = va / scale[0];
+        b[i] = a[i] - vd / scale[1];
     }
 }

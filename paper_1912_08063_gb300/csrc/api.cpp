@@ -6,11 +6,13 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "fwi_internal.h"
+#include "step3d.h"
 
 namespace fwi {
 std::vector<int32_t> revolve_actions(int32_t nsteps, int32_t nslots, int64_t *n_forward);
@@ -165,6 +167,14 @@ struct fwi_model {
     std::vector<cudaEvent_t> ev;
     std::vector<int> ev_kind;   // per event pair: 0 forward step, 1 reverse step
     size_t ev_used = 0;
+    // TMA tensor maps of the 3-D step, keyed by buffer, shot count and box
+    struct MapEntry {
+        const void *base;
+        int ns, bx, by;
+        CUtensorMap map;
+    };
+    std::vector<MapEntry> maps;
+    int resident = 0;   // resident CTAs of the 3-D step kernel
     int64_t t_fwd_n = 0, t_adj_n = 0;
     double t_fwd_ms = 0.0, t_adj_ms = 0.0;
 
@@ -187,7 +197,10 @@ const float *sig_x(const fwi_model *m) { return m->sig.as<float>() + m->g.nz + m
 
 int check_status(fwi_model *m)
 {
-    if (m->h_flag && *(volatile unsigned *)m->h_flag)
+    const unsigned st = m->h_flag ? *(volatile unsigned *)m->h_flag : 0u;
+    if (st & 2u)
+        return fail(FWI_ERR_TIMEOUT, "a bounded device wait ran out (latched device status)");
+    if (st & 1u)
         return fail(FWI_ERR_UNSTABLE, "a wavefield became non-finite (latched device status)");
     return FWI_OK;
 }
@@ -226,8 +239,8 @@ int set_velocity(fwi_model *m, const float *vp, cudaStream_t s)
     FWI_TRY(m->v.ensure(nphys * sizeof(float)));
     FWI_CU(cudaMemcpyAsync(m->v.p, vp, nphys * sizeof(float), cudaMemcpyDefault, s));
     // largest velocity through the codec's max|.| kernel (v > 0)
-    FWI_TRY(m->maxbits.ensure(64 * sizeof(unsigned)));
-    FWI_CU(cudaMemsetAsync(m->maxbits.p, 0, sizeof(unsigned), s));
+    FWI_TRY(m->maxbits.ensure(128 * sizeof(unsigned)));
+    FWI_CU(cudaMemsetAsync(m->maxbits.p, 0, 2 * sizeof(unsigned), s));
     FWI_LAUNCH(m, launch_maxabs(m->v.as<float>(), m->v.as<float>(), nphys, nphys, 1,
                          m->maxbits.as<unsigned>(), s));
     unsigned bits = 0;
@@ -321,7 +334,7 @@ int ensure_workspace(fwi_model *m, const fwi_acq *a, bool grad, cudaStream_t s)
     FWI_TRY(m->rec_off.ensure((size_t)ns * nr * sizeof(int64_t)));
     FWI_TRY(m->inj.ensure((size_t)ns * nr * sizeof(float)));
     FWI_TRY(m->src_scale.ensure(ns * sizeof(float)));
-    FWI_TRY(m->maxbits.ensure((ns > 64 ? ns : 64) * sizeof(unsigned)));
+    FWI_TRY(m->maxbits.ensure(2 * (ns > 64 ? ns : 64) * sizeof(unsigned)));
     FWI_TRY(m->partials.ensure(1024 * sizeof(double)));
     FWI_TRY(m->phi.ensure(sizeof(double)));
     if (grad) {
@@ -369,13 +382,98 @@ StepParams base_params(const fwi_model *m)
 
 // One time-step launch (kind 0: forward, 1: reverse); bracketed by CUDA events on the
 // launching stream when timing is on.
-int step_launch(fwi_model *m, const StepParams &p, int ns, bool img, int kind, cudaStream_t s)
+int field_map(fwi_model *m, const void *base, int ns, int bx, int by, CUtensorMap *out)
 {
-    ++m->launches;
-    if (!m->opts.timing) {
+    for (const auto &e : m->maps)
+        if (e.base == base && e.ns == ns && e.bx == bx && e.by == by) {
+            *out = e.map;
+            return FWI_OK;
+        }
+    fwi_model::MapEntry e{base, ns, bx, by, {}};
+    if (encode_field_map(&e.map, base, m->g, ns, bx, by) != 0)
+        return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    m->maps.push_back(e);
+    *out = e.map;
+    return FWI_OK;
+}
+
+// One launch of the TMA-staged 3-D kernel (k_step3d.cu) in `mode`.
+int step3d_launch(fwi_model *m, const StepParams &p, int ns, int mode, cudaStream_t s)
+{
+    const Geom &g = m->g;
+    Step3dParams q{};
+    q.M = g.M;
+    q.nx = g.nx;
+    q.ny = g.ny;
+    q.nz = g.nz;
+    q.px = g.px;
+    q.plane = g.plane;
+    q.field = g.field;
+    for (int k = 0; k <= kMaxM; ++k) {
+        q.cx[k] = m->co.cx[k];
+        q.cy[k] = m->co.cy[k];
+        q.cz[k] = m->co.cz[k];
+        q.cy2[k] = make_float2(m->co.cy[k], m->co.cy[k]);
+        q.cz2[k] = make_float2(m->co.cz[k], m->co.cz[k]);
+    }
+    q.c0 = m->co.c0;
+    q.c02 = make_float2(m->co.c0, m->co.c0);
+    q.sig_x = sig_x(m);
+    q.sig_y = sig_y(m);
+    q.sig_z = sig_z(m);
+    q.err = m->d_flag;
+    const int TY = step3d_variant(g.M).ty;
+    CUtensorMap mc, ma, mb;
+    if (mode == kModeStep) {
+        FWI_TRY(field_map(m, p.cur, ns, 64 + 2 * g.M, TY + 2 * g.M, &mc));
+        FWI_TRY(field_map(m, p.prev, ns, 64, TY, &ma));
+        FWI_TRY(field_map(m, m->W.p, 1, 64, TY, &mb));
+        q.out = p.prev;
+        q.src_off = p.src_off;
+        q.wavelet = p.wavelet;
+        q.nt = p.nt;
+        q.n = p.n;
+        q.dt2 = p.dt2;
+    } else {
+        FWI_TRY(field_map(m, p.u_img, ns, 64 + 2 * g.M, TY + 2 * g.M, &mc));
+        FWI_TRY(field_map(m, p.cur, ns, 64, TY, &ma));
+        FWI_TRY(field_map(m, p.gacc, ns, 64, TY, &mb));
+        q.out = p.gacc;
+    }
+    if (m->resident <= 0) m->resident = step3d_resident_ctas(g.M);
+    const int tiles = ((g.nx + 63) / 64) * ((g.ny + TY - 1) / TY);
+    const int nch = plan_zchunks(g.nz, g.M, tiles, ns, m->resident);
+    q.zchunk = (g.nz + nch - 1) / nch;
+    FWI_CU(launch_step3d_tma(q, ns, mode, (g.nz + q.zchunk - 1) / q.zchunk, mc, ma, mb, s));
+    return FWI_OK;
+}
+
+bool use_step3d(const fwi_model *m)
+{
+    if (m->ndim != 3 || (m->M != 4 && m->M != 8)) return false;
+    const char *e = std::getenv("FWI_STEP3D");
+    return !(e && std::strcmp(e, "v1") == 0);
+}
+
+// The time step itself: the fused v1 kernel (2-D), or in 3-D the TMA kernel, preceded
+// by its imaging pass when the reverse step images.
+int raw_step(fwi_model *m, const StepParams &p, int ns, bool img, cudaStream_t s)
+{
+    if (!use_step3d(m)) {
         FWI_CU(launch_step(p, ns, img, s));
         return FWI_OK;
     }
+    if (img) {
+        ++m->launches;
+        FWI_TRY(step3d_launch(m, p, ns, kModeImage, s));
+    }
+    return step3d_launch(m, p, ns, kModeStep, s);
+}
+
+int step_launch(fwi_model *m, const StepParams &p, int ns, bool img, int kind, cudaStream_t s)
+{
+    ++m->launches;
+    if (!m->opts.timing) return raw_step(m, p, ns, img, s);
     if (m->ev_used + 2 > m->ev.size()) {
         for (int i = 0; i < 256; ++i) {
             cudaEvent_t e;
@@ -384,7 +482,7 @@ int step_launch(fwi_model *m, const StepParams &p, int ns, bool img, int kind, c
         }
     }
     FWI_CU(cudaEventRecord(m->ev[m->ev_used], s));
-    FWI_CU(launch_step(p, ns, img, s));
+    FWI_TRY(raw_step(m, p, ns, img, s));
     FWI_CU(cudaEventRecord(m->ev[m->ev_used + 1], s));
     m->ev_used += 2;
     m->ev_kind.push_back(kind);
@@ -650,7 +748,7 @@ int fwi_adjoint_gradient(fwi_model *m, const fwi_acq *acq, const float *wavelets
         // shrink on failure rather than fail: fewer slots only cost recomputation
         while (slots > 0 && m->snaps.ensure((size_t)slots * per_slot) != FWI_OK) slots /= 2;
     }
-    FWI_TRY(m->scales.ensure((size_t)(slots > 0 ? slots : 1) * ns * sizeof(float)));
+    FWI_TRY(m->scales.ensure((size_t)(slots > 0 ? slots : 1) * 2 * ns * sizeof(float)));
     if (slots != m->sched_nslots) {
         m->sched = revolve_actions(nt, (int32_t)slots, &m->sched_fwd);
         m->sched_nslots = (int)slots;
@@ -701,13 +799,13 @@ int fwi_adjoint_gradient(fwi_model *m, const fwi_acq *acq, const float *wavelets
                 ++nfwd;
             }
         } else if (kind == 2) {   // STORE the pair (u^step, u^{step-1})
-            FWI_CU(cudaMemsetAsync(m->maxbits.p, 0, ns * sizeof(unsigned), s));
+            FWI_CU(cudaMemsetAsync(m->maxbits.p, 0, 2 * ns * sizeof(unsigned), s));
             FWI_LAUNCH(m, launch_maxabs(m->u[cur].as<float>(), m->u[1 - cur].as<float>(), g.field,
                                  g.field, ns, m->maxbits.as<unsigned>(), s));
             FWI_LAUNCH(m, launch_encode(m->u[cur].as<float>(), m->u[1 - cur].as<float>(), g.field,
                                  g.field, ns, m->opts.snap_dtype, m->maxbits.as<unsigned>(),
                                  (void *)(codes + (size_t)arg * per_slot), 2 * g.field,
-                                 m->scales.as<float>() + (size_t)arg * ns, m->d_flag, s));
+                                 m->scales.as<float>() + (size_t)arg * 2 * ns, m->d_flag, s));
             slot_step[arg] = step;
             ++nstore;
         } else if (kind == 3) {   // RESTORE
@@ -718,7 +816,7 @@ int fwi_adjoint_gradient(fwi_model *m, const fwi_acq *acq, const float *wavelets
                 step = 0;
             } else {
                 FWI_LAUNCH(m, launch_decode(codes + (size_t)arg * per_slot, 2 * g.field,
-                                     m->scales.as<float>() + (size_t)arg * ns, g.field, g.field,
+                                     m->scales.as<float>() + (size_t)arg * 2 * ns, g.field, g.field,
                                      ns, m->opts.snap_dtype, m->u[cur].as<float>(),
                                      m->u[1 - cur].as<float>(), s));
                 step = slot_step[arg];
@@ -842,8 +940,8 @@ int fwi_snapshot_encode(const float *a, const float *b, int64_t n, int32_t dtype
     if (!a || !b || !code || !scale || n < 0 || dtype < 0 || dtype > 2)
         return fail(FWI_ERR_ARG, "bad argument");
     unsigned *mb = nullptr;
-    FWI_CU(cudaMallocAsync((void **)&mb, sizeof(unsigned), s));
-    FWI_CU(cudaMemsetAsync(mb, 0, sizeof(unsigned), s));
+    FWI_CU(cudaMallocAsync((void **)&mb, 2 * sizeof(unsigned), s));
+    FWI_CU(cudaMemsetAsync(mb, 0, 2 * sizeof(unsigned), s));
     cudaError_t e = launch_maxabs(a, b, n, n, 1, mb, s);
     if (e == cudaSuccess) e = launch_encode(a, b, n, n, 1, dtype, mb, code, 2 * n, scale, nullptr, s);
     cudaError_t e2 = cudaFreeAsync(mb, s);

@@ -147,17 +147,27 @@ __global__ void k_sum_partials(const double *__restrict__ part, int nb, double *
 
 __device__ __forceinline__ unsigned absbits(float x) { return __float_as_uint(x) & 0x7fffffffu; }
 
+// out[2s] = bits of max|a|, out[2s+1] = bits of max|a - b| (FP32 difference) per shot s;
+// a NaN or infinity anywhere in a or b drives both to >= 0x7f800000.
 __global__ void k_maxabs(const float *__restrict__ a, const float *__restrict__ b, int64_t n,
                          int64_t stride, unsigned *__restrict__ out)
 {
     const int s = blockIdx.y;
     const float *pa = a + s * stride, *pb = b + s * stride;
-    unsigned m = 0;
+    unsigned ma = 0, md = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        m = max(m, max(absbits(pa[i]), absbits(pb[i])));
-    m = __reduce_max_sync(0xffffffffu, m);
-    if ((threadIdx.x & 31) == 0 && m) atomicMax(out + s, m);
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = pa[i], y = pb[i];
+        const unsigned bad = (absbits(x) >= 0x7f800000u || absbits(y) >= 0x7f800000u) ? 0x7fc00000u : 0u;
+        ma = max(ma, max(absbits(x), bad));
+        md = max(md, max(absbits(x - y), bad));
+    }
+    ma = __reduce_max_sync(0xffffffffu, ma);
+    md = __reduce_max_sync(0xffffffffu, md);
+    if ((threadIdx.x & 31) == 0) {
+        if (ma) atomicMax(out + 2 * s, ma);
+        if (md) atomicMax(out + 2 * s + 1, md);
+    }
 }
 
 // s = 2^floor(log2(T / max)) with T = 2^texp, from the bit pattern of max (exact
@@ -187,11 +197,15 @@ __global__ void k_encode(const float *__restrict__ a, const float *__restrict__ 
                          void *__restrict__ code, int64_t cstride, float *__restrict__ scale,
                          unsigned *flag)
 {
+    // 16-bit formats store a = u^n and d = u^n - u^{n-1}, each with its own scale; FP32
+    // stores the pair unchanged (lossless)
     const int s = blockIdx.y;
-    const float sc = snap_scale(maxbits[s], dtype);
+    const float sa = snap_scale(maxbits[2 * s], dtype);
+    const float sd = snap_scale(maxbits[2 * s + 1], dtype);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        scale[s] = sc;
-        if (flag && maxbits[s] >= 0x7f800000u) atomicOr(flag, 1u);
+        scale[2 * s] = sa;
+        scale[2 * s + 1] = sd;
+        if (flag && maxbits[2 * s] >= 0x7f800000u) atomicOr(flag, 1u);
     }
     const float *pa = a + s * stride, *pb = b + s * stride;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -203,12 +217,12 @@ __global__ void k_encode(const float *__restrict__ a, const float *__restrict__ 
             c[n + i] = vb;
         } else if (dtype == 1) {
             __nv_bfloat16 *c = (__nv_bfloat16 *)code + s * cstride;
-            c[i] = __float2bfloat16_rn(va * sc);
-            c[n + i] = __float2bfloat16_rn(vb * sc);
+            c[i] = __float2bfloat16_rn(va * sa);
+            c[n + i] = __float2bfloat16_rn((va - vb) * sd);
         } else {
             __half *c = (__half *)code + s * cstride;
-            c[i] = __float2half_rn(va * sc);
-            c[n + i] = __float2half_rn(vb * sc);
+            c[i] = __float2half_rn(va * sa);
+            c[n + i] = __float2half_rn((va - vb) * sd);
         }
     }
 }
@@ -218,7 +232,7 @@ __global__ void k_decode(const void *__restrict__ code, int64_t cstride,
                          float *__restrict__ a, float *__restrict__ b)
 {
     const int s = blockIdx.y;
-    const float sc = scale[s];
+    const float sa = scale[2 * s], sd = scale[2 * s + 1];
     float *pa = a + s * stride, *pb = b + s * stride;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -228,12 +242,14 @@ __global__ void k_decode(const void *__restrict__ code, int64_t cstride,
             pb[i] = c[n + i];
         } else if (dtype == 1) {
             const __nv_bfloat16 *c = (const __nv_bfloat16 *)code + s * cstride;
-            pa[i] = __bfloat162float(c[i]) / sc;
-            pb[i] = __bfloat162float(c[n + i]) / sc;
+            const float va = __bfloat162float(c[i]) / sa;
+            pa[i] = va;
+            pb[i] = va - __bfloat162float(c[n + i]) / sd;
         } else {
             const __half *c = (const __half *)code + s * cstride;
-            pa[i] = __half2float(c[i]) / sc;
-            pb[i] = __half2float(c[n + i]) / sc;
+            const float va = __half2float(c[i]) / sa;
+            pa[i] = va;
+            pb[i] = va - __half2float(c[n + i]) / sd;
         }
     }
 }

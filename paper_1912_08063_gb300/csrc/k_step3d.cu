@@ -1,0 +1,75 @@
+// Dispatch of the TMA-staged 3-D step kernel (template in k_step3d.cuh; the radius-4 and
+// radius-8 instantiations live in k_step3d_m4.cu and k_step3d_m8.cu so they compile in
+// parallel).
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "step3d.h"
+
+namespace fwi {
+
+// Configuration per radius; FWI_STEP3D_VARIANT=<ty>,<ry>,<pf>,<unroll> overrides it for
+// tuning runs (only the instantiated combinations are accepted).
+Step3dVariant step3d_variant(int M)
+{
+    Step3dVariant v = M == 8 ? Step3dVariant{32, 1, 2, true} : Step3dVariant{16, 1, 3, true};
+    if (const char *e = std::getenv("FWI_STEP3D_VARIANT")) {
+        int ty, ry, pf, un;
+        if (std::sscanf(e, "%d,%d,%d,%d", &ty, &ry, &pf, &un) == 4) {
+            Step3dVariant w{ty, ry, pf, un != 0};
+            const Step3dKernelInfo k = M == 8 ? step3d_kernel_m8(w, 0) : step3d_kernel_m4(w, 0);
+            if (k.fn) v = w;
+        }
+    }
+    return v;
+}
+
+static Step3dKernelInfo kernel_info(int M, int mode)
+{
+    const Step3dVariant v = step3d_variant(M);
+    if (M == 8) return step3d_kernel_m8(v, mode);
+    if (M == 4) return step3d_kernel_m4(v, mode);
+    return Step3dKernelInfo{nullptr, 0, 0};
+}
+
+int step3d_smem_bytes(int M) { return kernel_info(M, kModeStep).smem; }
+int step3d_threads(int M) { return kernel_info(M, kModeStep).threads; }
+
+int step3d_resident_ctas(int M)
+{
+    const Step3dKernelInfo k = kernel_info(M, kModeStep);
+    if (!k.fn) return 152;
+    if (cudaFuncSetAttribute((const void *)k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             k.smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 152;
+    }
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k.fn, k.threads,
+                                                      k.smem) != cudaSuccess || per < 1) {
+        cudaGetLastError();
+        per = 1;
+    }
+    return (sms > 0 ? sms : 152) * per;
+}
+
+cudaError_t launch_step3d_tma(const Step3dParams &p, int nshots, int mode, int nchunks,
+                              const CUtensorMap &mc, const CUtensorMap &ma,
+                              const CUtensorMap &mb, cudaStream_t s)
+{
+    const Step3dKernelInfo k = kernel_info(p.M, mode);
+    if (!k.fn) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute((const void *)k.fn,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem);
+    if (e != cudaSuccess) return e;
+    const int TY = step3d_variant(p.M).ty;
+    const int tiles = ((p.nx + 63) / 64) * ((p.ny + TY - 1) / TY);
+    dim3 grid(tiles, nchunks, nshots);
+    k.fn<<<grid, k.threads, k.smem, s>>>(p, mc, ma, mb);
+    return cudaGetLastError();
+}
+
+}  // namespace fwi

@@ -1,0 +1,401 @@
+// 3-D time step on GB300 (sm_103a): TMA-staged z-streaming stencil (kernel template).
+//
+// One template serves two modes on the same stencil machinery:
+//   kModeStep   out = (2 c + W (L c) - (1 - s) prev [+ dt^2 w at the source]) / (1 + s),
+//               written over prev           (Eq. 3 with the sponge; forward and, in the
+//               W-weighted variable mu = W nu, the reverse step)
+//   kModeImage  g += aux * (L c)            (zero-lag imaging: g += mu^{m+1} L u^m)
+// where c is the streamed field (u^n, mu^{m+1} or u^m) and L the order-2M Laplacian with
+// zero outside the computed grid.
+//
+// A CTA owns a 64 x TY tile of the (x, y) plane and a chunk of z-planes:
+//   * one elected thread issues TMA loads (cp.async.bulk.tensor, 4-D maps over
+//     [shot][z][y][x]) of the plane's halo tile (64 + 2M) x (TY + 2M) into a ring of
+//     SH = M + 1 + P shared-memory stages, and of the pointwise tiles (prev and W, or
+//     aux and g) into a ring of SP = P + 1 stages; completion is tracked by mbarriers
+//     with transaction counts and every wait is bounded;
+//   * out-of-grid halo cells are zero-filled by the TMA unit (the Dirichlet condition);
+//   * each thread computes 4 (x) x RY (y) points: the z-neighbours come from a register
+//     queue of 2M + 1 planes, the x/y-neighbours from the resident halo stage of the
+//     output plane (it arrived M planes earlier and the ring keeps it);
+//   * UNR = true unrolls the plane loop by 2M + 1 so that the register queue rotates at
+//     compile time (no register moves); y and z sums use packed FP32x2 FMAs and split
+//     accumulators;
+//   * results are stored with 16-byte stores straight from registers.
+// DRAM traffic per point and step: c once (halo re-reads hit L2), two pointwise fields
+// once, one write: 16 bytes in either mode.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <utility>
+
+#include "fwi_internal.h"
+#include "step3d.h"
+
+namespace fwi {
+namespace s3d {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~2^22 polls (each poll may suspend the thread briefly).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    for (int i = 0; i < (1 << 22); ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load4(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                          int w, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+template <int M_, int TY_, int RY_, int P_>
+struct Cfg {
+    static constexpr int M = M_, TY = TY_, RY = RY_, P = P_;
+    static constexpr int TX = 64, RX = 4;
+    static constexpr int NTX = TX / RX, NTY = TY / RY, NT = NTX * NTY;
+    static constexpr int SX = TX + 2 * M, SY = TY + 2 * M;
+    static constexpr int SH = M + 1 + P, SP = P + 1, Q = 2 * M + 1;
+    static constexpr int HALO_BYTES = SX * SY * 4;
+    static constexpr int TILE_BYTES = TX * TY * 4;
+    static constexpr int HALO_STRIDE = (HALO_BYTES + 1023) / 1024 * 1024;
+    static constexpr int PW_STRIDE = (2 * TILE_BYTES + 1023) / 1024 * 1024;
+    static constexpr int SMEM = SH * HALO_STRIDE + SP * PW_STRIDE + 1024 /* barriers */ + 1024;
+};
+
+// Everything one plane iteration needs; lives in registers (all accesses are inlined).
+template <class C, int MODE>
+struct Ctx {
+    const Step3dParams *p;
+    const CUtensorMap *mc, *ma, *mb;
+    unsigned char *halo, *pw;
+    uint64_t *bar_h, *bar_p;
+    int *abort_flag;
+    int tid, tx, ty, za, nout, niter, shot, bx, by, x0, y0, hx, hy;
+    int h_issued, p_issued;   // loads issued so far (thread 0's view)
+    int cur_it;               // iteration being executed
+    float sxp[4], syr[C::RY];
+    bool xin;
+    int64_t sb;
+    int src_j, src_r, src_e;   // source node in this thread's block (src_j < 0: none)
+    float srcv;
+    float4 q[C::Q][C::RY];
+
+    __device__ __forceinline__ void issue_halo(int it)
+    {
+        const int st = it % C::SH;
+        uint64_t *b = bar_h + st;
+        mbar_expect_tx(b, C::HALO_BYTES);
+        tma_load4(halo + st * C::HALO_STRIDE, mc, hx, hy, za - C::M + it, shot, b);
+    }
+
+    __device__ __forceinline__ void issue_pw(int o)
+    {
+        const int st = o % C::SP;
+        uint64_t *b = bar_p + st;
+        unsigned char *d = pw + st * C::PW_STRIDE;
+        mbar_expect_tx(b, 2 * C::TILE_BYTES);
+        tma_load4(d, ma, bx * C::TX, by * C::TY, za + o, shot, b);
+        tma_load4(d + C::TILE_BYTES, mb, bx * C::TX, by * C::TY, za + o,
+                  MODE == kModeStep ? 0 : shot, b);
+    }
+
+    // One plane iteration `it`; the queue slot of plane (it - 2M + i) is (R + 1 + i) % Q,
+    // so the newest plane lands in slot R.  Returns false when the loop must stop.
+    template <int R>
+    __device__ __forceinline__ bool plane(int it)
+    {
+        constexpr int M = C::M, Q = C::Q, SX = C::SX, SH = C::SH, SP = C::SP, TX = C::TX,
+                      RY = C::RY;
+        if (it >= niter) return false;
+        cur_it = it;
+        // every thread passes this barrier in every iteration, so an abort raised by any
+        // thread in iteration it is seen by all of them here, in iteration it + 1
+        __syncthreads();
+        if (*(volatile int *)abort_flag) return false;
+        if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (it + C::P < niter) {
+                issue_halo(it + C::P);
+                h_issued = it + C::P + 1;
+            }
+            const int op = it - 2 * M + C::P;
+            if (op >= 0 && op < nout) {
+                issue_pw(op);
+                p_issued = op + 1;
+            }
+        }
+        if (!mbar_wait(bar_h + it % SH, (it / SH) & 1)) {
+            atomicExch(abort_flag, 1);
+            return true;
+        }
+        const float *hk = (const float *)(halo + (it % SH) * C::HALO_STRIDE);
+#pragma unroll
+        for (int r = 0; r < RY; ++r)
+            q[R][r] = *(const float4 *)(hk + (ty * RY + r + M) * SX + tx * 4 + M);
+        if (it < 2 * M) return true;
+
+        const int o = it - 2 * M, j = za + o;
+        if (!mbar_wait(bar_p + o % SP, (o / SP) & 1)) {
+            atomicExch(abort_flag, 1);
+            return true;
+        }
+        const float *hj = (const float *)(halo + ((it - M) % SH) * C::HALO_STRIDE);
+        const float *ta = (const float *)(pw + (o % SP) * C::PW_STRIDE);
+        const float *tb = ta + TX * C::TY;
+        const float sz = MODE == kModeStep ? p->sig_z[j] : 0.0f;
+
+        // y: rows ty*RY .. ty*RY + 2M + RY - 1 of the halo tile, two accumulators per half
+        float2 ya[RY][2], yb[RY][2];
+        float4 ctr[RY];
+#pragma unroll
+        for (int r = 0; r < RY; ++r) ya[r][0] = ya[r][1] = yb[r][0] = yb[r][1] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < 2 * M + RY; ++t) {
+            const float4 v = *(const float4 *)(hj + (ty * RY + t) * SX + tx * 4 + M);
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+                const int d = t - M - r;
+                if (d == 0) {
+                    ctr[r] = v;
+                } else if (d >= -M && d <= M) {
+                    const float2 cc = p->cy2[d < 0 ? -d : d];
+                    if (t & 1) {
+                        ya[r][0] = __ffma2_rn(cc, lo2(v), ya[r][0]);
+                        ya[r][1] = __ffma2_rn(cc, hi2(v), ya[r][1]);
+                    } else {
+                        yb[r][0] = __ffma2_rn(cc, lo2(v), yb[r][0]);
+                        yb[r][1] = __ffma2_rn(cc, hi2(v), yb[r][1]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            // x window: halo columns tx*4 .. tx*4 + 4 + 2M - 1 of this row
+            float w[4 + 2 * M];
+            const float *row = hj + (ty * RY + r + M) * SX + tx * 4;
+#pragma unroll
+            for (int c4 = 0; c4 < (4 + 2 * M) / 4; ++c4) {
+                const float4 v = (c4 == M / 4) ? ctr[r] : *(const float4 *)(row + 4 * c4);
+                w[4 * c4] = v.x;
+                w[4 * c4 + 1] = v.y;
+                w[4 * c4 + 2] = v.z;
+                w[4 * c4 + 3] = v.w;
+            }
+            float lx[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+                for (int k = 1; k <= M; ++k) {
+                    const float s = w[M + e + k] + w[M + e - k];
+                    if (k & 1) a0 = fmaf(p->cx[k], s, a0);
+                    else a1 = fmaf(p->cx[k], s, a1);
+                }
+                lx[e] = a0 + a1;
+            }
+            // z from the register queue: plane j +- k sits in slot (R + 1 + M +- k) % Q
+            float2 za0 = make_float2(0.f, 0.f), za1 = za0, zb0 = za0, zb1 = za0;
+#pragma unroll
+            for (int k = 1; k <= M; ++k) {
+                const float4 up = q[(R + 1 + M + k) % Q][r], dn = q[(R + 1 + M - k) % Q][r];
+                const float2 cc = p->cz2[k];
+                if (k & 1) {
+                    za0 = __ffma2_rn(cc, __fadd2_rn(lo2(up), lo2(dn)), za0);
+                    za1 = __ffma2_rn(cc, __fadd2_rn(hi2(up), hi2(dn)), za1);
+                } else {
+                    zb0 = __ffma2_rn(cc, __fadd2_rn(lo2(up), lo2(dn)), zb0);
+                    zb1 = __ffma2_rn(cc, __fadd2_rn(hi2(up), hi2(dn)), zb1);
+                }
+            }
+            const float4 cz4 = q[(R + 1 + M) % Q][r];
+            const float2 c0 = p->c02;
+            const float2 s0 = __fadd2_rn(__fadd2_rn(za0, zb0), __fadd2_rn(ya[r][0], yb[r][0]));
+            const float2 s1 = __fadd2_rn(__fadd2_rn(za1, zb1), __fadd2_rn(ya[r][1], yb[r][1]));
+            const float2 l0 = __ffma2_rn(c0, lo2(cz4), __fadd2_rn(s0, make_float2(lx[0], lx[1])));
+            const float2 l1 = __ffma2_rn(c0, hi2(cz4), __fadd2_rn(s1, make_float2(lx[2], lx[3])));
+
+            const int y = y0 + r;
+            const float4 A = *(const float4 *)(ta + (ty * RY + r) * TX + tx * 4);
+            const float4 B = *(const float4 *)(tb + (ty * RY + r) * TX + tx * 4);
+            const int64_t base = (int64_t)j * p->plane + (int64_t)y * p->px + x0;
+            float4 out;
+            if (MODE == kModeStep) {
+                // A = prev, B = W:  out = (2c + W lap - (1 - s) prev) / (1 + s)
+                const float2 two = make_float2(2.0f, 2.0f);
+                const float2 r0 = __ffma2_rn(lo2(B), l0, __fmul2_rn(two, lo2(cz4)));
+                const float2 r1 = __ffma2_rn(hi2(B), l1, __fmul2_rn(two, hi2(cz4)));
+                float rhs[4] = {r0.x, r0.y, r1.x, r1.y};
+                const float pv[4] = {A.x, A.y, A.z, A.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float s = sxp[e] + syr[r] + sz;
+                    float v = fmaf(s - 1.0f, pv[e], rhs[e]);
+                    if (j == src_j && r == src_r && e == src_e) v += srcv;
+                    rhs[e] = __fdividef(v, 1.0f + s);
+                }
+                out = make_float4(rhs[0], rhs[1], rhs[2], rhs[3]);
+            } else {
+                // A = aux (mu^{m+1}), B = g
+                const float2 g0 = __ffma2_rn(lo2(A), l0, lo2(B));
+                const float2 g1 = __ffma2_rn(hi2(A), l1, hi2(B));
+                out = make_float4(g0.x, g0.y, g1.x, g1.y);
+            }
+            if (xin && y < p->ny) *(float4 *)(p->out + sb + base) = out;
+        }
+        return true;
+    }
+
+    template <int... Rs>
+    __device__ __forceinline__ bool cycle(int base, std::integer_sequence<int, Rs...>)
+    {
+        return (... && plane<Rs>(base + Rs));
+    }
+};
+
+template <int M, int TY, int RY, int P, int MODE, bool UNR>
+__global__ void __launch_bounds__(Cfg<M, TY, RY, P>::NT, (M == 4 ? 2 : 1))
+k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUtensorMap map_c,
+             const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b)
+{
+    using C = Cfg<M, TY, RY, P>;
+    constexpr int Q = C::Q;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+
+    Ctx<C, MODE> c;
+    c.p = &p;
+    c.mc = &map_c;
+    c.ma = &map_a;
+    c.mb = &map_b;
+    c.halo = smem;
+    c.pw = smem + C::SH * C::HALO_STRIDE;
+    c.bar_h = (uint64_t *)(c.pw + C::SP * C::PW_STRIDE);
+    c.bar_p = c.bar_h + C::SH;
+    c.abort_flag = (int *)(c.bar_p + C::SP);
+    c.tid = threadIdx.x;
+    c.tx = c.tid % C::NTX;
+    c.ty = c.tid / C::NTX;
+
+    if (c.tid == 0) {
+        for (int i = 0; i < C::SH; ++i) mbar_init(c.bar_h + i, 1);
+        for (int i = 0; i < C::SP; ++i) mbar_init(c.bar_p + i, 1);
+        *c.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const int tiles_x = (p.nx + C::TX - 1) / C::TX;
+    c.bx = blockIdx.x % tiles_x;
+    c.by = blockIdx.x / tiles_x;
+    c.shot = blockIdx.z;
+    c.za = blockIdx.y * p.zchunk;
+    const int zb = min(p.nz, c.za + p.zchunk);
+    if (c.za >= zb) return;
+    c.nout = zb - c.za;
+    c.niter = c.nout + 2 * M;
+    c.x0 = c.bx * C::TX + c.tx * C::RX;
+    c.y0 = c.by * C::TY + c.ty * RY;
+    c.hx = c.bx * C::TX - M;
+    c.hy = c.by * C::TY - M;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) c.sxp[e] = (c.x0 + e < p.nx) ? p.sig_x[c.x0 + e] : 0.0f;
+#pragma unroll
+    for (int r = 0; r < RY; ++r) c.syr[r] = (c.y0 + r < p.ny) ? p.sig_y[c.y0 + r] : 0.0f;
+    c.xin = c.x0 < p.nx;
+    c.sb = (int64_t)c.shot * p.field;
+    c.src_j = -1;
+    c.src_r = c.src_e = 0;
+    c.srcv = 0.0f;
+    if (MODE == kModeStep && p.src_off) {
+        const int64_t s = p.src_off[c.shot];
+        const int sz = (int)(s / p.plane), rem = (int)(s - (int64_t)sz * p.plane);
+        const int sy = rem / p.px, sx = rem - sy * p.px;
+        if (sy >= c.y0 && sy < c.y0 + RY && sx >= c.x0 && sx < c.x0 + 4) {
+            c.src_j = sz;
+            c.src_r = sy - c.y0;
+            c.src_e = sx - c.x0;
+            c.srcv = p.dt2 * p.wavelet[(int64_t)c.shot * p.nt + p.n];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+#pragma unroll
+        for (int r = 0; r < RY; ++r) c.q[i][r] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    c.h_issued = C::P < c.niter ? C::P : c.niter;
+    c.cur_it = 0;
+    c.p_issued = 0;
+    if (c.tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int it = 0; it < C::P && it < c.niter; ++it) c.issue_halo(it);
+    }
+
+    int it = 0;
+    if (UNR) {
+        for (; it < c.niter; it += Q)
+            if (!c.cycle(it, std::make_integer_sequence<int, Q>{})) break;
+    } else {
+        for (; it < c.niter; ++it) {
+#pragma unroll
+            for (int i = 0; i < Q - 1; ++i)
+#pragma unroll
+                for (int r = 0; r < RY; ++r) c.q[i][r] = c.q[i + 1][r];
+            if (!c.plane<Q - 1>(it)) break;
+        }
+    }
+    if (*(volatile int *)c.abort_flag && c.tid == 0) {
+        // a bounded wait gave up in iteration cur_it - 1 (seen by all in cur_it): report,
+        // then give the copies issued and not yet consumed a bounded chance to land before
+        // the CTA's shared memory is released
+        atomicOr(p.err, 2u);
+        const int failed = c.cur_it - 1 > 0 ? c.cur_it - 1 : 0;
+        for (int k = failed; k < c.h_issued; ++k)
+            (void)mbar_wait(c.bar_h + k % C::SH, (k / C::SH) & 1);
+        for (int o = failed - 2 * M > 0 ? failed - 2 * M : 0; o < c.p_issued; ++o)
+            (void)mbar_wait(c.bar_p + o % C::SP, (o / C::SP) & 1);
+    }
+}
+
+}  // namespace s3d
+}  // namespace fwi

@@ -1,0 +1,29 @@
+// Radius-8 (16th-order) instantiations of the TMA-staged 3-D step kernel.
+#include "k_step3d.cuh"
+
+namespace fwi {
+
+namespace {
+template <int TY, int RY, int P, bool UNR>
+Step3dKernelInfo info(int mode)
+{
+    using C = s3d::Cfg<8, TY, RY, P>;
+    Step3dKernelInfo k;
+    k.fn = mode == kModeStep ? (Step3dKernel)s3d::k_step3d_tma<8, TY, RY, P, kModeStep, UNR>
+                             : (Step3dKernel)s3d::k_step3d_tma<8, TY, RY, P, kModeImage, UNR>;
+    k.threads = C::NT;
+    k.smem = C::SMEM;
+    return k;
+}
+}  // namespace
+
+Step3dKernelInfo step3d_kernel_m8(const Step3dVariant &v, int mode)
+{
+    if (v.ty == 32 && v.ry == 1 && v.pf == 2 && v.unroll) return info<32, 1, 2, true>(mode);
+    if (v.ty == 32 && v.ry == 1 && v.pf == 2 && !v.unroll) return info<32, 1, 2, false>(mode);
+    if (v.ty == 32 && v.ry == 2 && v.pf == 2 && v.unroll) return info<32, 2, 2, true>(mode);
+    if (v.ty == 32 && v.ry == 2 && v.pf == 2 && !v.unroll) return info<32, 2, 2, false>(mode);
+    return Step3dKernelInfo{nullptr, 0, 0};
+}
+
+}  // namespace fwi

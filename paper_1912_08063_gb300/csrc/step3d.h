@@ -1,0 +1,71 @@
+// Parameters and launchers of the TMA-staged 3-D step kernel (k_step3d.cu) and its
+// host-side tensor-map helpers (tmap.cpp).  Internal to libfwi.
+#pragma once
+
+#include <cuda.h>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fwi_internal.h"
+
+namespace fwi {
+
+constexpr int kModeStep = 0;    // out = damped leapfrog update, written over prev
+constexpr int kModeImage = 1;   // g += aux * (L c)
+
+struct Step3dParams {
+    int M;
+    int nx, ny, nz, px;           // computed extents and row pitch (floats)
+    int64_t plane, field;         // floats per z-plane and per shot
+    int zchunk;                   // output planes per CTA
+    float cx[kMaxM + 1], cy[kMaxM + 1], cz[kMaxM + 1], c0;
+    float2 cy2[kMaxM + 1], cz2[kMaxM + 1], c02;   // the same weights as packed pairs
+    const float *sig_x, *sig_y, *sig_z;
+    float *out;                   // kModeStep: prev (in place); kModeImage: g
+    const int64_t *src_off;       // kModeStep only, may be null
+    const float *wavelet;
+    int nt, n;
+    float dt2;
+    unsigned *err;                // status word: bit 1 (value 2) = a bounded wait gave up
+};
+
+// Kernel configurations of the 3-D step: tile height, points per thread along y,
+// prefetch depth and whether the plane loop is unrolled to rotate the z-queue at compile
+// time.  step3d_variant() picks the configuration used for radius M.
+struct Step3dVariant {
+    int ty, ry, pf;
+    bool unroll;
+};
+Step3dVariant step3d_variant(int M);
+int step3d_smem_bytes(int M);
+int step3d_threads(int M);
+// Resident CTAs of the 3-D step kernel on the current device (SMs x CTAs per SM).
+int step3d_resident_ctas(int M);
+
+// map_c: 4-D [shot][z][y][x] map of the streamed field with the halo box;
+// map_a/map_b: maps of the pointwise fields with the 64 x TY tile box
+// (kModeStep: prev, W; kModeImage: aux, g).  W's map has a shot extent of 1.
+cudaError_t launch_step3d_tma(const Step3dParams &p, int nshots, int mode, int nchunks,
+                              const CUtensorMap &map_c, const CUtensorMap &map_a,
+                              const CUtensorMap &map_b, cudaStream_t s);
+
+// Per-radius pieces behind the dispatch (k_step3d_m4.cu, k_step3d_m8.cu).
+typedef void (*Step3dKernel)(const Step3dParams, const CUtensorMap, const CUtensorMap,
+                             const CUtensorMap);
+struct Step3dKernelInfo {
+    Step3dKernel fn;
+    int threads, smem;
+};
+Step3dKernelInfo step3d_kernel_m4(const Step3dVariant &v, int mode);
+Step3dKernelInfo step3d_kernel_m8(const Step3dVariant &v, int mode);
+
+// Encodes a 4-D FP32 tensor map over shots of a field laid out as in Geom, with box
+// (bx, by, 1, 1) and zero fill outside [0, nx) x [0, ny) x [0, nz) x [0, nshots).
+int encode_field_map(CUtensorMap *map, const void *base, const Geom &g, int nshots, int bx,
+                     int by);
+
+// Number of z-chunks per (tile, shot) that best fills whole waves of resident CTAs,
+// weighing the 2M warm-up planes each chunk adds.
+int plan_zchunks(int nz, int M, int tiles_per_shot, int nshots, int resident_ctas);
+
+}  // namespace fwi

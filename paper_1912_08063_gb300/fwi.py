@@ -317,3 +317,41 @@ class FwiModel:
         x = torch.empty((acq.nshots, self.nt), dtype=torch.float32, device=y.device)
         fwi_source_adjoint(self.handle, acq.c, y, x, stream)
         return x
+
+
+def _autograd_function():
+    import torch
+
+    class WaveFwi(torch.autograd.Function):
+        """misfit = WaveFwi.apply(v, model, acq, wavelets, d_obs)
+
+        Forward: installs v in the model and runs ``fwi_adjoint_gradient`` once, which
+        returns the misfit (Eq. 1) and its exact gradient; the gradient is kept for the
+        backward pass, which only scales it by the incoming gradient.  v is the physical
+        velocity grid (float32, CUDA)."""
+
+        @staticmethod
+        def forward(ctx, v, model, acq, wavelets, d_obs):
+            model.update_velocity(v.detach().contiguous())
+            phi, grad = model.gradient(acq, wavelets, d_obs)
+            ctx.save_for_backward(grad)
+            return phi.to(torch.float32).reshape(())
+
+        @staticmethod
+        def backward(ctx, gout):
+            (grad,) = ctx.saved_tensors
+            return gout * grad, None, None, None, None
+
+    return WaveFwi
+
+
+_wavefwi = None
+
+
+def __getattr__(name):
+    global _wavefwi
+    if name == "WaveFwi":
+        if _wavefwi is None:
+            _wavefwi = _autograd_function()
+        return _wavefwi
+    raise AttributeError(name)

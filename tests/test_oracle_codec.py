@@ -68,14 +68,21 @@ def test_snapshot_scale_is_largest_power_of_two(dtype, T):
 
 @pytest.mark.parametrize("dtype,rel", [("fp16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
 def test_snapshot_roundtrip_error_bound(dtype, rel):
+    """a comes back to the format's relative precision; the difference a - b (the part of
+    the state that drives the time stepping) comes back to its own relative precision,
+    although it is ten times smaller than a."""
     rng = np.random.default_rng(3)
     a = (rng.standard_normal(5000) * 3e-5).astype(np.float32)
-    b = (rng.standard_normal(5000) * 1e-5).astype(np.float32)
+    b = (a - rng.standard_normal(5000) * 3e-6).astype(np.float32)
     code, s = oracle.snap_encode(a, b, dtype)
     ra, rb = oracle.snap_decode(code, s, dtype)
-    mx = max(np.abs(a).max(), np.abs(b).max())
+    d, rd = (a - b).astype(np.float64), (ra - rb).astype(np.float64)
+    T = 2.0 ** 14 if dtype == "fp16" else 1.0
     # relative error of a normal number, plus the absolute floor of the format's subnormals
-    floor = (2.0 ** -24 if dtype == "fp16" else 0.0) / s
-    assert np.all(np.abs(ra - a) <= rel * np.abs(a) + floor)
-    assert np.all(np.abs(rb - b) <= rel * np.abs(b) + floor)
-    assert mx * s <= (2.0 ** 14 if dtype == "fp16" else 1.0)
+    fa = (2.0 ** -24 if dtype == "fp16" else 0.0) / s[0]
+    fd = (2.0 ** -24 if dtype == "fp16" else 0.0) / s[1]
+    assert np.all(np.abs(ra - a) <= rel * np.abs(a) + fa)
+    # the decoded difference is (a' - (a' - d')) in FP32: one extra rounding of size |a| eps
+    assert np.all(np.abs(rd - d) <= rel * np.abs(d) + fd + 2.0 ** -23 * np.abs(a) * 2)
+    assert np.abs(a).max() * s[0] <= T and np.abs(d).max() * s[1] <= T
+    assert s[1] >= 8 * s[0]   # the difference gets a finer scale

@@ -27,7 +27,7 @@ def fwi():
     return f
 
 
-def make_pair(w, vref=4600.0, snap="fp32", budget=0, nb=None, v=None):
+def make_pair(w, vref=4600.0, snap="fp32", budget=0, nb=None, v=None, order=None):
     f = fwi()
     nb = w.nb if nb is None else nb
     v = w.v if v is None else v
@@ -138,12 +138,12 @@ def test_codec_bit_exact(dtype):
     b = (rng.standard_normal(n) * 1e-6).astype(np.float32)
     a[:5] = [0.0, -0.0, 1e-30, -2.0 ** -20, 3.3e-3]
     code = torch.zeros(2 * n, dtype=torch.int16, device="cuda")
-    sc = torch.zeros(1, dtype=torch.float32, device="cuda")
+    sc = torch.zeros(2, dtype=torch.float32, device="cuda")
     ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
     dt_id = {"bf16": 1, "fp16": 2}[dtype]
     f.fwi_snapshot_encode(ta, tb, n, dt_id, code, sc)
     rcode, rs = oracle.snap_encode(a, b, dtype)
-    assert sc.item() == rs
+    assert np.array_equal(sc.cpu().numpy(), rs)
     assert np.array_equal(code.cpu().numpy().view(np.uint16).reshape(2, n), rcode)
     da, db = torch.empty_like(ta), torch.empty_like(tb)
     f.fwi_snapshot_decode(code, sc, n, dt_id, da, db)
@@ -172,14 +172,17 @@ def test_source_dot_product_gpu(ndim, shape, order):
     assert rel(Fty, ref) <= TOL_FWD
 
 
-def _grad_case(ndim, shape, order, nt=70, nb=5, seed=13, nshots=1):
+def _grad_case(ndim, shape, order, nt=70, nb=5, seed=13, nshots=1, f0=20.0):
     rng = np.random.default_rng(seed)
-    w = synth.random_small(rng, ndim, shape, nt=nt, order=order, nb=nb, nrec=12)
+    w = synth.random_small(rng, ndim, shape, nt=nt, order=order, nb=nb, nrec=12, f0=f0)
     if nshots > 1:
         src = np.repeat(w.src, nshots, 0)
         src[:, -1] = rng.integers(0, shape[-1], nshots)
         w.src = src
-    vobs = (w.v * (1.0 + 0.05 * synth.gaussian_random_field(rng, w.v.shape, w.h, 40.0, 1.0)))
+    # observed data from a model 10 % slower with 5 % random variations: the residual is
+    # a sizeable fraction of the data, as in an FWI iteration (a residual of ~1 % of the
+    # data would turn FP32 rounding of the traces into ~1e-4 misfit differences)
+    vobs = w.v * (0.9 + 0.05 * synth.gaussian_random_field(rng, w.v.shape, w.h, 40.0, 1.0))
     p_obs = oracle.Problem(vobs, w.h, w.dt, w.nt, order=order, nb=nb, vref=4600.0,
                            src=w.src, rec=w.rec, wavelet=w.wavelets())
     dobs = p_obs.forward().astype(np.float32)
@@ -194,9 +197,11 @@ def test_gradient_fp32_checkpoints(ndim, shape, order, nshots):
     phi, g = m.gradient(acq, torch.from_numpy(w.wavelets()).cuda(), torch.from_numpy(dobs).cuda())
     rphi, rg = p.gradient(dobs.astype(np.float64))
     e = rel(g.cpu().numpy(), rg)
-    print(f"grad fp32 {ndim}d o{order}: rel-L2 {e:.2e}, misfit rel {abs(phi.item()-rphi)/rphi:.2e}")
+    rr = np.sqrt(rphi) / np.linalg.norm(dobs)
+    print(f"grad fp32 {ndim}d o{order}: rel-L2 {e:.2e}, misfit rel "
+          f"{abs(phi.item() - rphi) / rphi:.2e}, |r|/|d_obs| {rr:.2f}")
     assert e <= TOL_GRAD32
-    assert abs(phi.item() - rphi) <= 1e-4 * rphi
+    assert abs(phi.item() - rphi) <= TOL_GRAD32 * rphi
 
 
 def test_gradient_independent_of_checkpoint_budget_fp32():
@@ -214,10 +219,72 @@ def test_gradient_independent_of_checkpoint_budget_fp32():
         assert np.array_equal(g, grads[0])
 
 
+def _config_case(w, nslots, snap):
+    """GPU and oracle gradients of workload w with nslots 16-bit checkpoints; d_obs from
+    the oracle on w.v_obs."""
+    vref = 4600.0
+    p_obs = oracle.Problem(w.v_obs, w.h, w.dt, w.nt, order=w.order, nb=w.nb, vref=vref,
+                           src=w.src, rec=w.rec, wavelet=w.wavelets())
+    dobs = p_obs.forward().astype(np.float32)
+    probe, _, _ = make_pair(w, snap=snap, budget=1, vref=vref)
+    pitch, comp = probe.info()["pitch_x"], probe.info()["computed"]
+    field = -(-comp[0] * comp[1] * pitch // 64) * 64
+    m, p, acq = make_pair(w, snap=snap, budget=nslots * 2 * 2 * field, vref=vref)
+    phi, g = m.gradient(acq, torch.from_numpy(w.wavelets()).cuda(), torch.from_numpy(dobs).cuda())
+    info = m.info()
+    rphi, rg = p.gradient(dobs.astype(np.float64))
+    return rel(g.cpu().numpy(), rg), info, abs(phi.item() - rphi) / rphi
+
+
+def test_gradient_layered_64_instance_bf16():
+    """64^3 instance of the 256^3 layered model (h 10 m, dt 0.8 ms, 8th order, 15 Hz,
+    receivers every 2nd cell on row 5), 300 steps, 20 BF16 checkpoints."""
+    w = synth.layered_3d(64, nt=300)
+    e, info, em = _config_case(w, 20, "bf16")
+    print(f"layered 64^3 bf16: grad rel-L2 {e:.2e}, misfit rel {em:.2e}, "
+          f"slots {info['snap_slots']}, forward steps {info['last_forward_steps']}")
+    assert info["snap_slots"] == 20 and info["last_forward_steps"] > w.nt
+    assert e <= TOL_GRAD16
+
+
+def test_gradient_salt_96_twin_fp16():
+    """96^3 twin of the 512^3 salt model (h and dt scaled by 512/96, 16th order, FP16
+    checkpoints), the first 250 steps, 12 checkpoints."""
+    w = synth.salt_3d(96)
+    w.nt = 250
+    e, info, em = _config_case(w, 12, "fp16")
+    print(f"salt 96^3 fp16: grad rel-L2 {e:.2e}, misfit rel {em:.2e}, "
+          f"slots {info['snap_slots']}, forward steps {info['last_forward_steps']}")
+    assert e <= TOL_GRAD16
+
+
+def test_autograd_matches_finite_difference():
+    """WaveFwi.apply/backward against a central difference of the GPU misfit (FP64
+    accumulated) along a smooth direction."""
+    f = fwi()
+    rng = np.random.default_rng(31)
+    w, dobs = _grad_case(2, (36, 44), 8, nt=120)
+    w.src[0, 2] = 20
+    m, _, acq = make_pair(w, snap="fp32")
+    wav = torch.from_numpy(w.wavelets()).cuda()
+    d = torch.from_numpy(dobs).cuda()
+    v = torch.from_numpy(w.v).cuda().requires_grad_(True)
+    phi = f.WaveFwi.apply(v, m, acq, wav, d)
+    phi.backward()
+    dv = torch.from_numpy(50.0 * synth.gaussian_random_field(rng, w.v.shape, w.h, 80.0, 1.0)).cuda()
+    eps = 1e-2
+    fp = f.WaveFwi.apply((v + eps * dv).detach(), m, acq, wav, d).item()
+    fm = f.WaveFwi.apply((v - eps * dv).detach(), m, acq, wav, d).item()
+    fd = (fp - fm) / (2 * eps)
+    an = float(torch.sum(v.grad.double() * dv.double()))
+    print(f"autograd FD: fd {fd:.6e} adjoint {an:.6e} rel {abs(fd - an) / abs(an):.2e}")
+    assert abs(fd - an) <= 1e-3 * abs(an)
+
+
 @pytest.mark.parametrize("snap", ["bf16", "fp16"])
 @pytest.mark.parametrize("ndim,shape,order", [(2, (40, 52), 8), (3, (15, 16, 18), 16)])
 def test_gradient_16bit_checkpoints(snap, ndim, shape, order):
-    w, dobs = _grad_case(ndim, shape, order, nt=90)
+    w, dobs = _grad_case(ndim, shape, order, nt=90, f0=10.0)
     probe, _, _ = make_pair(w, snap=snap, budget=1)
     pitch, comp = probe.info()["pitch_x"], probe.info()["computed"]
     field = -(-comp[0] * comp[1] * pitch // 64) * 64
