@@ -55,6 +55,12 @@ def parse():
     return ap.parse_args()
 
 
+def gpts_per_s(points, steps, seconds):
+    """Grid points updated per second, in billions: the Gcells/s of the paper's Table 1
+    (cells x steps / time)."""
+    return points * steps / seconds / 1e9
+
+
 def workload(name, nt_override, n=0):
     from paper_1912_08063_gb300 import synth
     if name == "salt_3d_512":
@@ -267,7 +273,7 @@ def main():
 
     pts = info1["points"]
     units = pts * w.nt * w.nshots
-    value = units * world / (ms * 1e-3) / 1e9
+    value = gpts_per_s(pts * w.nshots * world, w.nt, ms * 1e-3)
     fwd_n = info1["fwd_step_launches"] - info0["fwd_step_launches"]
     adj_n = info1["adj_step_launches"] - info0["adj_step_launches"]
     fwd_ms = info1["fwd_step_ms"] - info0["fwd_step_ms"]
@@ -311,7 +317,8 @@ def main():
         te = float(tt.item())
         h2d = v_h.numel() * 4 + wav_h.numel() * 4 + dobs_h.numel() * 4
         d2h = grad_h.numel() * 4 + 8
-        e2e = {"value": units * world / te / 1e9, "unit": "Gpts/s", "h2d_bytes_per_step": h2d,
+        e2e = {"value": gpts_per_s(pts * w.nshots * world, w.nt, te), "unit": "Gpts/s",
+               "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": te * 1e3, "misfit": float(phi_h[0])}
 
     cpu = None

@@ -13,7 +13,7 @@ namespace fwi {
 // tuning runs (only the instantiated combinations are accepted).
 Step3dVariant step3d_variant(int M)
 {
-    Step3dVariant v = M == 8 ? Step3dVariant{32, 1, 2, true} : Step3dVariant{16, 1, 3, true};
+    Step3dVariant v = M == 8 ? Step3dVariant{32, 2, 2, false} : Step3dVariant{16, 2, 3, false};
     if (const char *e = std::getenv("FWI_STEP3D_VARIANT")) {
         int ty, ry, pf, un;
         if (std::sscanf(e, "%d,%d,%d,%d", &ty, &ry, &pf, &un) == 4) {

@@ -4,13 +4,13 @@
 namespace fwi {
 
 namespace {
-template <int TY, int RY, int P, bool UNR>
+template <int TY, int RY, int P>
 Step3dKernelInfo info(int mode)
 {
     using C = s3d::Cfg<4, TY, RY, P>;
     Step3dKernelInfo k;
-    k.fn = mode == kModeStep ? (Step3dKernel)s3d::k_step3d_tma<4, TY, RY, P, kModeStep, UNR>
-                             : (Step3dKernel)s3d::k_step3d_tma<4, TY, RY, P, kModeImage, UNR>;
+    k.fn = mode == kModeStep ? (Step3dKernel)s3d::k_step3d_tma<4, TY, RY, P, kModeStep, false>
+                             : (Step3dKernel)s3d::k_step3d_tma<4, TY, RY, P, kModeImage, false>;
     k.threads = C::NT;
     k.smem = C::SMEM;
     return k;
@@ -19,10 +19,10 @@ Step3dKernelInfo info(int mode)
 
 Step3dKernelInfo step3d_kernel_m4(const Step3dVariant &v, int mode)
 {
-    if (v.ty == 16 && v.ry == 1 && v.pf == 3 && v.unroll) return info<16, 1, 3, true>(mode);
-    if (v.ty == 16 && v.ry == 1 && v.pf == 3 && !v.unroll) return info<16, 1, 3, false>(mode);
-    if (v.ty == 16 && v.ry == 2 && v.pf == 3 && v.unroll) return info<16, 2, 3, true>(mode);
-    if (v.ty == 16 && v.ry == 2 && v.pf == 3 && !v.unroll) return info<16, 2, 3, false>(mode);
+    if (v.unroll) return Step3dKernelInfo{nullptr, 0, 0};
+    if (v.ty == 16 && v.ry == 2 && v.pf == 3) return info<16, 2, 3>(mode);
+    if (v.ty == 16 && v.ry == 2 && v.pf == 4) return info<16, 2, 4>(mode);
+    if (v.ty == 32 && v.ry == 2 && v.pf == 3) return info<32, 2, 3>(mode);
     return Step3dKernelInfo{nullptr, 0, 0};
 }
 
