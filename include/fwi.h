@@ -149,6 +149,22 @@ int fwi_source_adjoint(fwi_model *m, const fwi_acq *acq, const float *y, float *
 int fwi_misfit(const float *d_mod, const float *d_obs, int64_t n, double *misfit_dev,
                cudaStream_t stream);
 
+/* The same misfit as fwi_misfit, for callers that cannot allocate device memory during
+ * the call: a framework that has reserved the device's memory for its own pool, or a
+ * latency-critical loop where an allocation call and its possible synchronisation are
+ * not allowed.  It allocates nothing: its block partial sums live in a fixed 32 KB
+ * array among the library's device globals, held by every device that loads the library
+ * until the process exits.  The paper has no counterpart; this is a deployment variant.
+ * Limits and rules: n <= 268435456 samples (4096 partials of 65536 samples); larger n
+ * returns FWI_ERR_ARG with a message and launches nothing.  The first call on each
+ * device looks up the array's device address (with that device current), so make that
+ * first call before any stream capture.  All calls share the array, so calls that
+ * overlap on the GPU (two streams of one device) race and must be ordered by the caller.
+ * The sum is deterministic; its summation order differs from fwi_misfit's, so the two
+ * agree to FP64 rounding, not bit for bit.  Device pointers; result in misfit_dev[0]. */
+int fwi_misfit_noalloc(const float *d_mod, const float *d_obs, int64_t n, double *misfit_dev,
+                       cudaStream_t stream);
+
 /* Checkpoint codec (device pointers) for a state pair (a, b) = (u^n, u^{n-1}) of n FP32
  * values.  FWI_SNAP_BF16 / FWI_SNAP_FP16 store the components a and d = a - b as 16-bit
  * codes (round to nearest even), each after scaling by its own

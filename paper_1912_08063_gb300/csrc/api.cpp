@@ -16,6 +16,7 @@
 
 namespace fwi {
 std::vector<int32_t> revolve_actions(int32_t nsteps, int32_t nslots, int64_t *n_forward);
+int report_error(int code, const std::string &msg);
 }
 
 using namespace fwi;
@@ -29,6 +30,13 @@ int fail(int code, const std::string &msg)
     g_err = msg;
     return code;
 }
+
+}  // namespace
+
+// Sets this thread's error message for entry points defined in other files.
+int fwi::report_error(int code, const std::string &msg) { return fail(code, msg); }
+
+namespace {
 
 #define FWI_CU(call)                                                                     \
     do {                                                                                 \

@@ -77,6 +77,7 @@ def lib():
                 "fwi_adjoint_gradient": ([P, P, P, P, P, P, P, P], c_i32),
                 "fwi_source_adjoint": ([P, P, P, P, P], c_i32),
                 "fwi_misfit": ([P, P, c_i64, P, P], c_i32),
+                "fwi_misfit_noalloc": ([P, P, c_i64, P, P], c_i32),
                 "fwi_snapshot_encode": ([P, P, c_i64, c_i32, P, P, P], c_i32),
                 "fwi_snapshot_decode": ([P, P, c_i64, c_i32, P, P, P], c_i32),
                 "fwi_revolve_schedule": ([c_i32, c_i32, P, c_i64, P, P], c_i32),
@@ -163,6 +164,11 @@ def fwi_source_adjoint(model, acq: fwi_acq, y, x, stream=None):
 def fwi_misfit(d_mod, d_obs, n, misfit_dev, stream=None):
     _check(lib().fwi_misfit(_ptr(d_mod), _ptr(d_obs), int(n), _ptr(misfit_dev),
                             _stream(stream)))
+
+
+def fwi_misfit_noalloc(d_mod, d_obs, n, misfit_dev, stream=None):
+    _check(lib().fwi_misfit_noalloc(_ptr(d_mod), _ptr(d_obs), int(n), _ptr(misfit_dev),
+                                    _stream(stream)))
 
 
 def fwi_snapshot_encode(a, b, n, dtype, code, scale, stream=None):
