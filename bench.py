@@ -72,12 +72,16 @@ def workload(name, nt_override, n=0):
     return w
 
 
+STEP3D_SOURCES = ["k_step3d.cuh", "k_step3d_m8.cu", "k_step3d_m4.cu", "k_step3d.cu", "step3d.h"]
+
+
 def kernel_source_hash():
+    """Hash of the 3-D step kernel's sources: a recorded DRAM traffic figure is reported
+    only while these are unchanged."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1912_08063_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in STEP3D_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 

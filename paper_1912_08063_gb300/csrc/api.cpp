@@ -164,6 +164,7 @@ struct fwi_model {
     // cached schedule
     int sched_nslots = -1;
     std::vector<int32_t> sched;
+    std::vector<int> sched_comps;   // per action: checkpoint components moved (1 or 2)
     int64_t sched_fwd = 0;
     // status
     unsigned *h_flag = nullptr, *d_flag = nullptr;
@@ -442,6 +443,7 @@ int step3d_launch(fwi_model *m, const StepParams &p, int ns, int mode, cudaStrea
         q.nt = p.nt;
         q.n = p.n;
         q.dt2 = p.dt2;
+        q.maxbits = p.maxbits;
     } else {
         FWI_TRY(field_map(m, p.u_img, ns, 64 + 2 * g.M, TY + 2 * g.M, &mc));
         FWI_TRY(field_map(m, p.cur, ns, 64, TY, &ma));
@@ -760,6 +762,31 @@ int fwi_adjoint_gradient(fwi_model *m, const fwi_acq *acq, const float *wavelets
     if (slots != m->sched_nslots) {
         m->sched = revolve_actions(nt, (int32_t)slots, &m->sched_fwd);
         m->sched_nslots = (int)slots;
+        // Components each checkpoint action moves: a restore followed by a reverse step
+        // needs u^m alone (the imaging pass reads only u^m; the following action is always
+        // another restore), and a checkpoint whose every restore is of that kind is
+        // stored as u^n alone.
+        const size_t na = m->sched.size() / 2;
+        m->sched_comps.assign(na, 2);
+        for (size_t i = 0; i < na; ++i) {
+            const int kind = m->sched[2 * i], arg = m->sched[2 * i + 1];
+            if (kind == 3 && arg >= 0 && i + 1 < na && m->sched[2 * (i + 1)] == 4)
+                m->sched_comps[i] = 1;
+        }
+        for (size_t i = 0; i < na; ++i) {
+            if (m->sched[2 * i] != 2) continue;
+            const int slot = m->sched[2 * i + 1];
+            int need = 1;
+            for (size_t k = i + 1; k < na; ++k) {
+                const int kk = m->sched[2 * k], aa = m->sched[2 * k + 1];
+                if (kk == 2 && aa == slot) break;
+                if (kk == 3 && aa == slot && m->sched_comps[k] == 2) {
+                    need = 2;
+                    break;
+                }
+            }
+            m->sched_comps[i] = need;
+        }
     }
     m->nslots = (int)slots;
     m->slot_bytes = per_slot;
@@ -789,13 +816,22 @@ int fwi_adjoint_gradient(fwi_model *m, const fwi_acq *acq, const float *wavelets
     int64_t nadj = 0, nfwd = 0, nstore = 0, nrestore = 0;
     const char *codes = m->snaps.as<char>();
 
-    for (size_t i = 0; i + 1 < m->sched.size(); i += 2) {
-        const int kind = m->sched[i], arg = m->sched[i + 1];
+    const bool fused_max = use_step3d(m);   // the 3-D step computes the checkpoint max-abs
+    const size_t nact = m->sched.size() / 2;
+    for (size_t ia = 0; ia < nact; ++ia) {
+        const int kind = m->sched[2 * ia], arg = m->sched[2 * ia + 1];
+        const int comps = m->sched_comps[ia];
+        const bool next_store = ia + 1 < nact && m->sched[2 * (ia + 1)] == 2;
         if (kind == 1) {   // ADVANCE
             for (int k = 0; k < arg; ++k) {
                 pf.cur = m->u[cur].as<float>();
                 pf.prev = m->u[1 - cur].as<float>();
                 pf.n = (int)step;
+                pf.maxbits = nullptr;
+                if (fused_max && next_store && k == arg - 1) {
+                    FWI_CU(cudaMemsetAsync(m->maxbits.p, 0, 2 * ns * sizeof(unsigned), s));
+                    pf.maxbits = m->maxbits.as<unsigned>();
+                }
                 FWI_TRY(step_launch(m, pf, ns, false, 0, s));
                 if (step >= recorded) {
                     FWI_LAUNCH(m, launch_sample(g, pf.prev, m->rec_off.as<int64_t>(), ns, nr, nt,
@@ -806,14 +842,17 @@ int fwi_adjoint_gradient(fwi_model *m, const fwi_acq *acq, const float *wavelets
                 ++step;
                 ++nfwd;
             }
-        } else if (kind == 2) {   // STORE the pair (u^step, u^{step-1})
-            FWI_CU(cudaMemsetAsync(m->maxbits.p, 0, 2 * ns * sizeof(unsigned), s));
-            FWI_LAUNCH(m, launch_maxabs(m->u[cur].as<float>(), m->u[1 - cur].as<float>(), g.field,
-                                 g.field, ns, m->maxbits.as<unsigned>(), s));
+        } else if (kind == 2) {   // STORE the pair (u^step, u^{step-1}), or u^step alone
+            const bool have_max = fused_max && ia > 0 && m->sched[2 * (ia - 1)] == 1;
+            if (!have_max) {
+                FWI_CU(cudaMemsetAsync(m->maxbits.p, 0, 2 * ns * sizeof(unsigned), s));
+                FWI_LAUNCH(m, launch_maxabs(m->u[cur].as<float>(), m->u[1 - cur].as<float>(),
+                                            g.field, g.field, ns, m->maxbits.as<unsigned>(), s));
+            }
             FWI_LAUNCH(m, launch_encode(m->u[cur].as<float>(), m->u[1 - cur].as<float>(), g.field,
                                  g.field, ns, m->opts.snap_dtype, m->maxbits.as<unsigned>(),
                                  (void *)(codes + (size_t)arg * per_slot), 2 * g.field,
-                                 m->scales.as<float>() + (size_t)arg * 2 * ns, m->d_flag, s));
+                                 m->scales.as<float>() + (size_t)arg * 2 * ns, m->d_flag, comps, s));
             slot_step[arg] = step;
             ++nstore;
         } else if (kind == 3) {   // RESTORE
@@ -826,7 +865,7 @@ int fwi_adjoint_gradient(fwi_model *m, const fwi_acq *acq, const float *wavelets
                 FWI_LAUNCH(m, launch_decode(codes + (size_t)arg * per_slot, 2 * g.field,
                                      m->scales.as<float>() + (size_t)arg * 2 * ns, g.field, g.field,
                                      ns, m->opts.snap_dtype, m->u[cur].as<float>(),
-                                     m->u[1 - cur].as<float>(), s));
+                                     m->u[1 - cur].as<float>(), comps, s));
                 step = slot_step[arg];
             }
             ++nrestore;
@@ -951,7 +990,7 @@ int fwi_snapshot_encode(const float *a, const float *b, int64_t n, int32_t dtype
     FWI_CU(cudaMallocAsync((void **)&mb, 2 * sizeof(unsigned), s));
     FWI_CU(cudaMemsetAsync(mb, 0, 2 * sizeof(unsigned), s));
     cudaError_t e = launch_maxabs(a, b, n, n, 1, mb, s);
-    if (e == cudaSuccess) e = launch_encode(a, b, n, n, 1, dtype, mb, code, 2 * n, scale, nullptr, s);
+    if (e == cudaSuccess) e = launch_encode(a, b, n, n, 1, dtype, mb, code, 2 * n, scale, nullptr, 2, s);
     cudaError_t e2 = cudaFreeAsync(mb, s);
     if (e != cudaSuccess || e2 != cudaSuccess)
         return fail(FWI_ERR_CUDA, std::string("encode: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
@@ -963,7 +1002,7 @@ int fwi_snapshot_decode(const void *code, const float *scale, int64_t n, int32_t
 {
     if (!a || !b || !code || !scale || n < 0 || dtype < 0 || dtype > 2)
         return fail(FWI_ERR_ARG, "bad argument");
-    FWI_CU(launch_decode(code, 2 * n, scale, n, n, 1, dtype, a, b, s));
+    FWI_CU(launch_decode(code, 2 * n, scale, n, n, 1, dtype, a, b, 2, s));
     return FWI_OK;
 }
 

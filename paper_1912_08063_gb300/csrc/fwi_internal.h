@@ -52,6 +52,8 @@ struct StepParams {
     float *gacc;              // imaging only: gradient accumulator
     int zchunk;               // planes per CTA along z
     int nzchunks;
+    unsigned *maxbits;        // 3-D TMA step only (nullable): checkpoint max-abs of the
+                              // new state pair, fused into the step
 };
 
 cudaError_t launch_step(const StepParams &p, int nshots, bool imaging, cudaStream_t s);
@@ -79,12 +81,14 @@ cudaError_t launch_misfit(const float *d, const float *dobs, float *r_out, int64
 int misfit_blocks(int64_t n);
 cudaError_t launch_maxabs(const float *a, const float *b, int64_t n, int64_t stride,
                           int nshots, unsigned *maxbits, cudaStream_t s);
+// comps = 2: the pair (a, b); comps = 1: a only (a checkpoint restored only for imaging)
 cudaError_t launch_encode(const float *a, const float *b, int64_t n, int64_t stride,
                           int nshots, int dtype, const unsigned *maxbits, void *code,
-                          int64_t code_stride, float *scale, unsigned *flag, cudaStream_t s);
+                          int64_t code_stride, float *scale, unsigned *flag, int comps,
+                          cudaStream_t s);
 cudaError_t launch_decode(const void *code, int64_t code_stride, const float *scale,
                           int64_t n, int64_t stride, int nshots, int dtype, float *a, float *b,
-                          cudaStream_t s);
+                          int comps, cudaStream_t s);
 cudaError_t launch_fold(float *g32, double *g64, int64_t n, cudaStream_t s);
 cudaError_t launch_finish(const Geom &g, int nb, const int64_t np[3], int nshots,
                           const double *g64, const float *v, float *grad32, double *grad64,

@@ -192,13 +192,31 @@ __device__ float snap_scale(unsigned mb, int dtype)
     return __int_as_float((k + 127) << 23);
 }
 
+// One value of the codec: FP32 copy, or x * scale rounded to the 16-bit format.
+__device__ __forceinline__ void put_code(void *code, int64_t i, int dtype, float x, float sc)
+{
+    if (dtype == 0) ((float *)code)[i] = x;
+    else if (dtype == 1) ((__nv_bfloat16 *)code)[i] = __float2bfloat16_rn(x * sc);
+    else ((__half *)code)[i] = __float2half_rn(x * sc);
+}
+
+__device__ __forceinline__ float get_code(const void *code, int64_t i, int dtype, float sc)
+{
+    if (dtype == 0) return ((const float *)code)[i];
+    if (dtype == 1) return __bfloat162float(((const __nv_bfloat16 *)code)[i]) / sc;
+    return __half2float(((const __half *)code)[i]) / sc;
+}
+
+// 16-bit formats store a = u^n and d = u^n - u^{n-1}, each with its own scale; FP32
+// stores the pair unchanged (lossless).  comps = 1 stores or restores a only (a
+// checkpoint that is only ever restored for an imaging step, which needs u^n alone).
+// VEC processes four values per thread (n a multiple of 4, 16-byte aligned fields).
+template <bool VEC>
 __global__ void k_encode(const float *__restrict__ a, const float *__restrict__ b, int64_t n,
                          int64_t stride, int dtype, const unsigned *__restrict__ maxbits,
                          void *__restrict__ code, int64_t cstride, float *__restrict__ scale,
-                         unsigned *flag)
+                         unsigned *flag, int comps)
 {
-    // 16-bit formats store a = u^n and d = u^n - u^{n-1}, each with its own scale; FP32
-    // stores the pair unchanged (lossless)
     const int s = blockIdx.y;
     const float sa = snap_scale(maxbits[2 * s], dtype);
     const float sd = snap_scale(maxbits[2 * s + 1], dtype);
@@ -208,48 +226,93 @@ __global__ void k_encode(const float *__restrict__ a, const float *__restrict__ 
         if (flag && maxbits[2 * s] >= 0x7f800000u) atomicOr(flag, 1u);
     }
     const float *pa = a + s * stride, *pb = b + s * stride;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float va = pa[i], vb = pb[i];
-        if (dtype == 0) {
-            float *c = (float *)code + s * cstride;
-            c[i] = va;
-            c[n + i] = vb;
-        } else if (dtype == 1) {
-            __nv_bfloat16 *c = (__nv_bfloat16 *)code + s * cstride;
-            c[i] = __float2bfloat16_rn(va * sa);
-            c[n + i] = __float2bfloat16_rn((va - vb) * sd);
-        } else {
-            __half *c = (__half *)code + s * cstride;
-            c[i] = __float2half_rn(va * sa);
-            c[n + i] = __float2half_rn((va - vb) * sd);
+    const int esz = dtype == 0 ? 4 : 2;
+    void *ca = (char *)code + (size_t)s * cstride * esz;
+    void *cd = (char *)ca + (size_t)n * esz;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    if (VEC) {
+        for (int64_t i4 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i4 < n / 4; i4 += step) {
+            const float4 va = ((const float4 *)pa)[i4];
+            float4 vb = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (comps == 2) vb = ((const float4 *)pb)[i4];
+            if (dtype == 0) {
+                ((float4 *)ca)[i4] = va;
+                if (comps == 2) ((float4 *)cd)[i4] = vb;
+                continue;
+            }
+            const float xa[4] = {va.x, va.y, va.z, va.w};
+            const float xd[4] = {va.x - vb.x, va.y - vb.y, va.z - vb.z, va.w - vb.w};
+            unsigned short ha[4], hd[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (dtype == 1) {
+                    ha[e] = __bfloat16_as_ushort(__float2bfloat16_rn(xa[e] * sa));
+                    hd[e] = __bfloat16_as_ushort(__float2bfloat16_rn(xd[e] * sd));
+                } else {
+                    ha[e] = __half_as_ushort(__float2half_rn(xa[e] * sa));
+                    hd[e] = __half_as_ushort(__float2half_rn(xd[e] * sd));
+                }
+            }
+            ((ushort4 *)ca)[i4] = make_ushort4(ha[0], ha[1], ha[2], ha[3]);
+            if (comps == 2) ((ushort4 *)cd)[i4] = make_ushort4(hd[0], hd[1], hd[2], hd[3]);
+        }
+    } else {
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += step) {
+            const float va = pa[i];
+            put_code(ca, i, dtype, va, sa);
+            if (comps == 2) {
+                const float vb = pb[i];
+                put_code(cd, i, dtype, dtype == 0 ? vb : va - vb, sd);
+            }
         }
     }
 }
 
+template <bool VEC>
 __global__ void k_decode(const void *__restrict__ code, int64_t cstride,
                          const float *__restrict__ scale, int64_t n, int64_t stride, int dtype,
-                         float *__restrict__ a, float *__restrict__ b)
+                         float *__restrict__ a, float *__restrict__ b, int comps)
 {
     const int s = blockIdx.y;
     const float sa = scale[2 * s], sd = scale[2 * s + 1];
     float *pa = a + s * stride, *pb = b + s * stride;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        if (dtype == 0) {
-            const float *c = (const float *)code + s * cstride;
-            pa[i] = c[i];
-            pb[i] = c[n + i];
-        } else if (dtype == 1) {
-            const __nv_bfloat16 *c = (const __nv_bfloat16 *)code + s * cstride;
-            const float va = __bfloat162float(c[i]) / sa;
+    const int esz = dtype == 0 ? 4 : 2;
+    const void *ca = (const char *)code + (size_t)s * cstride * esz;
+    const void *cd = (const char *)ca + (size_t)n * esz;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    if (VEC) {
+        for (int64_t i4 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i4 < n / 4; i4 += step) {
+            if (dtype == 0) {
+                ((float4 *)pa)[i4] = ((const float4 *)ca)[i4];
+                if (comps == 2) ((float4 *)pb)[i4] = ((const float4 *)cd)[i4];
+                continue;
+            }
+            const ushort4 ua = ((const ushort4 *)ca)[i4];
+            const unsigned short ha[4] = {ua.x, ua.y, ua.z, ua.w};
+            float xa[4], xb[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                xa[e] = (dtype == 1 ? __bfloat162float(__ushort_as_bfloat16(ha[e]))
+                                    : __half2float(__ushort_as_half(ha[e]))) / sa;
+            ((float4 *)pa)[i4] = make_float4(xa[0], xa[1], xa[2], xa[3]);
+            if (comps == 2) {
+                const ushort4 ud = ((const ushort4 *)cd)[i4];
+                const unsigned short hd[4] = {ud.x, ud.y, ud.z, ud.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    xb[e] = xa[e] - (dtype == 1 ? __bfloat162float(__ushort_as_bfloat16(hd[e]))
+                                                : __half2float(__ushort_as_half(hd[e]))) / sd;
+                ((float4 *)pb)[i4] = make_float4(xb[0], xb[1], xb[2], xb[3]);
+            }
+        }
+    } else {
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += step) {
+            const float va = get_code(ca, i, dtype, sa);
             pa[i] = va;
-            pb[i] = va - __bfloat162float(c[n + i]) / sd;
-        } else {
-            const __half *c = (const __half *)code + s * cstride;
-            const float va = __half2float(c[i]) / sa;
-            pa[i] = va;
-            pb[i] = va - __half2float(c[n + i]) / sd;
+            if (comps == 2) {
+                const float v = get_code(cd, i, dtype, sd);
+                pb[i] = dtype == 0 ? v : va - v;
+            }
         }
     }
 }
@@ -376,22 +439,44 @@ cudaError_t launch_maxabs(const float *a, const float *b, int64_t n, int64_t str
     return cudaGetLastError();
 }
 
+static bool vec_ok(int64_t n, int64_t stride, int64_t code_stride, const void *x, const void *y,
+                   const void *code)
+{
+    auto al = [](const void *p, int k) { return ((uintptr_t)p % k) == 0; };
+    return n % 4 == 0 && stride % 4 == 0 && code_stride % 4 == 0 && al(x, 16) && al(y, 16) &&
+           al(code, 16);
+}
+
 cudaError_t launch_encode(const float *a, const float *b, int64_t n, int64_t stride,
                           int nshots, int dtype, const unsigned *maxbits, void *code,
-                          int64_t code_stride, float *scale, unsigned *flag, cudaStream_t s)
+                          int64_t code_stride, float *scale, unsigned *flag, int comps,
+                          cudaStream_t s)
 {
-    dim3 grid(blocks_for(n, 152 * 8), nshots);
-    k_encode<<<grid, kThreads, 0, s>>>(a, b, n, stride, dtype, maxbits, code, code_stride,
-                                       scale, flag);
+    if (vec_ok(n, stride, code_stride, a, b, code)) {
+        dim3 grid(blocks_for(n / 4, 152 * 8), nshots);
+        k_encode<true><<<grid, kThreads, 0, s>>>(a, b, n, stride, dtype, maxbits, code,
+                                                 code_stride, scale, flag, comps);
+    } else {
+        dim3 grid(blocks_for(n, 152 * 8), nshots);
+        k_encode<false><<<grid, kThreads, 0, s>>>(a, b, n, stride, dtype, maxbits, code,
+                                                  code_stride, scale, flag, comps);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_decode(const void *code, int64_t code_stride, const float *scale,
                           int64_t n, int64_t stride, int nshots, int dtype, float *a, float *b,
-                          cudaStream_t s)
+                          int comps, cudaStream_t s)
 {
-    dim3 grid(blocks_for(n, 152 * 8), nshots);
-    k_decode<<<grid, kThreads, 0, s>>>(code, code_stride, scale, n, stride, dtype, a, b);
+    if (vec_ok(n, stride, code_stride, a, b, code)) {
+        dim3 grid(blocks_for(n / 4, 152 * 8), nshots);
+        k_decode<true><<<grid, kThreads, 0, s>>>(code, code_stride, scale, n, stride, dtype, a,
+                                                 b, comps);
+    } else {
+        dim3 grid(blocks_for(n, 152 * 8), nshots);
+        k_decode<false><<<grid, kThreads, 0, s>>>(code, code_stride, scale, n, stride, dtype, a,
+                                                  b, comps);
+    }
     return cudaGetLastError();
 }
 

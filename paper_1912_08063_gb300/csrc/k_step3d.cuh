@@ -18,10 +18,13 @@
 //   * each thread computes 4 (x) x RY (y) points: the z-neighbours come from a register
 //     queue of 2M + 1 planes, the x/y-neighbours from the resident halo stage of the
 //     output plane (it arrived M planes earlier and the ring keeps it);
-//   * UNR = true unrolls the plane loop by 2M + 1 so that the register queue rotates at
-//     compile time (no register moves); y and z sums use packed FP32x2 FMAs and split
-//     accumulators;
+//   * y and z sums use packed FP32x2 FMAs and split accumulators (independent chains);
+//     the sponge division is a fast reciprocal, branch-free;
 //   * results are stored with 16-byte stores straight from registers.
+// Measured on GB300 (radius 8, 512^3): this layout beat a variant that unrolls the
+// plane loop so the queue rotates at compile time (larger code, slower) and a variant
+// that reads the forward z-neighbours from the resident stages instead of registers
+// (more shared-memory loads, slower).
 // DRAM traffic per point and step: c once (halo re-reads hit L2), two pointwise fields
 // once, one write: 16 bytes in either mode.
 #pragma once
@@ -118,6 +121,7 @@ struct Ctx {
     int64_t sb;
     int src_j, src_r, src_e;   // source node in this thread's block (src_j < 0: none)
     float srcv;
+    unsigned mxa, mxd;         // bits of max|out| and max|out - c| (p->maxbits set)
     float4 q[C::Q][C::RY];
 
     __device__ __forceinline__ void issue_halo(int it)
@@ -275,6 +279,15 @@ struct Ctx {
                     rhs[e] = __fdividef(v, 1.0f + s);
                 }
                 out = make_float4(rhs[0], rhs[1], rhs[2], rhs[3]);
+                if (p->maxbits) {
+                    // |x| as bits: unsigned order is magnitude order, NaN above infinity
+                    const float cz[4] = {cz4.x, cz4.y, cz4.z, cz4.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        mxa = max(mxa, __float_as_uint(rhs[e]) & 0x7fffffffu);
+                        mxd = max(mxd, __float_as_uint(rhs[e] - cz[e]) & 0x7fffffffu);
+                    }
+                }
             } else {
                 // A = aux (mu^{m+1}), B = g
                 const float2 g0 = __ffma2_rn(lo2(A), l0, lo2(B));
@@ -285,15 +298,9 @@ struct Ctx {
         }
         return true;
     }
-
-    template <int... Rs>
-    __device__ __forceinline__ bool cycle(int base, std::integer_sequence<int, Rs...>)
-    {
-        return (... && plane<Rs>(base + Rs));
-    }
 };
 
-template <int M, int TY, int RY, int P, int MODE, bool UNR>
+template <int M, int TY, int RY, int P, int MODE>
 __global__ void __launch_bounds__(Cfg<M, TY, RY, P>::NT, (M == 4 ? 2 : 1))
 k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUtensorMap map_c,
              const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b)
@@ -347,6 +354,7 @@ k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUt
     c.src_j = -1;
     c.src_r = c.src_e = 0;
     c.srcv = 0.0f;
+    c.mxa = c.mxd = 0u;
     if (MODE == kModeStep && p.src_off) {
         const int64_t s = p.src_off[c.shot];
         const int sz = (int)(s / p.plane), rem = (int)(s - (int64_t)sz * p.plane);
@@ -371,17 +379,21 @@ k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUt
         for (int it = 0; it < C::P && it < c.niter; ++it) c.issue_halo(it);
     }
 
-    int it = 0;
-    if (UNR) {
-        for (; it < c.niter; it += Q)
-            if (!c.cycle(it, std::make_integer_sequence<int, Q>{})) break;
-    } else {
-        for (; it < c.niter; ++it) {
+    for (int it = 0; it < c.niter; ++it) {
+        // shift the queue: slot Q - 1 receives the plane that arrives in this iteration
 #pragma unroll
-            for (int i = 0; i < Q - 1; ++i)
+        for (int i = 0; i < Q - 1; ++i)
 #pragma unroll
-                for (int r = 0; r < RY; ++r) c.q[i][r] = c.q[i + 1][r];
-            if (!c.plane<Q - 1>(it)) break;
+            for (int r = 0; r < RY; ++r) c.q[i][r] = c.q[i + 1][r];
+        if (!c.plane<Q - 1>(it)) break;
+    }
+    if (MODE == kModeStep && p.maxbits) {
+        // every thread reaches this point (the loop above has no early return)
+        const unsigned a = __reduce_max_sync(0xffffffffu, c.mxa);
+        const unsigned d = __reduce_max_sync(0xffffffffu, c.mxd);
+        if ((c.tid & 31) == 0) {
+            if (a) atomicMax(p.maxbits + 2 * c.shot, a);
+            if (d) atomicMax(p.maxbits + 2 * c.shot + 1, d);
         }
     }
     if (*(volatile int *)c.abort_flag && c.tid == 0) {

@@ -9,8 +9,8 @@ Step3dKernelInfo info(int mode)
 {
     using C = s3d::Cfg<4, TY, RY, P>;
     Step3dKernelInfo k;
-    k.fn = mode == kModeStep ? (Step3dKernel)s3d::k_step3d_tma<4, TY, RY, P, kModeStep, false>
-                             : (Step3dKernel)s3d::k_step3d_tma<4, TY, RY, P, kModeImage, false>;
+    k.fn = mode == kModeStep ? (Step3dKernel)s3d::k_step3d_tma<4, TY, RY, P, kModeStep>
+                             : (Step3dKernel)s3d::k_step3d_tma<4, TY, RY, P, kModeImage>;
     k.threads = C::NT;
     k.smem = C::SMEM;
     return k;

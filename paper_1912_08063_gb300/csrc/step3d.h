@@ -27,6 +27,9 @@ struct Step3dParams {
     int nt, n;
     float dt2;
     unsigned *err;                // status word: bit 1 (value 2) = a bounded wait gave up
+    unsigned *maxbits;            // kModeStep, nullable: per shot, raise [2s] to the bits of
+                                  // max|out| and [2s+1] to max|out - c| (the checkpoint
+                                  // codec's scales of the new state pair)
 };
 
 // Kernel configurations of the 3-D step: tile height, points per thread along y,
