@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=32)
     return ap.parse_args()
 
 
@@ -189,6 +192,96 @@ def cpu_baseline(w, sample_n=320, sample_nt=30):
             f"{sample_nt} steps); Gpts/s = points x steps / wall time")
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return pts * sample_nt / t / 1e9, t, desc, threads
+
+
+def serving_section(dev, n_req, seed=4):
+    """Serving workload (Poisson stream of forward/gradient requests, 75 % 2-D / 25 % 3-D,
+    sides 128..1024 / 64..192, nt 500..3000): closed-loop capacity with continuous batching
+    and one request at a time, then Poisson arrivals at 0.8 x the batched capacity."""
+    import math
+
+    import torch
+
+    from paper_1912_08063_gb300 import fwi, synth
+
+    def dt_for(ndim, h):
+        lim = 1.0 / fwi.fwi_cfl_number(ndim, 8, (h, h, h), 4500.0, 1.0)
+        return math.floor(0.8 * lim * 1e4) / 1e4
+
+    reqs = synth.serving_requests(n_req, dt_for, seed=seed)
+    for r in reqs:   # observed traces of gradient requests, before any timing
+        if r["kind"] == "gradient":
+            m = fwi.FwiModel(torch.from_numpy(r["v_obs"]).to(dev), r["h"], r["dt"], r["nt"])
+            acq = fwi.Acquisition([r["src"]], r["rec"])
+            r["d_obs"] = m.forward(acq, torch.from_numpy(r["wavelet"][None]).to(dev))[0].cpu().numpy()
+            m.close()
+    torch.cuda.synchronize()
+
+    def run(max_active, arrivals):
+        for r, a in zip(reqs, arrivals):
+            r["arrival"] = float(a)
+        t0 = time.perf_counter()
+        res, _ = fwi.fwi_serve(reqs, max_active=max_active, steps_per_turn=16, snap_slots=16)
+        wall = time.perf_counter() - t0
+        lat = np.array([x["t_done"] - a for x, a in zip(res, arrivals)])
+        ok = sum(1 for x in res if x["status"] == 0)
+        return ok / wall, lat, ok
+
+    zero = np.zeros(n_req)
+    cap_b, _, ok_b = run(16, zero)
+    cap_1, _, ok_1 = run(1, zero)
+    lam = 0.8 * cap_b
+    rng = np.random.default_rng(seed)
+    arr = np.cumsum(rng.exponential(1.0 / lam, n_req))
+    _, lat_b, _ = run(16, arr)
+    _, lat_1, _ = run(1, arr)
+    return {"requests": n_req, "completed": [ok_b, ok_1],
+            "shots_per_s": round(cap_b, 3), "shots_per_s_one_at_a_time": round(cap_1, 3),
+            "poisson_rate_per_s": round(lam, 3),
+            "p50_s": round(float(np.percentile(lat_b, 50)), 3),
+            "p99_s": round(float(np.percentile(lat_b, 99)), 3),
+            "p50_s_one_at_a_time": round(float(np.percentile(lat_1, 50)), 3),
+            "p99_s_one_at_a_time": round(float(np.percentile(lat_1, 99)), 3),
+            "workload": "serving mix: 75 % 2-D (128..1024)^2, 25 % 3-D (64..192)^3, nt 500..3000, "
+                        "half forward / half gradient (BF16 checkpoints), 8th order"}
+
+
+def batched_section(dev, nt=3000):
+    """64 shots of the 400 x 1024 faulted 2-D model: one batched gradient call (shots on
+    the grid's z launch dimension, FP64 gradient sum over shots) against 64 one-shot
+    calls of the same kernels."""
+    import torch
+
+    from paper_1912_08063_gb300 import fwi, synth
+
+    w = synth.faulted_2d(nt=nt)
+    acq = fwi.Acquisition(w.src, w.rec)
+    wav = torch.from_numpy(w.wavelets()).to(dev)
+    obs = fwi.FwiModel(torch.from_numpy(w.v_obs).to(dev), w.h, w.dt, w.nt, order=w.order,
+                       sponge_vref=4500.0)
+    dobs = obs.forward(acq, wav)
+    obs.close()
+    m = fwi.FwiModel(torch.from_numpy(w.v).to(dev), w.h, w.dt, w.nt, order=w.order,
+                     snap_dtype=w.snap_dtype, snap_budget_bytes=16 << 30, sponge_vref=4500.0)
+    m.gradient(acq, wav, dobs)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    phi, g = m.gradient(acq, wav, dobs)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    singles = [fwi.Acquisition(w.src[i:i + 1], w.rec) for i in range(w.nshots)]
+    t0 = time.perf_counter()
+    for i, a in enumerate(singles):
+        m.gradient(a, wav[i:i + 1], dobs[i:i + 1])
+    torch.cuda.synchronize()
+    t1 = time.perf_counter() - t0
+    pts = m.info()["points"]
+    m.close()
+    return {"workload": w.name, "shots": w.nshots, "nt": w.nt,
+            "shots_per_s": round(w.nshots / tb, 3),
+            "shots_per_s_per_shot_calls": round(w.nshots / t1, 3),
+            "gpts_per_s": round(gpts_per_s(pts * w.nshots, w.nt, tb), 2),
+            "seconds": round(tb, 3), "seconds_per_shot_calls": round(t1, 3)}
 
 
 def run_reference(args):
@@ -331,6 +424,14 @@ def main():
         cpu = {"value": g, "unit": "Gpts/s", "cores": threads, "kind": "oracle",
                "sample": desc, "seconds": round(tsec, 2)}
 
+    # the other two workloads of the metric, measured after the timed region
+    model.close()
+    serving = batched = None
+    if rank == 0 and not args.no_serving:
+        serving = serving_section(dev, args.serving_requests)
+    if rank == 0 and not args.no_batched:
+        batched = batched_section(dev)
+
     if rank == 0:
         line = {"metric": "Gpts/s fwd+adjoint", "value": round(value, 3), "unit": "Gpts/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -345,7 +446,8 @@ def main():
                            "l2": "inputs larger than L2 (each field >= 100 MB)",
                            "parallelism": f"replicas x{world}"},
                 "clocks": ck, "e2e": e2e, "gpu_launches": launches,
-                "roofline": roof, "cpu_baseline": cpu, "misfit": float(phi.item())}
+                "roofline": roof, "cpu_baseline": cpu, "misfit": float(phi.item()),
+                "serving": serving, "batched_2d": batched}
         print(json.dumps(line), flush=True)
     model.close()
     if world > 1:

@@ -202,6 +202,64 @@ double fwi_cfl_number(int32_t ndim, int32_t order, const float spacing[3], float
 
 int fwi_model_info(const fwi_model *m, fwi_info *out);
 
+/* ------------------------------------------------------------------ serving loop
+ * Continuous batching of independent forward and gradient requests on one GPU (a
+ * systems pattern around the paper's method: each request is one shot of Eq. 2-3 or
+ * one misfit gradient on its own grid).  Requests are admitted in arrival order as soon
+ * as they have arrived, a slot is free and their device-memory estimate fits in the
+ * budget's remainder; an admitted request owns a model (wavefields and checkpoints stay
+ * on the device) and a stream, and one host thread issues the admitted requests' time
+ * steps round-robin (steps_per_turn at a time, at most two turns in flight per request),
+ * so their work overlaps on the device.  Finished requests are retired and release
+ * their memory.  max_active = 1 serves one request at a time on the same kernels. */
+#define FWI_REQ_FORWARD  0
+#define FWI_REQ_GRADIENT 1
+
+typedef struct {
+    int32_t kind;               /* FWI_REQ_FORWARD or FWI_REQ_GRADIENT                  */
+    int32_t ndim;
+    int64_t shape[3];           /* physical (nz, ny, nx), ny = 1 in 2-D                 */
+    float   spacing[3];
+    float   dt;
+    int32_t nt;
+    int32_t order;              /* 8 or 16                                              */
+    int32_t snap_dtype;         /* checkpoint storage of gradient requests (FWI_SNAP_*) */
+    int32_t nrec;
+    int32_t src[3];             /* (iz, iy, ix)                                         */
+    int32_t reserved;
+    const float   *vp;          /* HOST physical velocity                               */
+    const float   *wavelet;     /* HOST [nt]                                            */
+    const int32_t *rec;         /* HOST [nrec][3]                                       */
+    const float   *d_obs;       /* HOST [nt][nrec] (gradient requests)                  */
+    float         *traces_out;  /* HOST [nt][nrec] (forward requests), nullable         */
+    float         *grad_out;    /* HOST physical grid (gradient requests), nullable     */
+    double  arrival;            /* seconds after the start of fwi_serve                 */
+} fwi_request;
+
+typedef struct {
+    int32_t status;             /* FWI_OK or the request's error code                   */
+    int32_t reserved;
+    double  misfit;             /* gradient requests (Eq. 1)                            */
+    double  t_admit, t_start, t_done;   /* seconds after the start of fwi_serve         */
+    int64_t device_bytes;       /* device memory the request's model held at admission  */
+    int64_t reserved_bytes;     /* what admission reserved for it from the budget       */
+} fwi_result;
+
+typedef struct {
+    int64_t hbm_budget_bytes;   /* device memory for admitted requests (0: 80 % free)   */
+    int32_t max_active;         /* admitted requests at once (default 16)               */
+    int32_t steps_per_turn;     /* time steps issued per request per turn (default 8)   */
+    int32_t snap_slots;         /* checkpoints per gradient request (default 8)         */
+    int32_t nb;                 /* sponge width (default 20)                            */
+} fwi_serve_opts;
+
+/* Runs the request stream to completion: waits for each arrival time, admits, steps and
+ * retires requests; results[i] belongs to reqs[i].  The host buffers of every request
+ * must stay valid for the whole call.  Returns FWI_OK once every request has a status
+ * (per-request failures are reported in results[i].status). */
+int fwi_serve(const fwi_request *reqs, int32_t n, const fwi_serve_opts *opts,
+              fwi_result *results);
+
 /* Waits for the model's last stream and returns its latched device status. */
 int fwi_sync_status(fwi_model *m);
 

@@ -537,31 +537,6 @@ int set_coefs(fwi_model *m)
     return FWI_OK;
 }
 
-// Forward sweep of nt steps from rest; traces to `tr` (device), or skipped when null.
-// On return u[cur] holds u^nt and u[1-cur] holds u^{nt-1}.
-int run_forward(fwi_model *m, int ns, int nr, const float *wav, float *tr, int *cur_out,
-                cudaStream_t s)
-{
-    const size_t fb = (size_t)m->g.field * sizeof(float);
-    FWI_CU(cudaMemsetAsync(m->u[0].p, 0, ns * fb, s));
-    FWI_CU(cudaMemsetAsync(m->u[1].p, 0, ns * fb, s));
-    StepParams p = base_params(m);
-    p.src_off = m->src_off.as<int64_t>();
-    p.wavelet = wav;
-    int cur = 0;
-    for (int n = 0; n < m->nt; ++n) {
-        p.cur = m->u[cur].as<float>();
-        p.prev = m->u[1 - cur].as<float>();
-        p.n = n;
-        FWI_TRY(step_launch(m, p, ns, false, 0, s));
-        if (tr)
-            FWI_LAUNCH(m, launch_sample(m->g, p.prev, m->rec_off.as<int64_t>(), ns, nr, m->nt, n, tr, s));
-        cur = 1 - cur;
-    }
-    *cur_out = cur;
-    return FWI_OK;
-}
-
 int finish_output(void *user, const void *dev, size_t bytes, bool host, cudaStream_t s)
 {
     if (!user || !host) return FWI_OK;
@@ -570,6 +545,376 @@ int finish_output(void *user, const void *dev, size_t bytes, bool host, cudaStre
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------- resumable executors
+//
+// A forward or gradient evaluation is a job: set-up, then advance() issues the next
+// `units` time steps' worth of launches on the job's stream (a unit is one forward or one
+// reverse step; checkpoint stores and restores ride along with the step they precede),
+// then finish() issues the result copies.  The C ABI runs a job to the end in one call;
+// the serving loop interleaves the jobs of many requests on their own streams.
+
+namespace fwi {
+
+struct FwdJob {
+    fwi_model *m = nullptr;
+    cudaStream_t s = nullptr;
+    int ns = 0, nr = 0;
+    StepParams p{};
+    float *tr = nullptr;    // device traces target (may be null)
+    int cur = 0, n = 0;
+};
+
+int fwd_setup(FwdJob &j, fwi_model *m, int ns, int nr, const float *wav, float *tr,
+              cudaStream_t s)
+{
+    j.m = m;
+    j.s = s;
+    j.ns = ns;
+    j.nr = nr;
+    j.tr = tr;
+    const size_t fb = (size_t)m->g.field * sizeof(float);
+    FWI_CU(cudaMemsetAsync(m->u[0].p, 0, ns * fb, s));
+    FWI_CU(cudaMemsetAsync(m->u[1].p, 0, ns * fb, s));
+    j.p = base_params(m);
+    j.p.src_off = m->src_off.as<int64_t>();
+    j.p.wavelet = wav;
+    j.cur = 0;
+    j.n = 0;
+    return FWI_OK;
+}
+
+// On completion u[cur] holds u^nt and u[1-cur] holds u^{nt-1}.
+int fwd_advance(FwdJob &j, int64_t units, bool *done)
+{
+    fwi_model *m = j.m;
+    for (int64_t u = 0; u < units && j.n < m->nt; ++u, ++j.n) {
+        j.p.cur = m->u[j.cur].as<float>();
+        j.p.prev = m->u[1 - j.cur].as<float>();
+        j.p.n = j.n;
+        FWI_TRY(step_launch(m, j.p, j.ns, false, 0, j.s));
+        if (j.tr)
+            FWI_LAUNCH(m, launch_sample(m->g, j.p.prev, m->rec_off.as<int64_t>(), j.ns, j.nr,
+                                        m->nt, j.n, j.tr, j.s));
+        j.cur = 1 - j.cur;
+    }
+    *done = j.n >= m->nt;
+    return FWI_OK;
+}
+
+struct GradJob {
+    fwi_model *m = nullptr;
+    cudaStream_t s = nullptr;
+    int ns = 0, nr = 0, nt = 0;
+    int64_t nfield = 0;
+    size_t fb = 0, per_slot = 0;
+    const void *dobs = nullptr;
+    StepParams pf{}, pa{};
+    float *tr = nullptr, *res = nullptr;
+    int cur = 0, mcur = 0;
+    int64_t step = 0, recorded = 0;
+    std::vector<int64_t> slot_step;
+    bool first_adj = true;
+    int64_t nadj = 0, nfwd = 0, nstore = 0, nrestore = 0;
+    const char *codes = nullptr;
+    bool fused_max = false;
+    size_t ia = 0;    // next schedule action
+    int kdone = 0;    // forward steps already issued of the current ADVANCE action
+};
+
+// Checkpoint slots for the budget, the schedule and its per-action component counts,
+// staging of the inputs, and the initial state.
+int grad_setup(GradJob &j, fwi_model *m, const fwi_acq *acq, const float *wavelets,
+               const float *d_obs, cudaStream_t s)
+{
+    j.m = m;
+    j.s = s;
+    const int ns = acq->nshots, nr = acq->nrec, nt = m->nt;
+    j.ns = ns;
+    j.nr = nr;
+    j.nt = nt;
+    FWI_TRY(ensure_workspace(m, acq, true, s));
+    const Geom &g = m->g;
+    j.nfield = (int64_t)ns * g.field;
+    j.fb = (size_t)g.field * sizeof(float);
+
+    // checkpoint slots: as many as the budget holds, never more than nt
+    const int esz = m->opts.snap_dtype == FWI_SNAP_FP32 ? 4 : 2;
+    const size_t per_slot = (size_t)ns * 2 * g.field * esz;
+    j.per_slot = per_slot;
+    int64_t budget = m->opts.snap_budget_bytes;
+    if (budget <= 0) {
+        size_t fr = 0, tot = 0;
+        FWI_CU(cudaMemGetInfo(&fr, &tot));
+        budget = (int64_t)(fr / 4);
+    }
+    int64_t slots = budget / (int64_t)per_slot;
+    if (slots > nt) slots = nt;
+    if (slots < 0) slots = 0;
+    if ((size_t)slots * per_slot > m->snaps.bytes) {
+        // shrink on failure rather than fail: fewer slots only cost recomputation
+        while (slots > 0 && m->snaps.ensure((size_t)slots * per_slot) != FWI_OK) slots /= 2;
+    }
+    FWI_TRY(m->scales.ensure((size_t)(slots > 0 ? slots : 1) * 2 * ns * sizeof(float)));
+    if (slots != m->sched_nslots) {
+        m->sched = revolve_actions(nt, (int32_t)slots, &m->sched_fwd);
+        m->sched_nslots = (int)slots;
+        // Components each checkpoint action moves: a restore followed by a reverse step
+        // needs u^m alone (the imaging pass reads only u^m; the following action is always
+        // another restore), and a checkpoint whose every restore is of that kind is
+        // stored as u^n alone.
+        const size_t na = m->sched.size() / 2;
+        m->sched_comps.assign(na, 2);
+        for (size_t i = 0; i < na; ++i) {
+            const int kind = m->sched[2 * i], arg = m->sched[2 * i + 1];
+            if (kind == 3 && arg >= 0 && i + 1 < na && m->sched[2 * (i + 1)] == 4)
+                m->sched_comps[i] = 1;
+        }
+        for (size_t i = 0; i < na; ++i) {
+            if (m->sched[2 * i] != 2) continue;
+            const int slot = m->sched[2 * i + 1];
+            int need = 1;
+            for (size_t k = i + 1; k < na; ++k) {
+                const int kk = m->sched[2 * k], aa = m->sched[2 * k + 1];
+                if (kk == 2 && aa == slot) break;
+                if (kk == 3 && aa == slot && m->sched_comps[k] == 2) {
+                    need = 2;
+                    break;
+                }
+            }
+            m->sched_comps[i] = need;
+        }
+    }
+    m->nslots = (int)slots;
+    m->slot_bytes = per_slot;
+
+    const void *wav;
+    FWI_TRY(stage_input(m, 0, wavelets, (size_t)ns * nt * sizeof(float), s, &wav));
+    FWI_TRY(stage_input(m, 1, d_obs, (size_t)ns * nt * nr * sizeof(float), s, &j.dobs));
+
+    // adjoint receiver injection factor 2 W / a+ (the adjoint source is 2 r for Eq. 1)
+    FWI_LAUNCH(m, launch_rec_scale(g, m->W.as<float>(), sig_z(m), sig_y(m), sig_x(m),
+                                   m->rec_off.as<int64_t>(), ns * nr, 2.0f, 0,
+                                   m->inj.as<float>(), s));
+    FWI_CU(cudaMemsetAsync(m->u[0].p, 0, ns * j.fb, s));
+    FWI_CU(cudaMemsetAsync(m->u[1].p, 0, ns * j.fb, s));
+    FWI_CU(cudaMemsetAsync(m->g32.p, 0, ns * j.fb, s));
+    FWI_CU(cudaMemsetAsync(m->g64.p, 0, ns * 2 * j.fb, s));
+
+    j.pf = base_params(m);
+    j.pf.src_off = m->src_off.as<int64_t>();
+    j.pf.wavelet = (const float *)wav;
+    j.pa = base_params(m);   // reverse sweep: no source, receivers injected after each step
+    j.tr = m->traces.as<float>();
+    j.res = j.tr;            // residuals replace the traces in place
+    j.slot_step.assign(slots > 0 ? slots : 1, -1);
+    j.codes = m->snaps.as<char>();
+    j.fused_max = use_step3d(m);   // the 3-D step computes the checkpoint max-abs
+    return FWI_OK;
+}
+
+int grad_advance(GradJob &j, int64_t units, bool *done)
+{
+    fwi_model *m = j.m;
+    const Geom &g = m->g;
+    const cudaStream_t s = j.s;
+    const int ns = j.ns, nr = j.nr, nt = j.nt;
+    const size_t nact = m->sched.size() / 2;
+    int64_t used = 0;
+    while (j.ia < nact && used < units) {
+        const size_t ia = j.ia;
+        const int kind = m->sched[2 * ia], arg = m->sched[2 * ia + 1];
+        const int comps = m->sched_comps[ia];
+        const bool next_store = ia + 1 < nact && m->sched[2 * (ia + 1)] == 2;
+        if (kind == 1) {   // ADVANCE (may span several turns)
+            while (j.kdone < arg && used < units) {
+                j.pf.cur = m->u[j.cur].as<float>();
+                j.pf.prev = m->u[1 - j.cur].as<float>();
+                j.pf.n = (int)j.step;
+                j.pf.maxbits = nullptr;
+                if (j.fused_max && next_store && j.kdone == arg - 1) {
+                    FWI_CU(cudaMemsetAsync(m->maxbits.p, 0, 2 * ns * sizeof(unsigned), s));
+                    j.pf.maxbits = m->maxbits.as<unsigned>();
+                }
+                FWI_TRY(step_launch(m, j.pf, ns, false, 0, s));
+                if (j.step >= j.recorded) {
+                    FWI_LAUNCH(m, launch_sample(g, j.pf.prev, m->rec_off.as<int64_t>(), ns, nr,
+                                                nt, (int)j.step, j.tr, s));
+                    j.recorded = j.step + 1;
+                }
+                j.cur = 1 - j.cur;
+                ++j.step;
+                ++j.nfwd;
+                ++j.kdone;
+                ++used;
+            }
+            if (j.kdone < arg) break;
+            j.kdone = 0;
+        } else if (kind == 2) {   // STORE the pair (u^step, u^{step-1}), or u^step alone
+            const bool have_max = j.fused_max && ia > 0 && m->sched[2 * (ia - 1)] == 1;
+            if (!have_max) {
+                FWI_CU(cudaMemsetAsync(m->maxbits.p, 0, 2 * ns * sizeof(unsigned), s));
+                FWI_LAUNCH(m, launch_maxabs(m->u[j.cur].as<float>(), m->u[1 - j.cur].as<float>(),
+                                            g.field, g.field, ns, m->maxbits.as<unsigned>(), s));
+            }
+            FWI_LAUNCH(m, launch_encode(m->u[j.cur].as<float>(), m->u[1 - j.cur].as<float>(),
+                                        g.field, g.field, ns, m->opts.snap_dtype,
+                                        m->maxbits.as<unsigned>(),
+                                        (void *)(j.codes + (size_t)arg * j.per_slot), 2 * g.field,
+                                        m->scales.as<float>() + (size_t)arg * 2 * ns, m->d_flag,
+                                        comps, s));
+            j.slot_step[arg] = j.step;
+            ++j.nstore;
+        } else if (kind == 3) {   // RESTORE
+            if (arg < 0) {
+                FWI_CU(cudaMemsetAsync(m->u[0].p, 0, ns * j.fb, s));
+                FWI_CU(cudaMemsetAsync(m->u[1].p, 0, ns * j.fb, s));
+                j.cur = 0;
+                j.step = 0;
+            } else {
+                FWI_LAUNCH(m, launch_decode(j.codes + (size_t)arg * j.per_slot, 2 * g.field,
+                                            m->scales.as<float>() + (size_t)arg * 2 * ns, g.field,
+                                            g.field, ns, m->opts.snap_dtype,
+                                            m->u[j.cur].as<float>(),
+                                            m->u[1 - j.cur].as<float>(), comps, s));
+                j.step = j.slot_step[arg];
+            }
+            ++j.nrestore;
+        } else if (kind == 4) {   // ADJOINT step m = arg, needs u^m = u[cur]
+            const int mm = arg;
+            if (j.step != mm)
+                return fail(FWI_ERR_CUDA, "internal: checkpoint schedule out of step");
+            if (j.first_adj) {
+                ++m->launches;   // the misfit is two launches
+                FWI_LAUNCH(m, launch_misfit(j.tr, (const float *)j.dobs, j.res,
+                                            (int64_t)ns * nt * nr, m->partials.as<double>(),
+                                            misfit_blocks((int64_t)ns * nt * nr),
+                                            m->phi.as<double>(), m->d_flag, s));
+                FWI_CU(cudaMemsetAsync(m->mu[0].p, 0, ns * j.fb, s));
+                FWI_CU(cudaMemsetAsync(m->mu[1].p, 0, ns * j.fb, s));
+                j.first_adj = false;
+            }
+            j.pa.cur = m->mu[j.mcur].as<float>();        // mu^{m+1}
+            j.pa.prev = m->mu[1 - j.mcur].as<float>();   // mu^{m+2} -> mu^m
+            const bool img = mm < nt;                    // mu^{nt+1} = 0: no imaging at nt
+            j.pa.u_img = m->u[j.cur].as<float>();
+            j.pa.gacc = m->g32.as<float>();
+            FWI_TRY(step_launch(m, j.pa, ns, img, 1, s));
+            FWI_LAUNCH(m, launch_inject(g, j.pa.prev, m->rec_off.as<int64_t>(),
+                                        m->inj.as<float>(), j.res, ns, nr, nt, mm - 1, s));
+            j.mcur = 1 - j.mcur;
+            ++j.nadj;
+            ++used;
+            if (j.nadj % m->opts.fold_every == 0)
+                FWI_LAUNCH(m, launch_fold(m->g32.as<float>(), m->g64.as<double>(), j.nfield, s));
+        }
+        ++j.ia;
+    }
+    *done = j.ia >= nact;
+    return FWI_OK;
+}
+
+// FP64 fold of the last partial gradient and the finish into the outputs (device targets
+// of the caller or staging buffers; host copies are issued here).
+int grad_finish(GradJob &j, double *misfit, float *grad, double *grad64, bool *sync_needed)
+{
+    fwi_model *m = j.m;
+    const cudaStream_t s = j.s;
+    FWI_LAUNCH(m, launch_fold(m->g32.as<float>(), m->g64.as<double>(), j.nfield, s));
+    const int64_t nphys = m->np[0] * m->np[1] * m->np[2];
+    void *g32dev = nullptr, *g64dev = nullptr;
+    bool g32host = false, g64host = false;
+    if (grad) FWI_TRY(output_target(m, 0, grad, nphys * sizeof(float), &g32dev, &g32host));
+    if (grad64) FWI_TRY(output_target(m, 1, grad64, nphys * sizeof(double), &g64dev, &g64host));
+    FWI_LAUNCH(m, launch_finish(m->g, m->nb, m->np, j.ns, m->g64.as<double>(), m->v.as<float>(),
+                                (float *)g32dev, (double *)g64dev, s));
+    FWI_TRY(finish_output(grad, g32dev, nphys * sizeof(float), g32host, s));
+    FWI_TRY(finish_output(grad64, g64dev, nphys * sizeof(double), g64host, s));
+    bool sync = g32host || g64host;
+    if (misfit) {
+        const bool mh = !is_device_ptr(misfit);
+        FWI_CU(cudaMemcpyAsync(misfit, m->phi.p, sizeof(double),
+                               mh ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+        sync = sync || mh;
+    }
+    m->st_fwd = j.nfwd;
+    m->st_adj = j.nadj;
+    m->st_store = j.nstore;
+    m->st_restore = j.nrestore;
+    *sync_needed = sync;
+    return FWI_OK;
+}
+
+// ---- opaque jobs for the serving loop (jobs.h)
+
+struct Job {
+    int kind = 0;   // 0 forward, 1 gradient
+    FwdJob f;
+    GradJob gj;
+    int nrec = 0;
+};
+
+Job *job_forward(fwi_model *m, const fwi_acq *acq, const float *wavelets, cudaStream_t s,
+                 int *rc)
+{
+    *rc = validate_acq(m, acq);
+    if (*rc != FWI_OK) return nullptr;
+    *rc = ensure_workspace(m, acq, false, s);
+    if (*rc != FWI_OK) return nullptr;
+    const void *wav;
+    *rc = stage_input(m, 0, wavelets, (size_t)acq->nshots * m->nt * sizeof(float), s, &wav);
+    if (*rc != FWI_OK) return nullptr;
+    Job *j = new Job();
+    j->kind = 0;
+    j->nrec = acq->nrec;
+    *rc = fwd_setup(j->f, m, acq->nshots, acq->nrec, (const float *)wav, m->traces.as<float>(), s);
+    if (*rc != FWI_OK) {
+        delete j;
+        return nullptr;
+    }
+    return j;
+}
+
+Job *job_gradient(fwi_model *m, const fwi_acq *acq, const float *wavelets, const float *d_obs,
+                  cudaStream_t s, int *rc)
+{
+    *rc = validate_acq(m, acq);
+    if (*rc != FWI_OK) return nullptr;
+    Job *j = new Job();
+    j->kind = 1;
+    j->nrec = acq->nrec;
+    *rc = grad_setup(j->gj, m, acq, wavelets, d_obs, s);
+    if (*rc != FWI_OK) {
+        delete j;
+        return nullptr;
+    }
+    return j;
+}
+
+int job_advance(Job *j, int64_t units, bool *done)
+{
+    return j->kind == 0 ? fwd_advance(j->f, units, done) : grad_advance(j->gj, units, done);
+}
+
+// Issues the result copies into host buffers (traces [ns][nt][nrec] of a forward job, or
+// misfit and gradient of a gradient job) on the job's stream; the caller synchronises.
+int job_finish(Job *j, double *misfit_host, float *out_host)
+{
+    if (j->kind == 0) {
+        fwi_model *m = j->f.m;
+        if (out_host)
+            FWI_CU(cudaMemcpyAsync(out_host, m->traces.p,
+                                   (size_t)j->f.ns * m->nt * j->nrec * sizeof(float),
+                                   cudaMemcpyDeviceToHost, j->f.s));
+        return FWI_OK;
+    }
+    bool sync = false;
+    return grad_finish(j->gj, misfit_host, out_host, nullptr, &sync);
+}
+
+void job_free(Job *j) { delete j; }
+
+}  // namespace fwi
 
 // ====================================================================== C ABI
 
@@ -702,8 +1047,11 @@ int fwi_forward(fwi_model *m, const fwi_acq *acq, const float *wavelets, float *
     bool trhost = false;
     const size_t trbytes = (size_t)ns * m->nt * nr * sizeof(float);
     if (traces) FWI_TRY(output_target(m, 0, traces, trbytes, &trdev, &trhost));
-    int cur = 0;
-    FWI_TRY(run_forward(m, ns, nr, (const float *)wav, (float *)trdev, &cur, s));
+    FwdJob job;
+    FWI_TRY(fwd_setup(job, m, ns, nr, (const float *)wav, (float *)trdev, s));
+    bool done = false;
+    FWI_TRY(fwd_advance(job, INT64_MAX, &done));
+    const int cur = job.cur;
     FWI_LAUNCH(m, launch_nonfinite_check(m->u[cur].as<float>(), (int64_t)ns * m->g.field, m->d_flag, s));
     bool sync = trhost;
     if (final_state) {
@@ -736,187 +1084,12 @@ int fwi_adjoint_gradient(fwi_model *m, const fwi_acq *acq, const float *wavelets
     FWI_TRY(check_status(m));
     FWI_TRY(validate_acq(m, acq));
     m->last_stream = s;
-    const int ns = acq->nshots, nr = acq->nrec, nt = m->nt;
-    FWI_TRY(ensure_workspace(m, acq, true, s));
-    const Geom &g = m->g;
-    const int64_t nfield = (int64_t)ns * g.field;
-    const size_t fb = (size_t)g.field * sizeof(float);
-
-    // checkpoint slots: as many as the budget holds, never more than nt
-    const int esz = m->opts.snap_dtype == FWI_SNAP_FP32 ? 4 : 2;
-    const size_t per_slot = (size_t)ns * 2 * g.field * esz;
-    int64_t budget = m->opts.snap_budget_bytes;
-    if (budget <= 0) {
-        size_t fr = 0, tot = 0;
-        FWI_CU(cudaMemGetInfo(&fr, &tot));
-        budget = (int64_t)(fr / 4);
-    }
-    int64_t slots = budget / (int64_t)per_slot;
-    if (slots > nt) slots = nt;
-    if (slots < 0) slots = 0;
-    if ((size_t)slots * per_slot > m->snaps.bytes) {
-        // shrink on failure rather than fail: fewer slots only cost recomputation
-        while (slots > 0 && m->snaps.ensure((size_t)slots * per_slot) != FWI_OK) slots /= 2;
-    }
-    FWI_TRY(m->scales.ensure((size_t)(slots > 0 ? slots : 1) * 2 * ns * sizeof(float)));
-    if (slots != m->sched_nslots) {
-        m->sched = revolve_actions(nt, (int32_t)slots, &m->sched_fwd);
-        m->sched_nslots = (int)slots;
-        // Components each checkpoint action moves: a restore followed by a reverse step
-        // needs u^m alone (the imaging pass reads only u^m; the following action is always
-        // another restore), and a checkpoint whose every restore is of that kind is
-        // stored as u^n alone.
-        const size_t na = m->sched.size() / 2;
-        m->sched_comps.assign(na, 2);
-        for (size_t i = 0; i < na; ++i) {
-            const int kind = m->sched[2 * i], arg = m->sched[2 * i + 1];
-            if (kind == 3 && arg >= 0 && i + 1 < na && m->sched[2 * (i + 1)] == 4)
-                m->sched_comps[i] = 1;
-        }
-        for (size_t i = 0; i < na; ++i) {
-            if (m->sched[2 * i] != 2) continue;
-            const int slot = m->sched[2 * i + 1];
-            int need = 1;
-            for (size_t k = i + 1; k < na; ++k) {
-                const int kk = m->sched[2 * k], aa = m->sched[2 * k + 1];
-                if (kk == 2 && aa == slot) break;
-                if (kk == 3 && aa == slot && m->sched_comps[k] == 2) {
-                    need = 2;
-                    break;
-                }
-            }
-            m->sched_comps[i] = need;
-        }
-    }
-    m->nslots = (int)slots;
-    m->slot_bytes = per_slot;
-
-    const void *wav, *dobs;
-    FWI_TRY(stage_input(m, 0, wavelets, (size_t)ns * nt * sizeof(float), s, &wav));
-    FWI_TRY(stage_input(m, 1, d_obs, (size_t)ns * nt * nr * sizeof(float), s, &dobs));
-
-    // adjoint receiver injection factor 2 W / a+ (the adjoint source is 2 r for Eq. 1)
-    FWI_LAUNCH(m, launch_rec_scale(g, m->W.as<float>(), sig_z(m), sig_y(m), sig_x(m),
-                            m->rec_off.as<int64_t>(), ns * nr, 2.0f, 0, m->inj.as<float>(), s));
-    FWI_CU(cudaMemsetAsync(m->u[0].p, 0, ns * fb, s));
-    FWI_CU(cudaMemsetAsync(m->u[1].p, 0, ns * fb, s));
-    FWI_CU(cudaMemsetAsync(m->g32.p, 0, ns * fb, s));
-    FWI_CU(cudaMemsetAsync(m->g64.p, 0, ns * 2 * fb, s));
-
-    StepParams pf = base_params(m);
-    pf.src_off = m->src_off.as<int64_t>();
-    pf.wavelet = (const float *)wav;
-    StepParams pa = base_params(m);   // reverse sweep: no source, receivers injected after
-    float *tr = m->traces.as<float>();
-    float *res = tr;                  // residuals replace the traces in place
-    int cur = 0, mcur = 0;
-    int64_t step = 0, recorded = 0;
-    std::vector<int64_t> slot_step(slots > 0 ? slots : 1, -1);
-    bool first_adj = true;
-    int64_t nadj = 0, nfwd = 0, nstore = 0, nrestore = 0;
-    const char *codes = m->snaps.as<char>();
-
-    const bool fused_max = use_step3d(m);   // the 3-D step computes the checkpoint max-abs
-    const size_t nact = m->sched.size() / 2;
-    for (size_t ia = 0; ia < nact; ++ia) {
-        const int kind = m->sched[2 * ia], arg = m->sched[2 * ia + 1];
-        const int comps = m->sched_comps[ia];
-        const bool next_store = ia + 1 < nact && m->sched[2 * (ia + 1)] == 2;
-        if (kind == 1) {   // ADVANCE
-            for (int k = 0; k < arg; ++k) {
-                pf.cur = m->u[cur].as<float>();
-                pf.prev = m->u[1 - cur].as<float>();
-                pf.n = (int)step;
-                pf.maxbits = nullptr;
-                if (fused_max && next_store && k == arg - 1) {
-                    FWI_CU(cudaMemsetAsync(m->maxbits.p, 0, 2 * ns * sizeof(unsigned), s));
-                    pf.maxbits = m->maxbits.as<unsigned>();
-                }
-                FWI_TRY(step_launch(m, pf, ns, false, 0, s));
-                if (step >= recorded) {
-                    FWI_LAUNCH(m, launch_sample(g, pf.prev, m->rec_off.as<int64_t>(), ns, nr, nt,
-                                         (int)step, tr, s));
-                    recorded = step + 1;
-                }
-                cur = 1 - cur;
-                ++step;
-                ++nfwd;
-            }
-        } else if (kind == 2) {   // STORE the pair (u^step, u^{step-1}), or u^step alone
-            const bool have_max = fused_max && ia > 0 && m->sched[2 * (ia - 1)] == 1;
-            if (!have_max) {
-                FWI_CU(cudaMemsetAsync(m->maxbits.p, 0, 2 * ns * sizeof(unsigned), s));
-                FWI_LAUNCH(m, launch_maxabs(m->u[cur].as<float>(), m->u[1 - cur].as<float>(),
-                                            g.field, g.field, ns, m->maxbits.as<unsigned>(), s));
-            }
-            FWI_LAUNCH(m, launch_encode(m->u[cur].as<float>(), m->u[1 - cur].as<float>(), g.field,
-                                 g.field, ns, m->opts.snap_dtype, m->maxbits.as<unsigned>(),
-                                 (void *)(codes + (size_t)arg * per_slot), 2 * g.field,
-                                 m->scales.as<float>() + (size_t)arg * 2 * ns, m->d_flag, comps, s));
-            slot_step[arg] = step;
-            ++nstore;
-        } else if (kind == 3) {   // RESTORE
-            if (arg < 0) {
-                FWI_CU(cudaMemsetAsync(m->u[0].p, 0, ns * fb, s));
-                FWI_CU(cudaMemsetAsync(m->u[1].p, 0, ns * fb, s));
-                cur = 0;
-                step = 0;
-            } else {
-                FWI_LAUNCH(m, launch_decode(codes + (size_t)arg * per_slot, 2 * g.field,
-                                     m->scales.as<float>() + (size_t)arg * 2 * ns, g.field, g.field,
-                                     ns, m->opts.snap_dtype, m->u[cur].as<float>(),
-                                     m->u[1 - cur].as<float>(), comps, s));
-                step = slot_step[arg];
-            }
-            ++nrestore;
-        } else if (kind == 4) {   // ADJOINT step m = arg, needs u^m = u[cur]
-            const int mm = arg;
-            if (step != mm) return fail(FWI_ERR_CUDA, "internal: checkpoint schedule out of step");
-            if (first_adj) {
-                ++m->launches;   // the misfit is two launches
-                FWI_LAUNCH(m, launch_misfit(tr, (const float *)dobs, res, (int64_t)ns * nt * nr,
-                                     m->partials.as<double>(), misfit_blocks((int64_t)ns * nt * nr),
-                                     m->phi.as<double>(), m->d_flag, s));
-                FWI_CU(cudaMemsetAsync(m->mu[0].p, 0, ns * fb, s));
-                FWI_CU(cudaMemsetAsync(m->mu[1].p, 0, ns * fb, s));
-                first_adj = false;
-            }
-            pa.cur = m->mu[mcur].as<float>();        // mu^{m+1}
-            pa.prev = m->mu[1 - mcur].as<float>();   // mu^{m+2} -> mu^m
-            const bool img = mm < nt;                // mu^{nt+1} = 0: no imaging at m = nt
-            pa.u_img = m->u[cur].as<float>();
-            pa.gacc = m->g32.as<float>();
-            FWI_TRY(step_launch(m, pa, ns, img, 1, s));
-            FWI_LAUNCH(m, launch_inject(g, pa.prev, m->rec_off.as<int64_t>(), m->inj.as<float>(), res,
-                                 ns, nr, nt, mm - 1, s));
-            mcur = 1 - mcur;
-            ++nadj;
-            if (nadj % m->opts.fold_every == 0)
-                FWI_LAUNCH(m, launch_fold(m->g32.as<float>(), m->g64.as<double>(), nfield, s));
-        }
-    }
-    FWI_LAUNCH(m, launch_fold(m->g32.as<float>(), m->g64.as<double>(), nfield, s));
-
-    const int64_t nphys = m->np[0] * m->np[1] * m->np[2];
-    void *g32dev = nullptr, *g64dev = nullptr;
-    bool g32host = false, g64host = false;
-    if (grad) FWI_TRY(output_target(m, 0, grad, nphys * sizeof(float), &g32dev, &g32host));
-    if (grad64) FWI_TRY(output_target(m, 1, grad64, nphys * sizeof(double), &g64dev, &g64host));
-    FWI_LAUNCH(m, launch_finish(g, m->nb, m->np, ns, m->g64.as<double>(), m->v.as<float>(),
-                         (float *)g32dev, (double *)g64dev, s));
-    FWI_TRY(finish_output(grad, g32dev, nphys * sizeof(float), g32host, s));
-    FWI_TRY(finish_output(grad64, g64dev, nphys * sizeof(double), g64host, s));
-    bool sync = g32host || g64host;
-    if (misfit) {
-        const bool mh = !is_device_ptr(misfit);
-        FWI_CU(cudaMemcpyAsync(misfit, m->phi.p, sizeof(double),
-                               mh ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
-        sync = sync || mh;
-    }
-    m->st_fwd = nfwd;
-    m->st_adj = nadj;
-    m->st_store = nstore;
-    m->st_restore = nrestore;
+    GradJob job;
+    FWI_TRY(grad_setup(job, m, acq, wavelets, d_obs, s));
+    bool done = false;
+    FWI_TRY(grad_advance(job, INT64_MAX, &done));
+    bool sync = false;
+    FWI_TRY(grad_finish(job, misfit, grad, grad64, &sync));
     if (sync) {
         FWI_CU(cudaStreamSynchronize(s));
         FWI_TRY(check_status(m));

@@ -52,6 +52,25 @@ class fwi_info(ctypes.Structure):
                 ("adj_step_launches", c_i64), ("fwd_step_ms", c_f64), ("adj_step_ms", c_f64)]
 
 
+class fwi_request(ctypes.Structure):
+    _fields_ = [("kind", c_i32), ("ndim", c_i32), ("shape", c_i64 * 3), ("spacing", c_f32 * 3),
+                ("dt", c_f32), ("nt", c_i32), ("order", c_i32), ("snap_dtype", c_i32),
+                ("nrec", c_i32), ("src", c_i32 * 3), ("reserved", c_i32), ("vp", c_vp),
+                ("wavelet", c_vp), ("rec", c_vp), ("d_obs", c_vp), ("traces_out", c_vp),
+                ("grad_out", c_vp), ("arrival", c_f64)]
+
+
+class fwi_result(ctypes.Structure):
+    _fields_ = [("status", c_i32), ("reserved", c_i32), ("misfit", c_f64), ("t_admit", c_f64),
+                ("t_start", c_f64), ("t_done", c_f64), ("device_bytes", c_i64),
+                ("reserved_bytes", c_i64)]
+
+
+class fwi_serve_opts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", c_i64), ("max_active", c_i32), ("steps_per_turn", c_i32),
+                ("snap_slots", c_i32), ("nb", c_i32)]
+
+
 class FwiError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
@@ -84,6 +103,7 @@ def lib():
                 "fwi_fd_coeffs": ([c_i32, P], c_i32),
                 "fwi_cfl_number": ([c_i32, c_i32, P, c_f32, c_f32], c_f64),
                 "fwi_model_info": ([P, P], c_i32),
+                "fwi_serve": ([P, c_i32, P, P], c_i32),
                 "fwi_sync_status": ([P], c_i32),
                 "fwi_destroy": ([P], None),
                 "fwi_last_error": ([], ctypes.c_char_p),
@@ -211,6 +231,59 @@ def fwi_model_info(model) -> dict:
         v = getattr(info, name)
         out[name] = list(v) if hasattr(v, "__len__") else v
     return out
+
+
+def fwi_serve(requests, budget_bytes=0, max_active=16, steps_per_turn=8, snap_slots=8, nb=20):
+    """Runs a request stream through the serving loop.  `requests` is a list of dicts with
+    keys kind ('forward'/'gradient'), v (float32 physical grid), h, dt, nt, order,
+    snap_dtype, src (3 ints), rec (int32 [nrec][3]), wavelet (float32 [nt]), d_obs
+    (float32 [nt][nrec], gradients) and arrival (s).  Returns (results as dicts, outputs):
+    outputs[i] is the traces [nt][nrec] of a forward request or the gradient of a
+    gradient request."""
+    n = len(requests)
+    arr = (fwi_request * n)()
+    keep, outs = [], []
+    for i, r in enumerate(requests):
+        v = np.ascontiguousarray(r["v"], dtype=np.float32)
+        ndim = v.ndim
+        shape = v.shape if ndim == 3 else (v.shape[0], 1, v.shape[1])
+        h = float(r["h"])
+        wav = np.ascontiguousarray(r["wavelet"], dtype=np.float32)
+        rec = np.ascontiguousarray(r["rec"], dtype=np.int32).reshape(-1, 3)
+        nrec = rec.shape[0]
+        grad = r["kind"] == "gradient"
+        if grad:
+            dobs = np.ascontiguousarray(r["d_obs"], dtype=np.float32)
+            out = np.zeros(v.shape, dtype=np.float32)
+        else:
+            dobs = None
+            out = np.zeros((int(r["nt"]), nrec), dtype=np.float32)
+        keep += [v, wav, rec, dobs]
+        outs.append(out)
+        q = arr[i]
+        q.kind = 1 if grad else 0
+        q.ndim = ndim
+        q.shape = (c_i64 * 3)(*shape)
+        q.spacing = (c_f32 * 3)(h, h if ndim == 3 else 1.0, h)
+        q.dt = float(r["dt"])
+        q.nt = int(r["nt"])
+        q.order = int(r.get("order", 8))
+        q.snap_dtype = SNAP_DTYPES[r.get("snap_dtype", "bf16")]
+        q.nrec = nrec
+        q.src = (c_i32 * 3)(*[int(x) for x in r["src"]])
+        q.vp = v.ctypes.data
+        q.wavelet = wav.ctypes.data
+        q.rec = rec.ctypes.data
+        q.d_obs = dobs.ctypes.data if grad else None
+        q.traces_out = None if grad else out.ctypes.data
+        q.grad_out = out.ctypes.data if grad else None
+        q.arrival = float(r.get("arrival", 0.0))
+    res = (fwi_result * n)()
+    opts = fwi_serve_opts(int(budget_bytes), int(max_active), int(steps_per_turn),
+                          int(snap_slots), int(nb))
+    _check(lib().fwi_serve(arr, n, ctypes.byref(opts), res))
+    results = [{k: getattr(x, k) for k, _ in fwi_result._fields_ if k != "reserved"} for x in res]
+    return results, outs
 
 
 def fwi_sync_status(model):

@@ -250,6 +250,48 @@ def smooth_random(rng, shape, h: float, ell: float = 300.0) -> np.ndarray:
     return (1500.0 + 3000.0 * (f - lo) / (hi - lo)).astype(np.float32)
 
 
+def serving_requests(n: int, dt_for, seed: int = 4, size2d=(128, 1024), size3d=(64, 192),
+                     nt_range=(500, 3000), frac_grad: float = 0.5, frac_2d: float = 0.75,
+                     h: float = 10.0):
+    """Request mix of the serving workload: 2-D grids with sides ~U{size2d}, 3-D grids
+    with sides ~U{size3d}, nt ~U{nt_range}, forward or gradient, smooth random velocity
+    (Gaussian random field, correlation length 300 m, mapped onto 1500..4500 m/s),
+    source at the surface centre (row 2), receivers on every cell of row 2, 8th order,
+    BF16 checkpoints, 15 Hz Ricker.  dt_for(ndim, h) gives the time step (the caller's
+    rule, e.g. 0.8 of the stability limit).  The observed model of a gradient request is
+    its velocity times (1 + 5 % random field).  Arrival times are left at 0; the caller
+    draws them."""
+    rng = rng_for(4, 1000 + seed)
+    reqs = []
+    for i in range(n):
+        is2d = rng.random() < frac_2d
+        kind = "gradient" if rng.random() < frac_grad else "forward"
+        nt = int(rng.integers(nt_range[0], nt_range[1] + 1))
+        if is2d:
+            nz, nx = (int(x) for x in rng.integers(size2d[0], size2d[1] + 1, 2))
+            shape = (nz, nx)
+            ndim = 2
+        else:
+            shape = tuple(int(x) for x in rng.integers(size3d[0], size3d[1] + 1, 3))
+            ndim = 3
+        v = smooth_random(rng, shape, h, ell=300.0)
+        dt = float(dt_for(ndim, h))
+        if ndim == 2:
+            src = [2, 0, shape[1] // 2]
+            rec = np.stack([np.full(shape[1], 2), np.zeros(shape[1]), np.arange(shape[1])], 1)
+        else:
+            src = [2, shape[1] // 2, shape[2] // 2]
+            yy, xx = np.meshgrid(np.arange(shape[1]), np.arange(shape[2]), indexing="ij")
+            rec = np.stack([np.full(yy.size, 2), yy.ravel(), xx.ravel()], 1)
+        r = {"kind": kind, "v": v, "h": h, "dt": dt, "nt": nt, "order": 8, "snap_dtype": "bf16",
+             "src": src, "rec": rec.astype(np.int32), "wavelet": ricker(15.0, dt, nt),
+             "arrival": 0.0}
+        if kind == "gradient":
+            r["v_obs"] = (v * (1.0 + gaussian_random_field(rng, shape, h, 200.0, 0.05))).astype(np.float32)
+        reqs.append(r)
+    return reqs
+
+
 def random_small(rng, ndim: int, shape, h: float = 10.0, nt: int = 60, order: int = 8,
                  nb: int = 6, nrec: int = 7, f0: float = 20.0) -> Workload:
     """Small random case for parity tests: smooth random model, random source and

@@ -1,0 +1,74 @@
+"""Serving loop (continuous batching): each request's result is the same alone and in
+the mix, work from several requests overlaps, and admission respects the memory budget."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1912_08063_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _requests(n, seed):
+    from paper_1912_08063_gb300 import fwi
+
+    def dt_for(ndim, h):
+        lim = 1.0 / fwi.fwi_cfl_number(ndim, 8, (h, h, h), 4500.0, 1.0)
+        return math.floor(0.8 * lim * 1e4) / 1e4
+
+    reqs = synth.serving_requests(n, dt_for, seed=seed, size2d=(40, 140), size3d=(20, 44),
+                                  nt_range=(60, 220))
+    for r in reqs:
+        if r["kind"] == "gradient":   # observed traces from the perturbed model
+            m = fwi.FwiModel(torch.from_numpy(r["v_obs"]).cuda(), r["h"], r["dt"], r["nt"])
+            acq = fwi.Acquisition([r["src"]], r["rec"])
+            r["d_obs"] = m.forward(acq, torch.from_numpy(r["wavelet"][None]).cuda())[0].cpu().numpy()
+            m.close()
+    return reqs
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_results_same_alone_and_in_the_mix():
+    from paper_1912_08063_gb300 import fwi
+    reqs = _requests(8, seed=1)
+    for i, r in enumerate(reqs):
+        r["arrival"] = 0.002 * i
+    mix, mix_out = fwi.fwi_serve(reqs, max_active=8, steps_per_turn=4, snap_slots=6)
+    assert all(x["status"] == 0 for x in mix), mix
+    for i, r in enumerate(reqs):
+        r1 = dict(r, arrival=0.0)
+        alone, alone_out = fwi.fwi_serve([r1], max_active=1, snap_slots=6)
+        assert alone[0]["status"] == 0
+        e = _rel(mix_out[i], alone_out[0])
+        assert e <= 1e-6, (i, r["kind"], e)
+        if r["kind"] == "gradient":
+            assert abs(mix[i]["misfit"] - alone[0]["misfit"]) <= 1e-6 * abs(alone[0]["misfit"])
+            assert np.abs(alone_out[0]).max() > 0
+    # the requests really ran together: some [start, done] intervals overlap
+    iv = sorted((x["t_start"], x["t_done"]) for x in mix)
+    assert any(b[0] < a[1] for a, b in zip(iv, iv[1:]))
+
+
+def test_admission_respects_the_budget():
+    from paper_1912_08063_gb300 import fwi
+    reqs = _requests(10, seed=2)
+    # a budget that holds only a few of these requests at once
+    budget = 3 * 10 ** 8
+    res, _ = fwi.fwi_serve(reqs, budget_bytes=budget, max_active=16, steps_per_turn=4,
+                           snap_slots=4)
+    assert all(x["status"] == 0 for x in res), res
+    for x in res:
+        assert 0 < x["device_bytes"] <= x["reserved_bytes"], x
+    events = sorted([(x["t_admit"], x["reserved_bytes"]) for x in res] +
+                    [(x["t_done"], -x["reserved_bytes"]) for x in res], key=lambda e: (e[0], e[1]))
+    held = 0
+    for _, d in events:
+        held += d
+        assert held <= budget
+    # and requests were admitted as memory freed up, not all at once
+    assert len({round(x["t_admit"], 6) for x in res}) > 1
