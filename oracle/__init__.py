@@ -45,46 +45,80 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            P = ctypes.c_void_p
-            i64p = ctypes.POINTER(ctypes.c_int64)
-            d = ctypes.c_double
-            i = ctypes.c_int
-            lib.oracle_fd_coeffs.argtypes = [i, P]
-            lib.oracle_fd_coeffs.restype = i
-            lib.oracle_cfl_number.argtypes = [i, i, P, d, d]
-            lib.oracle_cfl_number.restype = d
-            lib.oracle_laplacian.argtypes = [i, i64p, P, i, P, P]
-            lib.oracle_laplacian.restype = i
-            common = [i, i64p, P, P, d, i, i, i, d, d]
-            lib.oracle_forward.argtypes = common + [i, P, P, i, P, P, P]
-            lib.oracle_forward.restype = i
-            lib.oracle_misfit.argtypes = [P, P, ctypes.c_int64]
-            lib.oracle_misfit.restype = d
-            lib.oracle_gradient.argtypes = common + [i, P, P, i, P, P, P, P, P, P, i]
-            lib.oracle_gradient.restype = i
-            lib.oracle_source_adjoint.argtypes = common + [i, P, i, P, P, P]
-            lib.oracle_source_adjoint.restype = i
-            lib.oracle_model_fields.argtypes = [i, i64p, P, P, d, i, i, d, d, i64p, P, P, P]
-            lib.oracle_model_fields.restype = i
-            f = ctypes.c_float
-            u16 = ctypes.c_uint16
-            lib.oracle_snap_scale.argtypes = [f, i]
-            lib.oracle_snap_scale.restype = f
-            lib.oracle_f32_to_bf16.argtypes = [f]
-            lib.oracle_f32_to_bf16.restype = u16
-            lib.oracle_f32_to_f16.argtypes = [f]
-            lib.oracle_f32_to_f16.restype = u16
-            lib.oracle_bf16_to_f32.argtypes = [u16]
-            lib.oracle_bf16_to_f32.restype = f
-            lib.oracle_f16_to_f32.argtypes = [u16]
-            lib.oracle_f16_to_f32.restype = f
-            lib.oracle_snap_encode.argtypes = [P, P, ctypes.c_int64, i, P, P]
-            lib.oracle_snap_encode.restype = None
-            lib.oracle_snap_decode.argtypes = [P, P, ctypes.c_int64, i, P, P]
-            lib.oracle_snap_decode.restype = None
-            _lib = lib
+            _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+def compile_source(text: str, out_path: str) -> str:
+    """Compiles C source text with the oracle's flags (used by the tests that plant a
+    mistake in a copy of the oracle and check that a pin catches it)."""
+    src = out_path + ".c"
+    with open(src, "w") as f:
+        f.write(text)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
+                    "-ffp-contract=off", src, "-o", out_path, "-lm"], check=True)
+    return out_path
+
+
+class use_library:
+    """Context manager: route every oracle call to the library at `path`."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        _load()
+        self.saved = _lib
+        _lib = _configure(ctypes.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def _configure(lib):
+    """Declares the argument and result types of every oracle function on `lib`."""
+    P = ctypes.c_void_p
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    d = ctypes.c_double
+    i = ctypes.c_int
+    lib.oracle_fd_coeffs.argtypes = [i, P]
+    lib.oracle_fd_coeffs.restype = i
+    lib.oracle_cfl_number.argtypes = [i, i, P, d, d]
+    lib.oracle_cfl_number.restype = d
+    lib.oracle_laplacian.argtypes = [i, i64p, P, i, P, P]
+    lib.oracle_laplacian.restype = i
+    common = [i, i64p, P, P, d, i, i, i, d, d]
+    lib.oracle_forward.argtypes = common + [i, P, P, i, P, P, P]
+    lib.oracle_forward.restype = i
+    lib.oracle_misfit.argtypes = [P, P, ctypes.c_int64]
+    lib.oracle_misfit.restype = d
+    lib.oracle_gradient.argtypes = common + [i, P, P, i, P, P, P, P, P, P, i]
+    lib.oracle_gradient.restype = i
+    lib.oracle_source_adjoint.argtypes = common + [i, P, i, P, P, P]
+    lib.oracle_source_adjoint.restype = i
+    lib.oracle_model_fields.argtypes = [i, i64p, P, P, d, i, i, d, d, i64p, P, P, P]
+    lib.oracle_model_fields.restype = i
+    f = ctypes.c_float
+    u16 = ctypes.c_uint16
+    lib.oracle_snap_scale.argtypes = [f, i]
+    lib.oracle_snap_scale.restype = f
+    lib.oracle_f32_to_bf16.argtypes = [f]
+    lib.oracle_f32_to_bf16.restype = u16
+    lib.oracle_f32_to_f16.argtypes = [f]
+    lib.oracle_f32_to_f16.restype = u16
+    lib.oracle_bf16_to_f32.argtypes = [u16]
+    lib.oracle_bf16_to_f32.restype = f
+    lib.oracle_f16_to_f32.argtypes = [u16]
+    lib.oracle_f16_to_f32.restype = f
+    lib.oracle_snap_encode.argtypes = [P, P, ctypes.c_int64, i, P, P]
+    lib.oracle_snap_encode.restype = None
+    lib.oracle_snap_decode.argtypes = [P, P, ctypes.c_int64, i, P, P]
+    lib.oracle_snap_decode.restype = None
+    return lib
 
 
 def _f64(a):

@@ -458,19 +458,14 @@ int step3d_launch(fwi_model *m, const StepParams &p, int ns, int mode, cudaStrea
     return FWI_OK;
 }
 
-bool use_step3d(const fwi_model *m)
-{
-    if (m->ndim != 3 || (m->M != 4 && m->M != 8)) return false;
-    const char *e = std::getenv("FWI_STEP3D");
-    return !(e && std::strcmp(e, "v1") == 0);
-}
+bool use_step3d(const fwi_model *m) { return m->ndim == 3; }
 
-// The time step itself: the fused v1 kernel (2-D), or in 3-D the TMA kernel, preceded
-// by its imaging pass when the reverse step images.
+// The time step itself: in 2-D the register-streaming kernel (imaging fused), in 3-D the
+// TMA kernel, preceded by its imaging pass when the reverse step images.
 int raw_step(fwi_model *m, const StepParams &p, int ns, bool img, cudaStream_t s)
 {
     if (!use_step3d(m)) {
-        FWI_CU(launch_step(p, ns, img, s));
+        FWI_CU(launch_step2d(p, ns, img, s));
         return FWI_OK;
     }
     if (img) {

@@ -56,7 +56,8 @@ struct StepParams {
                               // new state pair, fused into the step
 };
 
-cudaError_t launch_step(const StepParams &p, int nshots, bool imaging, cudaStream_t s);
+// 2-D step (k_step2d.cu); the 3-D step has its own launcher (step3d.h)
+cudaError_t launch_step2d(const StepParams &p, int nshots, bool imaging, cudaStream_t s);
 
 // ---- auxiliary kernels (k_aux.cu) ----
 cudaError_t launch_build_W(const Geom &g, int nb, const int64_t np[3], const float *v,
