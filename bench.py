@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=32)
+    ap.add_argument("--batched-nt", type=int, default=3000,
+                    help="time steps of the batched 2-D section (shorter for profiling)")
     return ap.parse_args()
 
 
@@ -262,13 +264,25 @@ def batched_section(dev, nt=3000):
     dobs = obs.forward(acq, wav)
     obs.close()
     m = fwi.FwiModel(torch.from_numpy(w.v).to(dev), w.h, w.dt, w.nt, order=w.order,
-                     snap_dtype=w.snap_dtype, snap_budget_bytes=16 << 30, sponge_vref=4500.0)
+                     snap_dtype=w.snap_dtype, snap_budget_bytes=16 << 30, sponge_vref=4500.0,
+                     timing=True)
     m.gradient(acq, wav, dobs)   # warm-up
     torch.cuda.synchronize()
+    i0 = m.info()
     t0 = time.perf_counter()
     phi, g = m.gradient(acq, wav, dobs)
     torch.cuda.synchronize()
     tb = time.perf_counter() - t0
+    i1 = m.info()
+    nf = i1["fwd_step_launches"] - i0["fwd_step_launches"]
+    na = i1["adj_step_launches"] - i0["adj_step_launches"]
+    fms = (i1["fwd_step_ms"] - i0["fwd_step_ms"]) / max(nf, 1)
+    ams = (i1["adj_step_ms"] - i0["adj_step_ms"]) / max(na, 1)
+    kern = {"fwd_step_avg_ms": round(fms, 4), "fwd_step_launches": nf,
+            "fwd_step_GB/s": round(BYTES_FWD * i1["points"] * w.nshots / (fms * 1e-3) / 1e9, 1),
+            "adj_step_avg_ms": round(ams, 4), "adj_step_launches": na,
+            "adj_step_GB/s": round(BYTES_ADJ * i1["points"] * w.nshots / (ams * 1e-3) / 1e9, 1),
+            "kernel_seconds": round((nf * fms + na * ams) / 1e3, 3)}
     singles = [fwi.Acquisition(w.src[i:i + 1], w.rec) for i in range(w.nshots)]
     t0 = time.perf_counter()
     for i, a in enumerate(singles):
@@ -281,7 +295,7 @@ def batched_section(dev, nt=3000):
             "shots_per_s": round(w.nshots / tb, 3),
             "shots_per_s_per_shot_calls": round(w.nshots / t1, 3),
             "gpts_per_s": round(gpts_per_s(pts * w.nshots, w.nt, tb), 2),
-            "seconds": round(tb, 3), "seconds_per_shot_calls": round(t1, 3)}
+            "seconds": round(tb, 3), "seconds_per_shot_calls": round(t1, 3), "kernels": kern}
 
 
 def run_reference(args):
@@ -430,7 +444,7 @@ def main():
     if rank == 0 and not args.no_serving:
         serving = serving_section(dev, args.serving_requests)
     if rank == 0 and not args.no_batched:
-        batched = batched_section(dev)
+        batched = batched_section(dev, args.batched_nt)
 
     if rank == 0:
         line = {"metric": "Gpts/s fwd+adjoint", "value": round(value, 3), "unit": "Gpts/s",

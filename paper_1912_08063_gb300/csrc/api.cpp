@@ -704,7 +704,7 @@ int grad_setup(GradJob &j, fwi_model *m, const fwi_acq *acq, const float *wavele
     j.res = j.tr;            // residuals replace the traces in place
     j.slot_step.assign(slots > 0 ? slots : 1, -1);
     j.codes = m->snaps.as<char>();
-    j.fused_max = use_step3d(m);   // the 3-D step computes the checkpoint max-abs
+    j.fused_max = true;   // the step kernels compute the checkpoint max-abs when asked
     return FWI_OK;
 }
 

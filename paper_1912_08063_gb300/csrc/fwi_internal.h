@@ -52,8 +52,9 @@ struct StepParams {
     float *gacc;              // imaging only: gradient accumulator
     int zchunk;               // planes per CTA along z
     int nzchunks;
-    unsigned *maxbits;        // 3-D TMA step only (nullable): checkpoint max-abs of the
-                              // new state pair, fused into the step
+    unsigned *maxbits;        // nullable, forward step only: per shot, raise [2s] / [2s+1]
+                              // to the bits of max|out| / max|out - cur| (the checkpoint
+                              // codec's scales of the new state pair)
 };
 
 // 2-D step (k_step2d.cu); the 3-D step has its own launcher (step3d.h)

@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
         }
     }
     const float2 two = make_float2(2.0f, 2.0f);
+    unsigned mxa = 0u, mxd = 0u;   // bits of max|out| and max|out - c| (p.maxbits set)
 
     for (int z = z0; z < z1; ++z) {
         const int zn = z + M;
@@ -123,6 +124,14 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
                 rhs[e] = __fdividef(v, 1.0f + s);
             }
             *(float4 *)(prev + row + x0) = make_float4(rhs[0], rhs[1], rhs[2], rhs[3]);
+            if (!IMG && p.maxbits) {
+                const float cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    mxa = max(mxa, __float_as_uint(rhs[e]) & 0x7fffffffu);
+                    mxd = max(mxd, __float_as_uint(rhs[e] - cc[e]) & 0x7fffffffu);
+                }
+            }
             if (IMG) {
                 float lu[4];
 #pragma unroll
@@ -155,6 +164,15 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
         for (int i = 0; i < Q - 1; ++i) {
             q[i] = q[i + 1];
             if (IMG) qu[i] = qu[i + 1];
+        }
+    }
+    if (!IMG && p.maxbits) {
+        // the checkpoint codec's max-abs of the new state pair (u^{n+1}, u^n)
+        const unsigned a = __reduce_max_sync(0xffffffffu, mxa);
+        const unsigned d = __reduce_max_sync(0xffffffffu, mxd);
+        if ((threadIdx.x & 31) == 0) {
+            if (a) atomicMax(p.maxbits + 2 * shot, a);
+            if (d) atomicMax(p.maxbits + 2 * shot + 1, d);
         }
     }
 }

@@ -13,14 +13,17 @@ from typing import Callable, List, Tuple
 
 def descend(v0, misfit_and_grad: Callable, iters: int = 5, max_dv: float = 50.0,
             vmin: float = 1500.0, vmax: float = 4500.0, shrink: float = 0.5,
-            max_tries: int = 6, c1: float = 1e-4) -> Tuple[object, List[float]]:
+            max_tries: int = 6, c1: float = 1e-4, mask=None) -> Tuple[object, List[float]]:
     """Minimises phi(v) from v0.  `misfit_and_grad(v)` returns (phi, grad) for a torch
     tensor or numpy array v; `v` keeps its type.  Returns (v, misfit history).  A trial
     step alpha * d with d = -grad * (max_dv / max|grad|) (cells held at a bound by the
     descent left out: projected gradient) is accepted when
     phi(clip(v + alpha d)) <= phi(v) + c1 * alpha * <grad, d>; otherwise alpha halves (at
     most max_tries times, then the loop stops).  Each line search starts from twice the
-    previously accepted alpha (at most 1)."""
+    previously accepted alpha (at most 1).  `mask` (same shape as v, values in [0, 1])
+    mutes the update where it is 0: the usual mute of the cells next to the sources and
+    receivers, where the gradient's near-field peaks would otherwise set the step size
+    and leave the rest of the model almost unchanged."""
     v = v0.clone() if hasattr(v0, "clone") else v0.copy()
     phi, g = misfit_and_grad(v)
     hist = [float(phi)]
@@ -29,6 +32,8 @@ def descend(v0, misfit_and_grad: Callable, iters: int = 5, max_dv: float = 50.0,
         # projected direction: cells at a bound that the descent would push outward stay
         blocked = ((v <= vmin) & (g > 0)) | ((v >= vmax) & (g < 0))
         gp = g * (~blocked)
+        if mask is not None:
+            gp = gp * mask
         gmax = float(abs(gp).max())
         if gmax == 0.0:
             break
