@@ -432,47 +432,45 @@ int step3d_launch(fwi_model *m, const StepParams &p, int ns, int mode, cudaStrea
     q.sig_z = sig_z(m);
     q.err = m->d_flag;
     const int TY = step3d_variant(g.M).ty;
-    CUtensorMap mc, ma, mb;
+    CUtensorMap mc, ma, mb, md, me;
+    FWI_TRY(field_map(m, p.cur, ns, 64 + 2 * g.M, TY + 2 * g.M, &mc));
+    FWI_TRY(field_map(m, p.prev, ns, 64, TY, &ma));
+    FWI_TRY(field_map(m, m->W.p, 1, 64, TY, &mb));
+    q.out = p.prev;
+    q.src_off = p.src_off;
+    q.wavelet = p.wavelet;
+    q.nt = p.nt;
+    q.n = p.n;
+    q.dt2 = p.dt2;
     if (mode == kModeStep) {
-        FWI_TRY(field_map(m, p.cur, ns, 64 + 2 * g.M, TY + 2 * g.M, &mc));
-        FWI_TRY(field_map(m, p.prev, ns, 64, TY, &ma));
-        FWI_TRY(field_map(m, m->W.p, 1, 64, TY, &mb));
-        q.out = p.prev;
-        q.src_off = p.src_off;
-        q.wavelet = p.wavelet;
-        q.nt = p.nt;
-        q.n = p.n;
-        q.dt2 = p.dt2;
         q.maxbits = p.maxbits;
+        md = ma;
+        me = ma;
     } else {
-        FWI_TRY(field_map(m, p.u_img, ns, 64 + 2 * g.M, TY + 2 * g.M, &mc));
-        FWI_TRY(field_map(m, p.cur, ns, 64, TY, &ma));
-        FWI_TRY(field_map(m, p.gacc, ns, 64, TY, &mb));
-        q.out = p.gacc;
+        FWI_TRY(field_map(m, p.u_img, ns, 64, TY, &md));
+        FWI_TRY(field_map(m, p.gacc, ns, 64, TY, &me));
+        q.g = p.gacc;
     }
     if (m->resident <= 0) m->resident = step3d_resident_ctas(g.M);
     const int tiles = ((g.nx + 63) / 64) * ((g.ny + TY - 1) / TY);
     const int nch = plan_zchunks(g.nz, g.M, tiles, ns, m->resident);
     q.zchunk = (g.nz + nch - 1) / nch;
-    FWI_CU(launch_step3d_tma(q, ns, mode, (g.nz + q.zchunk - 1) / q.zchunk, mc, ma, mb, s));
+    FWI_CU(launch_step3d_tma(q, ns, mode, (g.nz + q.zchunk - 1) / q.zchunk, mc, ma, mb, md, me,
+                             s));
     return FWI_OK;
 }
 
 bool use_step3d(const fwi_model *m) { return m->ndim == 3; }
 
-// The time step itself: in 2-D the register-streaming kernel (imaging fused), in 3-D the
-// TMA kernel, preceded by its imaging pass when the reverse step images.
+// The time step itself: in 2-D the register-streaming kernel, in 3-D the TMA kernel;
+// with `img` the reverse step that also accumulates the imaging condition.
 int raw_step(fwi_model *m, const StepParams &p, int ns, bool img, cudaStream_t s)
 {
     if (!use_step3d(m)) {
         FWI_CU(launch_step2d(p, ns, img, s));
         return FWI_OK;
     }
-    if (img) {
-        ++m->launches;
-        FWI_TRY(step3d_launch(m, p, ns, kModeImage, s));
-    }
-    return step3d_launch(m, p, ns, kModeStep, s);
+    return step3d_launch(m, p, ns, img ? kModeAdj : kModeStep, s);
 }
 
 int step_launch(fwi_model *m, const StepParams &p, int ns, bool img, int kind, cudaStream_t s)
@@ -699,7 +697,9 @@ int grad_setup(GradJob &j, fwi_model *m, const fwi_acq *acq, const float *wavele
     j.pf = base_params(m);
     j.pf.src_off = m->src_off.as<int64_t>();
     j.pf.wavelet = (const float *)wav;
-    j.pa = base_params(m);   // reverse sweep: no source, receivers injected after each step
+    j.pa = base_params(m);   // reverse sweep: receivers injected after each step; the
+                             // wavelet enters only the imaging term at the source point
+    j.pa.wavelet = (const float *)wav;
     j.tr = m->traces.as<float>();
     j.res = j.tr;            // residuals replace the traces in place
     j.slot_step.assign(slots > 0 ? slots : 1, -1);
@@ -780,6 +780,11 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
             if (j.step != mm)
                 return fail(FWI_ERR_CUDA, "internal: checkpoint schedule out of step");
             if (j.first_adj) {
+                // the receiver term of the imaging sum, from the traces before the misfit
+                // turns them into residuals
+                FWI_LAUNCH(m, launch_rec_image(g, j.tr, (const float *)j.dobs,
+                                               m->rec_off.as<int64_t>(), ns, nr, nt,
+                                               m->g64.as<double>(), s));
                 ++m->launches;   // the misfit is two launches
                 FWI_LAUNCH(m, launch_misfit(j.tr, (const float *)j.dobs, j.res,
                                             (int64_t)ns * nt * nr, m->partials.as<double>(),
@@ -792,11 +797,17 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
             j.pa.cur = m->mu[j.mcur].as<float>();        // mu^{m+1}
             j.pa.prev = m->mu[1 - j.mcur].as<float>();   // mu^{m+2} -> mu^m
             const bool img = mm < nt;                    // mu^{nt+1} = 0: no imaging at nt
-            j.pa.u_img = m->u[j.cur].as<float>();
+            j.pa.u_img = m->u[j.cur].as<float>();        // u^m
             j.pa.gacc = m->g32.as<float>();
+            j.pa.src_off = img ? m->src_off.as<int64_t>() : nullptr;
+            j.pa.n = mm;
             FWI_TRY(step_launch(m, j.pa, ns, img, 1, s));
             FWI_LAUNCH(m, launch_inject(g, j.pa.prev, m->rec_off.as<int64_t>(),
                                         m->inj.as<float>(), j.res, ns, nr, nt, mm - 1, s));
+            if (mm == 1)   // mu^1 is complete: the m = 0 source term of the imaging sum
+                FWI_LAUNCH(m, launch_src_image(g, j.pa.prev, m->src_off.as<int64_t>(),
+                                               m->W.as<float>(), j.pa.wavelet, j.pa.dt2, ns,
+                                               nt, m->g64.as<double>(), s));
             j.mcur = 1 - j.mcur;
             ++j.nadj;
             ++used;

@@ -34,9 +34,10 @@ struct Coefs {
 // One time step of the damped leapfrog on every shot of a batch:
 //   out = (2 cur + W (L cur) - (1 - s) prev + [dt^2 w[n] at the source]) / (1 + s),
 //   s = sig_z[z] + sig_y[y] + sig_x[x]  (= eta dt / 2),
-// written over `prev`.  With `u_img`/`gacc` set (imaging), additionally
-//   gacc += cur * (L u_img)
-// for the zero-lag imaging condition of the reverse sweep.
+// written over `prev`.  The reverse step with imaging (cur = mu^{m+1}, u_img = u^m) adds
+// no source to `out` and accumulates the transposed zero-lag imaging term
+//   gacc += u_img * (L cur),   at the source point  gacc -= dt^2 w[n] cur / W
+// (the receiver term of the same sum is added once from the traces: launch_rec_image).
 struct StepParams {
     Geom g;
     Coefs c;
@@ -48,7 +49,7 @@ struct StepParams {
     const float *wavelet;     // [nshots][nt]
     int nt, n;
     float dt2;
-    const float *u_img;       // imaging only
+    const float *u_img;       // imaging only: u^m
     float *gacc;              // imaging only: gradient accumulator
     int zchunk;               // planes per CTA along z
     int nzchunks;
@@ -63,6 +64,16 @@ cudaError_t launch_step2d(const StepParams &p, int nshots, bool imaging, cudaStr
 // ---- auxiliary kernels (k_aux.cu) ----
 cudaError_t launch_build_W(const Geom &g, int nb, const int64_t np[3], const float *v,
                            float dt, float *W, cudaStream_t s);
+// gacc64[rec] += 2 sum_k d[k] (d[k] - dobs[k]) per receiver: the receiver term of the
+// transposed imaging sum (traces d[shot][k][rec] hold u^{k+1} at the receivers)
+cudaError_t launch_rec_image(const Geom &g, const float *d, const float *dobs,
+                             const int64_t *rec_off, int nshots, int nrec, int nt,
+                             double *gacc64, cudaStream_t s);
+// gacc64[src] -= dt^2 w[0] mu1[src] / W[src] per shot: the m = 0 source term of the same
+// sum (no reverse step runs at m = 0)
+cudaError_t launch_src_image(const Geom &g, const float *mu1, const int64_t *src_off,
+                             const float *W, const float *wavelet, float dt2, int nshots,
+                             int nt, double *gacc64, cudaStream_t s);
 cudaError_t launch_sample(const Geom &g, const float *field, const int64_t *rec_off,
                           int nshots, int nrec, int nt, int n, float *traces,
                           cudaStream_t s);

@@ -86,6 +86,39 @@ __global__ void k_inject(int64_t fs, float *__restrict__ f, const int64_t *__res
     atomicAdd(f + (int64_t)s * fs + off[i], scale[i] * q[((int64_t)s * nt + sample) * nrec + r]);
 }
 
+// One thread per (shot, receiver): 2 sum_k d (d - dobs) in FP64, with the residual rounded
+// to FP32 exactly as the misfit kernel rounds it (the value injected into the adjoint).
+__global__ void k_rec_image(int64_t fs, const float *__restrict__ d,
+                            const float *__restrict__ dobs, const int64_t *__restrict__ off,
+                            int nshots, int nrec, int nt, double *__restrict__ g)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nshots * nrec) return;
+    const int s = i / nrec, r = i - s * nrec;
+    double acc = 0.0;
+    for (int k = 0; k < nt; ++k) {
+        const int64_t t = ((int64_t)s * nt + k) * nrec + r;
+        const float dd = d[t];
+        const float rr = dd - dobs[t];
+        acc = fma(2.0 * (double)dd, (double)rr, acc);
+    }
+    atomicAdd(g + (int64_t)s * fs + off[i], acc);
+}
+
+// One thread per shot: g[src] -= dt^2 w[0] mu^1[src] / W[src], the m = 0 source term of
+// the transposed imaging sum (the reverse sweep ends with the step that makes mu^1).
+__global__ void k_src_image(int64_t fs, const float *__restrict__ mu1,
+                            const int64_t *__restrict__ off, const float *__restrict__ W,
+                            const float *__restrict__ wav, float dt2, int nshots, int nt,
+                            double *__restrict__ g)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nshots) return;
+    const int64_t o = off[s];
+    const float f0 = dt2 * wav[(int64_t)s * nt];
+    g[(int64_t)s * fs + o] -= (double)f0 * (double)mu1[(int64_t)s * fs + o] / (double)W[o];
+}
+
 __global__ void k_gather_src(int64_t fs, const float *__restrict__ f,
                              const int64_t *__restrict__ off, const float *__restrict__ sc,
                              int nshots, int nt, int sample, float *__restrict__ x)
@@ -397,6 +430,27 @@ cudaError_t launch_inject(const Geom &g, float *field, const int64_t *rec_off,
     k_inject<<<(cnt + kThreads - 1) / kThreads, kThreads, 0, s>>>(g.field, field, rec_off,
                                                                  scale, q, nshots, nrec, nt,
                                                                  sample);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rec_image(const Geom &g, const float *d, const float *dobs,
+                             const int64_t *rec_off, int nshots, int nrec, int nt,
+                             double *gacc64, cudaStream_t s)
+{
+    int cnt = nshots * nrec;
+    if (cnt <= 0 || nt <= 0) return cudaSuccess;
+    k_rec_image<<<(cnt + kThreads - 1) / kThreads, kThreads, 0, s>>>(g.field, d, dobs, rec_off,
+                                                                     nshots, nrec, nt, gacc64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_src_image(const Geom &g, const float *mu1, const int64_t *src_off,
+                             const float *W, const float *wavelet, float dt2, int nshots,
+                             int nt, double *gacc64, cudaStream_t s)
+{
+    if (nshots <= 0) return cudaSuccess;
+    k_src_image<<<(nshots + kThreads - 1) / kThreads, kThreads, 0, s>>>(
+        g.field, mu1, src_off, W, wavelet, dt2, nshots, nt, gacc64);
     return cudaGetLastError();
 }
 

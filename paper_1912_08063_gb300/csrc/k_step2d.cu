@@ -7,8 +7,11 @@
 // (M floats either side, in 16-byte groups) straight from global memory: the row was read
 // by the neighbouring threads a few iterations earlier, so those loads hit L1/L2, and the
 // kernel needs neither shared memory nor barriers.  prev and W are read once, the new
-// row is written once with 16-byte stores: 16 bytes per point per step (imaging adds u_img
-// and the gradient accumulator).  Shots run on grid.z.
+// row is written once with 16-byte stores: 16 bytes per point per step.  The reverse step
+// with imaging (IMG) adds the transposed zero-lag imaging term g += u^m (L mu^{m+1}) with
+// the Laplacian it computes for the step (u^m read pointwise, g read and written: 28
+// bytes per point), and at the source point g -= dt^2 w[m] mu^{m+1} / W.  Shots run on
+// grid.z.
 #include "fwi_internal.h"
 
 namespace fwi {
@@ -44,20 +47,19 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
     float *__restrict__ prev = p.prev + sb;
     const float *__restrict__ uim = IMG ? p.u_img + sb : nullptr;
 
-    float4 q[Q], qu[IMG ? Q : 1];
+    float4 q[Q];
 #pragma unroll
     for (int i = 0; i < Q - 1; ++i) {
         const int z = z0 - M + i;
         const bool zin = z >= 0 && z < nz;
         q[i] = ld4(cur, (int64_t)z * plane, x0, px, zin);
-        if (IMG) qu[i] = ld4(uim, (int64_t)z * plane, x0, px, zin);
     }
     float sx[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) sx[e] = (x0 + e < nx) ? p.sig_x[x0 + e] : 0.0f;
     int src_z = -1, src_e = 0;
     float srcv = 0.0f;
-    if (!IMG && p.src_off) {
+    if (p.src_off) {
         const int64_t s = p.src_off[shot];
         const int sz = (int)(s / plane), sxx = (int)(s - (int64_t)sz * plane);
         if (sxx >= x0 && sxx < x0 + 4) {
@@ -72,18 +74,13 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
     for (int z = z0; z < z1; ++z) {
         const int zn = z + M;
         q[Q - 1] = ld4(cur, (int64_t)zn * plane, x0, px, zn < nz);
-        if (IMG) qu[Q - 1] = ld4(uim, (int64_t)zn * plane, x0, px, zn < nz);
         const int64_t row = (int64_t)z * plane;
         // x-window of the output row: groups x0 - M .. x0 + 3 + M
-        float w[4 + 2 * M], wu[IMG ? 4 + 2 * M : 1];
+        float w[4 + 2 * M];
 #pragma unroll
         for (int g4 = 0; g4 < 2 * W4 + 1; ++g4) {
             const float4 v = (g4 == W4) ? q[M] : ld4(cur, row, x0 + 4 * (g4 - W4), px, true);
             w[4 * g4] = v.x, w[4 * g4 + 1] = v.y, w[4 * g4 + 2] = v.z, w[4 * g4 + 3] = v.w;
-            if (IMG) {
-                const float4 u = (g4 == W4) ? qu[M] : ld4(uim, row, x0 + 4 * (g4 - W4), px, true);
-                wu[4 * g4] = u.x, wu[4 * g4 + 1] = u.y, wu[4 * g4 + 2] = u.z, wu[4 * g4 + 3] = u.w;
-            }
         }
         float lx[4];
 #pragma unroll
@@ -120,7 +117,7 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
             for (int e = 0; e < 4; ++e) {
                 const float s = sx[e] + sz;
                 float v = fmaf(s - 1.0f, pp[e], rhs[e]);
-                if (z == src_z && e == src_e) v += srcv;
+                if (!IMG && z == src_z && e == src_e) v += srcv;
                 rhs[e] = __fdividef(v, 1.0f + s);
             }
             *(float4 *)(prev + row + x0) = make_float4(rhs[0], rhs[1], rhs[2], rhs[3]);
@@ -133,38 +130,26 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
                 }
             }
             if (IMG) {
-                float lu[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-                    for (int k = 1; k <= M; ++k) {
-                        const float s = wu[M + e + k] + wu[M + e - k];
-                        if (k & 1) a0 = fmaf(p.c.cx[k], s, a0);
-                        else a1 = fmaf(p.c.cx[k], s, a1);
-                    }
-                    lu[e] = a0 + a1;
+                // g += u^m (L mu^{m+1});  at the source point g -= dt^2 w[m] mu^{m+1} / W
+                const float4 uv = __ldg((const float4 *)(uim + row + x0));
+                const float4 gv = *(const float4 *)(p.gacc + sb + row + x0);
+                float2 g0 = __ffma2_rn(lo2(uv), l0, lo2(gv));
+                float2 g1 = __ffma2_rn(hi2(uv), l1, hi2(gv));
+                if (z == src_z) {
+                    // g[e] -= srcv c[e] / W[e] at the source point e
+                    const float ce = src_e == 0 ? c.x : src_e == 1 ? c.y : src_e == 2 ? c.z : c.w;
+                    const float we = src_e == 0 ? Wv.x : src_e == 1 ? Wv.y : src_e == 2 ? Wv.z : Wv.w;
+                    const float qv = __fdividef(ce, we);
+                    if (src_e == 0) g0.x = fmaf(-srcv, qv, g0.x);
+                    else if (src_e == 1) g0.y = fmaf(-srcv, qv, g0.y);
+                    else if (src_e == 2) g1.x = fmaf(-srcv, qv, g1.x);
+                    else g1.y = fmaf(-srcv, qv, g1.y);
                 }
-                float2 ua = make_float2(0.f, 0.f), ub = ua;
-#pragma unroll
-                for (int k = 1; k <= M; ++k) {
-                    const float2 cc = make_float2(p.c.cz[k], p.c.cz[k]);
-                    ua = __ffma2_rn(cc, __fadd2_rn(lo2(qu[M + k]), lo2(qu[M - k])), ua);
-                    ub = __ffma2_rn(cc, __fadd2_rn(hi2(qu[M + k]), hi2(qu[M - k])), ub);
-                }
-                const float2 m0 = __ffma2_rn(c0, lo2(qu[M]), __fadd2_rn(ua, make_float2(lu[0], lu[1])));
-                const float2 m1 = __ffma2_rn(c0, hi2(qu[M]), __fadd2_rn(ub, make_float2(lu[2], lu[3])));
-                float4 gv = *(float4 *)(p.gacc + sb + row + x0);
-                const float2 g0 = __ffma2_rn(lo2(c), m0, lo2(gv));
-                const float2 g1 = __ffma2_rn(hi2(c), m1, hi2(gv));
                 *(float4 *)(p.gacc + sb + row + x0) = make_float4(g0.x, g0.y, g1.x, g1.y);
             }
         }
 #pragma unroll
-        for (int i = 0; i < Q - 1; ++i) {
-            q[i] = q[i + 1];
-            if (IMG) qu[i] = qu[i + 1];
-        }
+        for (int i = 0; i < Q - 1; ++i) q[i] = q[i + 1];
     }
     if (!IMG && p.maxbits) {
         // the checkpoint codec's max-abs of the new state pair (u^{n+1}, u^n)

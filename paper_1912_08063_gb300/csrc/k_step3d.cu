@@ -9,15 +9,15 @@
 
 namespace fwi {
 
-// Configuration per radius; FWI_STEP3D_VARIANT=<ty>,<ry>,<pf>,<unroll> overrides it for
+// Configuration per radius; FWI_STEP3D_VARIANT=<ty>,<ry>,<pf>,<u>,<opt> overrides it for
 // tuning runs (only the instantiated combinations are accepted).
 Step3dVariant step3d_variant(int M)
 {
-    Step3dVariant v = M == 8 ? Step3dVariant{32, 2, 2, false} : Step3dVariant{16, 2, 3, false};
+    Step3dVariant v = M == 8 ? Step3dVariant{32, 2, 2, 3, 0} : Step3dVariant{16, 2, 3, 2, 0};
     if (const char *e = std::getenv("FWI_STEP3D_VARIANT")) {
-        int ty, ry, pf, un;
-        if (std::sscanf(e, "%d,%d,%d,%d", &ty, &ry, &pf, &un) == 4) {
-            Step3dVariant w{ty, ry, pf, un != 0};
+        int ty, ry, pf, un, opt;
+        if (std::sscanf(e, "%d,%d,%d,%d,%d", &ty, &ry, &pf, &un, &opt) == 5) {
+            Step3dVariant w{ty, ry, pf, un, opt};
             const Step3dKernelInfo k = M == 8 ? step3d_kernel_m8(w, 0) : step3d_kernel_m4(w, 0);
             if (k.fn) v = w;
         }
@@ -58,7 +58,8 @@ int step3d_resident_ctas(int M)
 
 cudaError_t launch_step3d_tma(const Step3dParams &p, int nshots, int mode, int nchunks,
                               const CUtensorMap &mc, const CUtensorMap &ma,
-                              const CUtensorMap &mb, cudaStream_t s)
+                              const CUtensorMap &mb, const CUtensorMap &md,
+                              const CUtensorMap &me, cudaStream_t s)
 {
     const Step3dKernelInfo k = kernel_info(p.M, mode);
     if (!k.fn) return cudaErrorInvalidValue;
@@ -68,7 +69,7 @@ cudaError_t launch_step3d_tma(const Step3dParams &p, int nshots, int mode, int n
     const int TY = step3d_variant(p.M).ty;
     const int tiles = ((p.nx + 63) / 64) * ((p.ny + TY - 1) / TY);
     dim3 grid(tiles, nchunks, nshots);
-    k.fn<<<grid, k.threads, k.smem, s>>>(p, mc, ma, mb);
+    k.fn<<<grid, k.threads, k.smem, s>>>(p, mc, ma, mb, md, me);
     return cudaGetLastError();
 }
 

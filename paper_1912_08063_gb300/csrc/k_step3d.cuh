@@ -1,32 +1,40 @@
 // 3-D time step on GB300 (sm_103a): TMA-staged z-streaming stencil (kernel template).
 //
 // One template serves two modes on the same stencil machinery:
-//   kModeStep   out = (2 c + W (L c) - (1 - s) prev [+ dt^2 w at the source]) / (1 + s),
-//               written over prev           (Eq. 3 with the sponge; forward and, in the
-//               W-weighted variable mu = W nu, the reverse step)
-//   kModeImage  g += aux * (L c)            (zero-lag imaging: g += mu^{m+1} L u^m)
-// where c is the streamed field (u^n, mu^{m+1} or u^m) and L the order-2M Laplacian with
-// zero outside the computed grid.
+//   kModeStep  out = (2 c + W (L c) - (1 - s) prev [+ dt^2 w[n] at the source]) / (1 + s),
+//              written over prev (Eq. 3 with the sponge: the forward step, c = u^n)
+//   kModeAdj   the same update without the source (the reverse step in the W-weighted
+//              adjoint variable mu = W nu, c = mu^{m+1}), and the imaging condition
+//              g += aux * (L c) with aux = u^m, g -= dt^2 w[m] c / W at the source point
+// where L is the order-2M Laplacian with zero outside the computed grid.  kModeAdj uses
+// the transposed form of the zero-lag imaging sum: substituting the forward recursion
+// for W L u^m in sum_m mu^{m+1} (L u^m) and the reverse recursion for the result gives
+// sum_m u^m (L mu^{m+1}) plus a source-point term (here) and a receiver term (added
+// once from the traces), so the reverse step images with the Laplacian it computes
+// anyway instead of a second pass over u^m.
 //
 // A CTA owns a 64 x TY tile of the (x, y) plane and a chunk of z-planes:
 //   * one elected thread issues TMA loads (cp.async.bulk.tensor, 4-D maps over
 //     [shot][z][y][x]) of the plane's halo tile (64 + 2M) x (TY + 2M) into a ring of
-//     SH = M + 1 + P shared-memory stages, and of the pointwise tiles (prev and W, or
-//     aux and g) into a ring of SP = P + 1 stages; completion is tracked by mbarriers
-//     with transaction counts and every wait is bounded;
+//     SH = M + 1 + P shared-memory stages, and of the pointwise tiles (prev and W, plus
+//     aux and g in kModeAdj) into a ring of SP = P + 1 stages; completion is tracked by
+//     mbarriers with transaction counts and every wait is bounded;
 //   * out-of-grid halo cells are zero-filled by the TMA unit (the Dirichlet condition);
 //   * each thread computes 4 (x) x RY (y) points: the z-neighbours come from a register
-//     queue of 2M + 1 planes, the x/y-neighbours from the resident halo stage of the
+//     queue of 2M + U planes that shifts by U every U planes (U - 1 spare slots halve or
+//     third the register moves), the x/y-neighbours from the resident halo stage of the
 //     output plane (it arrived M planes earlier and the ring keeps it);
 //   * y and z sums use packed FP32x2 FMAs and split accumulators (independent chains);
 //     the sponge division is a fast reciprocal, branch-free;
 //   * results are stored with 16-byte stores straight from registers.
 // Measured on GB300 (radius 8, 512^3): this layout beat a variant that unrolls the
-// plane loop so the queue rotates at compile time (larger code, slower) and a variant
-// that reads the forward z-neighbours from the resident stages instead of registers
-// (more shared-memory loads, slower).
-// DRAM traffic per point and step: c once (halo re-reads hit L2), two pointwise fields
-// once, one write: 16 bytes in either mode.
+// plane loop so the queue rotates at compile time (larger code, slower), a variant that
+// reads the forward z-neighbours from the resident stages instead of registers (more
+// shared-memory loads, slower), and one thread per 4 x 1 points (more y loads, slower);
+// U = 2 or 3 beat U = 1 by 7 %.
+// DRAM traffic per point and step: c once (halo re-reads hit L2), the pointwise fields
+// once, the writes once: 16 bytes (kModeStep) or 28 bytes (kModeAdj: + aux, g read and
+// written).
 #pragma once
 
 #include <cuda.h>
@@ -91,17 +99,42 @@ __device__ __forceinline__ void tma_load4(void *dst, const CUtensorMap *map, int
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 
-template <int M_, int TY_, int RY_, int P_>
+// Source-point term of the transposed imaging sum at point e of a 4-point group:
+// g[e] -= srcv c[e] / W[e]  (srcv = dt^2 w[m]).
+__device__ __forceinline__ void src_image(float2 &g0, float2 &g1, float4 c, float4 W, int e,
+                                          float srcv)
+{
+    const float ce = e == 0 ? c.x : e == 1 ? c.y : e == 2 ? c.z : c.w;
+    const float we = e == 0 ? W.x : e == 1 ? W.y : e == 2 ? W.z : W.w;
+    const float q = __fdividef(ce, we);
+    if (e == 0) g0.x = fmaf(-srcv, q, g0.x);
+    else if (e == 1) g0.y = fmaf(-srcv, q, g0.y);
+    else if (e == 2) g1.x = fmaf(-srcv, q, g1.x);
+    else g1.y = fmaf(-srcv, q, g1.y);
+}
+
+// Options of the plane loop (bits of Cfg::F):
+//   kPackX     x-sums as packed FP32x2 on register pairs that are 64-bit aligned (even
+//              offsets pair points (0,1) and (2,3), odd offsets pair (1,2))
+//   kInterior  rows with no damping (s = 0 at all four points) skip the sponge division
+constexpr int kPackX = 1, kInterior = 2;
+
+template <int M_, int TY_, int RY_, int P_, int U_, int F_, int NPW_>
 struct Cfg {
-    static constexpr int M = M_, TY = TY_, RY = RY_, P = P_;
+    static constexpr int M = M_, TY = TY_, RY = RY_, P = P_, U = U_, F = F_;
+    static constexpr int NPW = NPW_;   // pointwise tiles per stage
     static constexpr int TX = 64, RX = 4;
     static constexpr int NTX = TX / RX, NTY = TY / RY, NT = NTX * NTY;
     static constexpr int SX = TX + 2 * M, SY = TY + 2 * M;
     static constexpr int SH = M + 1 + P, SP = P + 1, Q = 2 * M + 1;
+    // the z-queue holds Q + U - 1 planes and shifts by U every U planes
+    static constexpr int L = Q + U - 1;
+    static_assert(U >= 1 && U <= 4, "queue shift interval");
+    static_assert(M % 2 == 0, "packed x-sums pair even offsets");
     static constexpr int HALO_BYTES = SX * SY * 4;
     static constexpr int TILE_BYTES = TX * TY * 4;
     static constexpr int HALO_STRIDE = (HALO_BYTES + 1023) / 1024 * 1024;
-    static constexpr int PW_STRIDE = (2 * TILE_BYTES + 1023) / 1024 * 1024;
+    static constexpr int PW_STRIDE = (NPW * TILE_BYTES + 1023) / 1024 * 1024;
     static constexpr int SMEM = SH * HALO_STRIDE + SP * PW_STRIDE + 1024 /* barriers */ + 1024;
 };
 
@@ -109,7 +142,7 @@ struct Cfg {
 template <class C, int MODE>
 struct Ctx {
     const Step3dParams *p;
-    const CUtensorMap *mc, *ma, *mb;
+    const CUtensorMap *mc, *ma, *mb, *md, *me;
     unsigned char *halo, *pw;
     uint64_t *bar_h, *bar_p;
     int *abort_flag;
@@ -117,12 +150,12 @@ struct Ctx {
     int h_issued, p_issued;   // loads issued so far (thread 0's view)
     int cur_it;               // iteration being executed
     float sxp[4], syr[C::RY];
-    bool xin;
+    bool xin, sxnz;            // sxnz: some sig_x of this thread's columns is nonzero
     int64_t sb;
     int src_j, src_r, src_e;   // source node in this thread's block (src_j < 0: none)
     float srcv;
     unsigned mxa, mxd;         // bits of max|out| and max|out - c| (p->maxbits set)
-    float4 q[C::Q][C::RY];
+    float4 q[C::L][C::RY];
 
     __device__ __forceinline__ void issue_halo(int it)
     {
@@ -137,19 +170,23 @@ struct Ctx {
         const int st = o % C::SP;
         uint64_t *b = bar_p + st;
         unsigned char *d = pw + st * C::PW_STRIDE;
-        mbar_expect_tx(b, 2 * C::TILE_BYTES);
+        mbar_expect_tx(b, C::NPW * C::TILE_BYTES);
         tma_load4(d, ma, bx * C::TX, by * C::TY, za + o, shot, b);
-        tma_load4(d + C::TILE_BYTES, mb, bx * C::TX, by * C::TY, za + o,
-                  MODE == kModeStep ? 0 : shot, b);
+        tma_load4(d + C::TILE_BYTES, mb, bx * C::TX, by * C::TY, za + o, 0, b);
+        if (C::NPW == 4) {
+            tma_load4(d + 2 * C::TILE_BYTES, md, bx * C::TX, by * C::TY, za + o, shot, b);
+            tma_load4(d + 3 * C::TILE_BYTES, me, bx * C::TX, by * C::TY, za + o, shot, b);
+        }
     }
 
-    // One plane iteration `it`; the queue slot of plane (it - 2M + i) is (R + 1 + i) % Q,
-    // so the newest plane lands in slot R.  Returns false when the loop must stop.
+    // One plane iteration `it`; the queue slot of plane (it - 2M + i) is R - 2M + i
+    // (R >= 2M), so the newest plane lands in slot R.  Returns false when the loop must
+    // stop.
     template <int R>
     __device__ __forceinline__ bool plane(int it)
     {
-        constexpr int M = C::M, Q = C::Q, SX = C::SX, SH = C::SH, SP = C::SP, TX = C::TX,
-                      RY = C::RY;
+        constexpr int M = C::M, SX = C::SX, SH = C::SH, SP = C::SP, TX = C::TX, RY = C::RY;
+        static_assert(R >= 2 * M && R < C::L, "queue slot");
         if (it >= niter) return false;
         cur_it = it;
         // every thread passes this barrier in every iteration, so an abort raised by any
@@ -186,7 +223,7 @@ struct Ctx {
         const float *hj = (const float *)(halo + ((it - M) % SH) * C::HALO_STRIDE);
         const float *ta = (const float *)(pw + (o % SP) * C::PW_STRIDE);
         const float *tb = ta + TX * C::TY;
-        const float sz = MODE == kModeStep ? p->sig_z[j] : 0.0f;
+        const float sz = p->sig_z[j];
 
         // y: rows ty*RY .. ty*RY + 2M + RY - 1 of the halo tile, two accumulators per half
         float2 ya[RY][2], yb[RY][2];
@@ -227,22 +264,49 @@ struct Ctx {
                 w[4 * c4 + 3] = v.w;
             }
             float lx[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                float a0 = 0.0f, a1 = 0.0f;
+            if (C::F & kPackX) {
+                // offsets k even: pairs (0,1), (2,3) start at even w indices; k odd: the
+                // pair (1,2) does, points 0 and 3 stay scalar
+                float2 xa = make_float2(0.f, 0.f), xb = xa, xm = xa;
+                float x0 = 0.0f, x3 = 0.0f;
 #pragma unroll
                 for (int k = 1; k <= M; ++k) {
-                    const float s = w[M + e + k] + w[M + e - k];
-                    if (k & 1) a0 = fmaf(p->cx[k], s, a0);
-                    else a1 = fmaf(p->cx[k], s, a1);
+                    const float ck = p->cx[k];
+                    const float2 ck2 = make_float2(ck, ck);
+                    if ((k & 1) == 0) {
+                        xa = __ffma2_rn(ck2, __fadd2_rn(make_float2(w[M + k], w[M + k + 1]),
+                                                        make_float2(w[M - k], w[M - k + 1])), xa);
+                        xb = __ffma2_rn(ck2, __fadd2_rn(make_float2(w[M + 2 + k], w[M + 3 + k]),
+                                                        make_float2(w[M + 2 - k], w[M + 3 - k])), xb);
+                    } else {
+                        xm = __ffma2_rn(ck2, __fadd2_rn(make_float2(w[M + 1 + k], w[M + 2 + k]),
+                                                        make_float2(w[M + 1 - k], w[M + 2 - k])), xm);
+                        x0 = fmaf(ck, w[M + k] + w[M - k], x0);
+                        x3 = fmaf(ck, w[M + 3 + k] + w[M + 3 - k], x3);
+                    }
                 }
-                lx[e] = a0 + a1;
+                lx[0] = xa.x + x0;
+                lx[1] = xa.y + xm.x;
+                lx[2] = xb.x + xm.y;
+                lx[3] = xb.y + x3;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+                    for (int k = 1; k <= M; ++k) {
+                        const float s = w[M + e + k] + w[M + e - k];
+                        if (k & 1) a0 = fmaf(p->cx[k], s, a0);
+                        else a1 = fmaf(p->cx[k], s, a1);
+                    }
+                    lx[e] = a0 + a1;
+                }
             }
-            // z from the register queue: plane j +- k sits in slot (R + 1 + M +- k) % Q
+            // z from the register queue: plane j +- k sits in slot R - M +- k
             float2 za0 = make_float2(0.f, 0.f), za1 = za0, zb0 = za0, zb1 = za0;
 #pragma unroll
             for (int k = 1; k <= M; ++k) {
-                const float4 up = q[(R + 1 + M + k) % Q][r], dn = q[(R + 1 + M - k) % Q][r];
+                const float4 up = q[R - M + k][r], dn = q[R - M - k][r];
                 const float2 cc = p->cz2[k];
                 if (k & 1) {
                     za0 = __ffma2_rn(cc, __fadd2_rn(lo2(up), lo2(dn)), za0);
@@ -252,7 +316,7 @@ struct Ctx {
                     zb1 = __ffma2_rn(cc, __fadd2_rn(hi2(up), hi2(dn)), zb1);
                 }
             }
-            const float4 cz4 = q[(R + 1 + M) % Q][r];
+            const float4 cz4 = q[R - M][r];
             const float2 c0 = p->c02;
             const float2 s0 = __fadd2_rn(__fadd2_rn(za0, zb0), __fadd2_rn(ya[r][0], yb[r][0]));
             const float2 s1 = __fadd2_rn(__fadd2_rn(za1, zb1), __fadd2_rn(ya[r][1], yb[r][1]));
@@ -260,53 +324,78 @@ struct Ctx {
             const float2 l1 = __ffma2_rn(c0, hi2(cz4), __fadd2_rn(s1, make_float2(lx[2], lx[3])));
 
             const int y = y0 + r;
-            const float4 A = *(const float4 *)(ta + (ty * RY + r) * TX + tx * 4);
-            const float4 B = *(const float4 *)(tb + (ty * RY + r) * TX + tx * 4);
+            const int toff = (ty * RY + r) * TX + tx * 4;
+            const float4 A = *(const float4 *)(ta + toff);   // prev
+            const float4 B = *(const float4 *)(tb + toff);   // W
             const int64_t base = (int64_t)j * p->plane + (int64_t)y * p->px + x0;
-            float4 out;
-            if (MODE == kModeStep) {
-                // A = prev, B = W:  out = (2c + W lap - (1 - s) prev) / (1 + s)
-                const float2 two = make_float2(2.0f, 2.0f);
-                const float2 r0 = __ffma2_rn(lo2(B), l0, __fmul2_rn(two, lo2(cz4)));
-                const float2 r1 = __ffma2_rn(hi2(B), l1, __fmul2_rn(two, hi2(cz4)));
-                float rhs[4] = {r0.x, r0.y, r1.x, r1.y};
-                const float pv[4] = {A.x, A.y, A.z, A.w};
+            const bool store = xin && y < p->ny;
+            const bool at_src = j == src_j && r == src_r;
+            // out = (2c + W lap - (1 - s) prev [+ dt^2 w at the source]) / (1 + s)
+            const float2 two = make_float2(2.0f, 2.0f);
+            const float2 r0 = __ffma2_rn(lo2(B), l0, __fmul2_rn(two, lo2(cz4)));
+            const float2 r1 = __ffma2_rn(hi2(B), l1, __fmul2_rn(two, hi2(cz4)));
+            float rhs[4] = {r0.x, r0.y, r1.x, r1.y};
+            const float pv[4] = {A.x, A.y, A.z, A.w};
+            const bool inj = MODE == kModeStep && at_src;
+            if (!(C::F & kInterior) || sxnz || syr[r] != 0.0f || sz != 0.0f) {
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const float s = sxp[e] + syr[r] + sz;
                     float v = fmaf(s - 1.0f, pv[e], rhs[e]);
-                    if (j == src_j && r == src_r && e == src_e) v += srcv;
+                    if (inj && e == src_e) v += srcv;
                     rhs[e] = __fdividef(v, 1.0f + s);
                 }
-                out = make_float4(rhs[0], rhs[1], rhs[2], rhs[3]);
-                if (p->maxbits) {
-                    // |x| as bits: unsigned order is magnitude order, NaN above infinity
-                    const float cz[4] = {cz4.x, cz4.y, cz4.z, cz4.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        mxa = max(mxa, __float_as_uint(rhs[e]) & 0x7fffffffu);
-                        mxd = max(mxd, __float_as_uint(rhs[e] - cz[e]) & 0x7fffffffu);
-                    }
-                }
             } else {
-                // A = aux (mu^{m+1}), B = g
-                const float2 g0 = __ffma2_rn(lo2(A), l0, lo2(B));
-                const float2 g1 = __ffma2_rn(hi2(A), l1, hi2(B));
-                out = make_float4(g0.x, g0.y, g1.x, g1.y);
+                // s = 0: (2c + W lap - prev) / 1
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    float v = rhs[e] - pv[e];
+                    if (inj && e == src_e) v += srcv;
+                    rhs[e] = v;
+                }
             }
-            if (xin && y < p->ny) *(float4 *)(p->out + sb + base) = out;
+            if (MODE == kModeStep && p->maxbits) {
+                // |x| as bits: unsigned order is magnitude order, NaN above infinity
+                const float cz[4] = {cz4.x, cz4.y, cz4.z, cz4.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    mxa = max(mxa, __float_as_uint(rhs[e]) & 0x7fffffffu);
+                    mxd = max(mxd, __float_as_uint(rhs[e] - cz[e]) & 0x7fffffffu);
+                }
+            }
+            if (store) *(float4 *)(p->out + sb + base) = make_float4(rhs[0], rhs[1], rhs[2], rhs[3]);
+            if (MODE == kModeAdj) {
+                // g += u^m * (L mu^{m+1});  at the source point g -= dt^2 w[m] mu^{m+1} / W
+                const float *td = ta + 2 * TX * C::TY, *te = ta + 3 * TX * C::TY;
+                const float4 Ua = *(const float4 *)(td + toff);
+                const float4 G = *(const float4 *)(te + toff);
+                float2 g0 = __ffma2_rn(lo2(Ua), l0, lo2(G));
+                float2 g1 = __ffma2_rn(hi2(Ua), l1, hi2(G));
+                if (at_src) src_image(g0, g1, cz4, B, src_e, srcv);
+                if (store) *(float4 *)(p->g + sb + base) = make_float4(g0.x, g0.y, g1.x, g1.y);
+            }
         }
         return true;
     }
 };
 
-template <int M, int TY, int RY, int P, int MODE>
-__global__ void __launch_bounds__(Cfg<M, TY, RY, P>::NT, (M == 4 ? 2 : 1))
-k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUtensorMap map_c,
-             const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b)
+// Runs planes it .. it + U - 1 of one queue-shift group (newest plane in slot L - U + u).
+template <class C, int MODE, int u>
+__device__ __forceinline__ bool plane_group(Ctx<C, MODE> &c, int it)
 {
-    using C = Cfg<M, TY, RY, P>;
-    constexpr int Q = C::Q;
+    if (!c.template plane<C::L - C::U + u>(it + u)) return false;
+    if constexpr (u + 1 < C::U) return plane_group<C, MODE, u + 1>(c, it);
+    return true;
+}
+
+template <int M, int TY, int RY, int P, int U, int F, int MODE>
+__global__ void __launch_bounds__(Cfg<M, TY, RY, P, U, F, 2>::NT, (M == 4 ? 2 : 1))
+k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUtensorMap map_c,
+             const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+             const __grid_constant__ CUtensorMap map_d, const __grid_constant__ CUtensorMap map_e)
+{
+    using C = Cfg<M, TY, RY, P, U, F, MODE == kModeAdj ? 4 : 2>;
+    constexpr int L = C::L;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
 
@@ -315,6 +404,8 @@ k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUt
     c.mc = &map_c;
     c.ma = &map_a;
     c.mb = &map_b;
+    c.md = &map_d;
+    c.me = &map_e;
     c.halo = smem;
     c.pw = smem + C::SH * C::HALO_STRIDE;
     c.bar_h = (uint64_t *)(c.pw + C::SP * C::PW_STRIDE);
@@ -347,6 +438,7 @@ k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUt
     c.hy = c.by * C::TY - M;
 #pragma unroll
     for (int e = 0; e < 4; ++e) c.sxp[e] = (c.x0 + e < p.nx) ? p.sig_x[c.x0 + e] : 0.0f;
+    c.sxnz = c.sxp[0] != 0.0f || c.sxp[1] != 0.0f || c.sxp[2] != 0.0f || c.sxp[3] != 0.0f;
 #pragma unroll
     for (int r = 0; r < RY; ++r) c.syr[r] = (c.y0 + r < p.ny) ? p.sig_y[c.y0 + r] : 0.0f;
     c.xin = c.x0 < p.nx;
@@ -355,7 +447,7 @@ k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUt
     c.src_r = c.src_e = 0;
     c.srcv = 0.0f;
     c.mxa = c.mxd = 0u;
-    if (MODE == kModeStep && p.src_off) {
+    if (p.src_off) {
         const int64_t s = p.src_off[c.shot];
         const int sz = (int)(s / p.plane), rem = (int)(s - (int64_t)sz * p.plane);
         const int sy = rem / p.px, sx = rem - sy * p.px;
@@ -367,7 +459,7 @@ k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUt
         }
     }
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
+    for (int i = 0; i < L; ++i)
 #pragma unroll
         for (int r = 0; r < RY; ++r) c.q[i][r] = make_float4(0.f, 0.f, 0.f, 0.f);
 
@@ -379,13 +471,13 @@ k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUt
         for (int it = 0; it < C::P && it < c.niter; ++it) c.issue_halo(it);
     }
 
-    for (int it = 0; it < c.niter; ++it) {
-        // shift the queue: slot Q - 1 receives the plane that arrives in this iteration
+    for (int it = 0; it < c.niter; it += C::U) {
+        // shift the queue by U: slots L - U .. L - 1 receive the planes of this group
 #pragma unroll
-        for (int i = 0; i < Q - 1; ++i)
+        for (int i = 0; i < L - C::U; ++i)
 #pragma unroll
-            for (int r = 0; r < RY; ++r) c.q[i][r] = c.q[i + 1][r];
-        if (!c.plane<Q - 1>(it)) break;
+            for (int r = 0; r < RY; ++r) c.q[i][r] = c.q[i + C::U][r];
+        if (!plane_group<C, MODE, 0>(c, it)) break;
     }
     if (MODE == kModeStep && p.maxbits) {
         // every thread reaches this point (the loop above has no early return)
@@ -407,6 +499,38 @@ k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUt
         for (int o = failed - 2 * M > 0 ? failed - 2 * M : 0; o < c.p_issued; ++o)
             (void)mbar_wait(c.bar_p + o % C::SP, (o / C::SP) & 1);
     }
+}
+
+// Largest prefetch depth <= P whose kModeAdj stages (four pointwise tiles) fit the
+// shared memory of the CTAs resident per SM.
+template <int M, int TY, int RY, int P, int U, int F>
+constexpr int adj_prefetch()
+{
+    constexpr int budget = (M == 4 ? 232448 / 2 - 1024 : 232448);
+    if constexpr (P > 1 && Cfg<M, TY, RY, P, U, F, 4>::SMEM > budget)
+        return adj_prefetch<M, TY, RY, P - 1, U, F>();
+    return P;
+}
+
+// Kernel, block size and dynamic shared memory of one configuration in `mode`.
+template <int M, int TY, int RY, int P, int U, int F>
+Step3dKernelInfo kernel_info(int mode)
+{
+    Step3dKernelInfo k;
+    if (mode == kModeStep) {
+        using C = Cfg<M, TY, RY, P, U, F, 2>;
+        k.fn = (Step3dKernel)k_step3d_tma<M, TY, RY, P, U, F, kModeStep>;
+        k.threads = C::NT;
+        k.smem = C::SMEM;
+    } else {
+        constexpr int PA = adj_prefetch<M, TY, RY, P, U, F>();
+        using C = Cfg<M, TY, RY, PA, U, F, 4>;
+        static_assert(C::SMEM <= 232448, "shared memory of the reverse-step kernel");
+        k.fn = (Step3dKernel)k_step3d_tma<M, TY, RY, PA, U, F, kModeAdj>;
+        k.threads = C::NT;
+        k.smem = C::SMEM;
+    }
+    return k;
 }
 
 }  // namespace s3d

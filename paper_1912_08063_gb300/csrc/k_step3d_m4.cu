@@ -3,26 +3,13 @@
 
 namespace fwi {
 
-namespace {
-template <int TY, int RY, int P>
-Step3dKernelInfo info(int mode)
-{
-    using C = s3d::Cfg<4, TY, RY, P>;
-    Step3dKernelInfo k;
-    k.fn = mode == kModeStep ? (Step3dKernel)s3d::k_step3d_tma<4, TY, RY, P, kModeStep>
-                             : (Step3dKernel)s3d::k_step3d_tma<4, TY, RY, P, kModeImage>;
-    k.threads = C::NT;
-    k.smem = C::SMEM;
-    return k;
-}
-}  // namespace
-
 Step3dKernelInfo step3d_kernel_m4(const Step3dVariant &v, int mode)
 {
-    if (v.unroll) return Step3dKernelInfo{nullptr, 0, 0};
-    if (v.ty == 16 && v.ry == 2 && v.pf == 3) return info<16, 2, 3>(mode);
-    if (v.ty == 16 && v.ry == 2 && v.pf == 4) return info<16, 2, 4>(mode);
-    if (v.ty == 32 && v.ry == 2 && v.pf == 3) return info<32, 2, 3>(mode);
+    if (v.ty == 16 && v.ry == 2 && v.pf == 3 && v.opt == 0) {
+        if (v.u == 1) return s3d::kernel_info<4, 16, 2, 3, 1, 0>(mode);
+        if (v.u == 2) return s3d::kernel_info<4, 16, 2, 3, 2, 0>(mode);
+        if (v.u == 3) return s3d::kernel_info<4, 16, 2, 3, 3, 0>(mode);
+    }
     return Step3dKernelInfo{nullptr, 0, 0};
 }
 

@@ -10,8 +10,9 @@
 
 namespace fwi {
 
-constexpr int kModeStep = 0;    // out = damped leapfrog update, written over prev
-constexpr int kModeImage = 1;   // g += aux * (L c)
+constexpr int kModeStep = 0;   // out = damped leapfrog update, written over prev
+constexpr int kModeAdj = 1;    // the same update (no source) and g += aux * (L c), with the
+                               // source-point term g -= dt^2 w[n] c / W
 
 struct Step3dParams {
     int M;
@@ -21,8 +22,9 @@ struct Step3dParams {
     float cx[kMaxM + 1], cy[kMaxM + 1], cz[kMaxM + 1], c0;
     float2 cy2[kMaxM + 1], cz2[kMaxM + 1], c02;   // the same weights as packed pairs
     const float *sig_x, *sig_y, *sig_z;
-    float *out;                   // kModeStep: prev (in place); kModeImage: g
-    const int64_t *src_off;       // kModeStep only, may be null
+    float *out;                   // the new state, over prev (in place)
+    float *g;                     // kModeAdj: gradient accumulator
+    const int64_t *src_off;       // may be null (kModeStep: injection; kModeAdj: g term)
     const float *wavelet;
     int nt, n;
     float dt2;
@@ -33,11 +35,11 @@ struct Step3dParams {
 };
 
 // Kernel configurations of the 3-D step: tile height, points per thread along y,
-// prefetch depth and whether the plane loop is unrolled to rotate the z-queue at compile
-// time.  step3d_variant() picks the configuration used for radius M.
+// prefetch depth, planes between shifts of the register z-queue, and option bits
+// (1: packed x-sums, 2: undamped fast path).  step3d_variant() picks the configuration
+// used for radius M.
 struct Step3dVariant {
-    int ty, ry, pf;
-    bool unroll;
+    int ty, ry, pf, u, opt;
 };
 Step3dVariant step3d_variant(int M);
 int step3d_smem_bytes(int M);
@@ -46,15 +48,17 @@ int step3d_threads(int M);
 int step3d_resident_ctas(int M);
 
 // map_c: 4-D [shot][z][y][x] map of the streamed field with the halo box;
-// map_a/map_b: maps of the pointwise fields with the 64 x TY tile box
-// (kModeStep: prev, W; kModeImage: aux, g).  W's map has a shot extent of 1.
+// map_a, map_b, map_d, map_e: maps of the pointwise fields prev, W, aux, g with the
+// 64 x TY tile box (map_d and map_e are read in kModeAdj only).  W's map has a shot
+// extent of 1.
 cudaError_t launch_step3d_tma(const Step3dParams &p, int nshots, int mode, int nchunks,
                               const CUtensorMap &map_c, const CUtensorMap &map_a,
-                              const CUtensorMap &map_b, cudaStream_t s);
+                              const CUtensorMap &map_b, const CUtensorMap &map_d,
+                              const CUtensorMap &map_e, cudaStream_t s);
 
 // Per-radius pieces behind the dispatch (k_step3d_m4.cu, k_step3d_m8.cu).
 typedef void (*Step3dKernel)(const Step3dParams, const CUtensorMap, const CUtensorMap,
-                             const CUtensorMap);
+                             const CUtensorMap, const CUtensorMap, const CUtensorMap);
 struct Step3dKernelInfo {
     Step3dKernel fn;
     int threads, smem;
