@@ -179,7 +179,8 @@ struct fwi_model {
     // TMA tensor maps of the 3-D step, keyed by buffer, shot count and box
     struct MapEntry {
         const void *base;
-        int ns, bx, by;
+        int ns, bx, by, eb;
+        int64_t stride;
         CUtensorMap map;
     };
     std::vector<MapEntry> maps;
@@ -391,15 +392,20 @@ StepParams base_params(const fwi_model *m)
 
 // One time-step launch (kind 0: forward, 1: reverse); bracketed by CUDA events on the
 // launching stream when timing is on.
-int field_map(fwi_model *m, const void *base, int ns, int bx, int by, CUtensorMap *out)
+// Tensor map of `ns` shots of a field (elements of eb bytes, shots `stride` elements
+// apart; stride 0 = the field layout), cached per model.
+int field_map(fwi_model *m, const void *base, int ns, int bx, int by, CUtensorMap *out,
+              int eb = 4, int64_t stride = 0)
 {
+    if (stride == 0) stride = m->g.field;
     for (const auto &e : m->maps)
-        if (e.base == base && e.ns == ns && e.bx == bx && e.by == by) {
+        if (e.base == base && e.ns == ns && e.bx == bx && e.by == by && e.eb == eb &&
+            e.stride == stride) {
             *out = e.map;
             return FWI_OK;
         }
-    fwi_model::MapEntry e{base, ns, bx, by, {}};
-    if (encode_field_map(&e.map, base, m->g, ns, bx, by) != 0)
+    fwi_model::MapEntry e{base, ns, bx, by, eb, stride, {}};
+    if (encode_field_map(&e.map, base, m->g, ns, bx, by, eb, stride) != 0)
         return fail(FWI_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     m->maps.push_back(e);
     *out = e.map;
@@ -447,16 +453,17 @@ int step3d_launch(fwi_model *m, const StepParams &p, int ns, int mode, cudaStrea
         md = ma;
         me = ma;
     } else {
-        FWI_TRY(field_map(m, p.u_img, ns, 64, TY, &md));
+        FWI_TRY(field_map(m, p.aux, ns, 64, TY, &md, p.aux_fmt ? 2 : 4, p.aux_stride));
         FWI_TRY(field_map(m, p.gacc, ns, 64, TY, &me));
         q.g = p.gacc;
+        q.aux_fmt = p.aux_fmt;
+        q.aux_scale = p.aux_scale;
     }
     if (m->resident <= 0) m->resident = step3d_resident_ctas(g.M);
     const int tiles = ((g.nx + 63) / 64) * ((g.ny + TY - 1) / TY);
-    const int nch = plan_zchunks(g.nz, g.M, tiles, ns, m->resident);
-    q.zchunk = (g.nz + nch - 1) / nch;
-    FWI_CU(launch_step3d_tma(q, ns, mode, (g.nz + q.zchunk - 1) / q.zchunk, mc, ma, mb, md, me,
-                             s));
+    q.nshots = ns;
+    const int ctas = plan_persistent(q, tiles * ns, m->resident);
+    FWI_CU(launch_step3d_tma(q, mode, ctas, mc, ma, mb, md, me, s));
     return FWI_OK;
 }
 
@@ -613,6 +620,7 @@ struct GradJob {
     bool fused_max = false;
     size_t ia = 0;    // next schedule action
     int kdone = 0;    // forward steps already issued of the current ADVANCE action
+    int aux_slot = -1;   // checkpoint the next reverse step reads u^m from in place
 };
 
 // Checkpoint slots for the budget, the schedule and its per-action component counts,
@@ -653,9 +661,9 @@ int grad_setup(GradJob &j, fwi_model *m, const fwi_acq *acq, const float *wavele
         m->sched = revolve_actions(nt, (int32_t)slots, &m->sched_fwd);
         m->sched_nslots = (int)slots;
         // Components each checkpoint action moves: a restore followed by a reverse step
-        // needs u^m alone (the imaging pass reads only u^m; the following action is always
-        // another restore), and a checkpoint whose every restore is of that kind is
-        // stored as u^n alone.
+        // needs u^m alone (the reverse step reads only u^m, straight from the checkpoint;
+        // the following action is always another restore), and a checkpoint whose every
+        // restore is of that kind is stored as u^n alone.
         const size_t na = m->sched.size() / 2;
         m->sched_comps.assign(na, 2);
         for (size_t i = 0; i < na; ++i) {
@@ -766,6 +774,11 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
                 FWI_CU(cudaMemsetAsync(m->u[1].p, 0, ns * j.fb, s));
                 j.cur = 0;
                 j.step = 0;
+            } else if (comps == 1) {
+                // only the next reverse step needs this state, and it reads u^m from the
+                // checkpoint in place: nothing to decode
+                j.aux_slot = arg;
+                j.step = j.slot_step[arg];
             } else {
                 FWI_LAUNCH(m, launch_decode(j.codes + (size_t)arg * j.per_slot, 2 * g.field,
                                             m->scales.as<float>() + (size_t)arg * 2 * ns, g.field,
@@ -797,7 +810,18 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
             j.pa.cur = m->mu[j.mcur].as<float>();        // mu^{m+1}
             j.pa.prev = m->mu[1 - j.mcur].as<float>();   // mu^{m+2} -> mu^m
             const bool img = mm < nt;                    // mu^{nt+1} = 0: no imaging at nt
-            j.pa.u_img = m->u[j.cur].as<float>();        // u^m
+            if (j.aux_slot >= 0) {                        // u^m from its checkpoint
+                j.pa.aux = j.codes + (size_t)j.aux_slot * j.per_slot;
+                j.pa.aux_fmt = m->opts.snap_dtype;
+                j.pa.aux_stride = 2 * g.field;
+                j.pa.aux_scale = m->scales.as<float>() + (size_t)j.aux_slot * 2 * ns;
+            } else {                                      // u^m in the forward buffer
+                j.pa.aux = m->u[j.cur].as<float>();
+                j.pa.aux_fmt = FWI_SNAP_FP32;
+                j.pa.aux_stride = g.field;
+                j.pa.aux_scale = nullptr;
+            }
+            j.aux_slot = -1;
             j.pa.gacc = m->g32.as<float>();
             j.pa.src_off = img ? m->src_off.as<int64_t>() : nullptr;
             j.pa.n = mm;
@@ -1005,7 +1029,7 @@ int fwi_create_model(fwi_model **out, int32_t ndim, const int64_t shape[3],
     g.nz = (int)nz;
     g.ny = (int)ny;
     g.nx = (int)nx;
-    g.px = (int)round_up(nx, 4);
+    g.px = (int)round_up(nx, 8);
     g.plane = (int64_t)g.ny * g.px;
     g.field = round_up((int64_t)g.nz * g.plane, 64);
     int rc = set_coefs(m);

@@ -10,8 +10,9 @@ namespace fwi {
 constexpr int kMaxM = 8;   // stencil radius of the 16th-order Laplacian
 
 // Device layout of one shot's field on the computed grid (sponge included):
-// C-order [nz][ny][px] FP32, rows padded to px floats (a multiple of 4, so every row
-// starts on a 16-byte boundary), shots `field` floats apart (a multiple of 64).
+// C-order [nz][ny][px] FP32, rows padded to px floats (a multiple of 8, so every row
+// starts on a 16-byte boundary in FP32 and in the 16-bit checkpoint codes), shots
+// `field` floats apart (a multiple of 64).
 // Columns nx..px-1 are zero and never written.
 struct Geom {
     int ndim;       // 2 or 3
@@ -34,9 +35,9 @@ struct Coefs {
 // One time step of the damped leapfrog on every shot of a batch:
 //   out = (2 cur + W (L cur) - (1 - s) prev + [dt^2 w[n] at the source]) / (1 + s),
 //   s = sig_z[z] + sig_y[y] + sig_x[x]  (= eta dt / 2),
-// written over `prev`.  The reverse step with imaging (cur = mu^{m+1}, u_img = u^m) adds
+// written over `prev`.  The reverse step with imaging (cur = mu^{m+1}, aux = u^m) adds
 // no source to `out` and accumulates the transposed zero-lag imaging term
-//   gacc += u_img * (L cur),   at the source point  gacc -= dt^2 w[n] cur / W
+//   gacc += aux * (L cur),   at the source point  gacc -= dt^2 w[n] cur / W
 // (the receiver term of the same sum is added once from the traces: launch_rec_image).
 struct StepParams {
     Geom g;
@@ -49,7 +50,13 @@ struct StepParams {
     const float *wavelet;     // [nshots][nt]
     int nt, n;
     float dt2;
-    const float *u_img;       // imaging only: u^m
+    // imaging only: u^m, an FP32 field (aux_fmt 0, aux_scale null) or the first component
+    // of a checkpoint slot read in place (aux_fmt = its FWI_SNAP_* type, u^m = code /
+    // scale, bit for bit what the decode kernel would write)
+    const void *aux;
+    int aux_fmt;              // 0 FP32, 1 BF16, 2 FP16
+    int64_t aux_stride;       // elements per shot
+    const float *aux_scale;   // per shot at [2 s], or nullptr (scale 1)
     float *gacc;              // imaging only: gradient accumulator
     int zchunk;               // planes per CTA along z
     int nzchunks;

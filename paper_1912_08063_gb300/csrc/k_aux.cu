@@ -233,11 +233,13 @@ __device__ __forceinline__ void put_code(void *code, int64_t i, int dtype, float
     else ((__half *)code)[i] = __float2half_rn(x * sc);
 }
 
-__device__ __forceinline__ float get_code(const void *code, int64_t i, int dtype, float sc)
+// inv = 1 / scale.  Scales are powers of two (2^-126 .. 2^127), so their reciprocals are
+// exact and code * inv equals code / scale bit for bit.
+__device__ __forceinline__ float get_code(const void *code, int64_t i, int dtype, float inv)
 {
     if (dtype == 0) return ((const float *)code)[i];
-    if (dtype == 1) return __bfloat162float(((const __nv_bfloat16 *)code)[i]) / sc;
-    return __half2float(((const __half *)code)[i]) / sc;
+    if (dtype == 1) return __bfloat162float(((const __nv_bfloat16 *)code)[i]) * inv;
+    return __half2float(((const __half *)code)[i]) * inv;
 }
 
 // 16-bit formats store a = u^n and d = u^n - u^{n-1}, each with its own scale; FP32
@@ -307,7 +309,7 @@ __global__ void k_decode(const void *__restrict__ code, int64_t cstride,
                          float *__restrict__ a, float *__restrict__ b, int comps)
 {
     const int s = blockIdx.y;
-    const float sa = scale[2 * s], sd = scale[2 * s + 1];
+    const float sa = 1.0f / scale[2 * s], sd = 1.0f / scale[2 * s + 1];   // exact: powers of 2
     float *pa = a + s * stride, *pb = b + s * stride;
     const int esz = dtype == 0 ? 4 : 2;
     const void *ca = (const char *)code + (size_t)s * cstride * esz;
@@ -326,7 +328,7 @@ __global__ void k_decode(const void *__restrict__ code, int64_t cstride,
 #pragma unroll
             for (int e = 0; e < 4; ++e)
                 xa[e] = (dtype == 1 ? __bfloat162float(__ushort_as_bfloat16(ha[e]))
-                                    : __half2float(__ushort_as_half(ha[e]))) / sa;
+                                    : __half2float(__ushort_as_half(ha[e]))) * sa;
             ((float4 *)pa)[i4] = make_float4(xa[0], xa[1], xa[2], xa[3]);
             if (comps == 2) {
                 const ushort4 ud = ((const ushort4 *)cd)[i4];
@@ -334,7 +336,7 @@ __global__ void k_decode(const void *__restrict__ code, int64_t cstride,
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
                     xb[e] = xa[e] - (dtype == 1 ? __bfloat162float(__ushort_as_bfloat16(hd[e]))
-                                                : __half2float(__ushort_as_half(hd[e]))) / sd;
+                                                : __half2float(__ushort_as_half(hd[e]))) * sd;
                 ((float4 *)pb)[i4] = make_float4(xb[0], xb[1], xb[2], xb[3]);
             }
         }

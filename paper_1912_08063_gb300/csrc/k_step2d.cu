@@ -9,9 +9,10 @@
 // kernel needs neither shared memory nor barriers.  prev and W are read once, the new
 // row is written once with 16-byte stores: 16 bytes per point per step.  The reverse step
 // with imaging (IMG) adds the transposed zero-lag imaging term g += u^m (L mu^{m+1}) with
-// the Laplacian it computes for the step (u^m read pointwise, g read and written: 28
-// bytes per point), and at the source point g -= dt^2 w[m] mu^{m+1} / W.  Shots run on
-// grid.z.
+// the Laplacian it computes for the step (u^m read pointwise, from an FP32 field or in
+// place from a 16-bit checkpoint; g read and written: 26-28 bytes per point), and at the
+// source point g -= dt^2 w[m] mu^{m+1} / W.  Shots run on grid.z.
+#include "code16.cuh"
 #include "fwi_internal.h"
 
 namespace fwi {
@@ -45,7 +46,10 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
     const int64_t sb = (int64_t)shot * p.g.field;
     const float *__restrict__ cur = p.cur + sb;
     float *__restrict__ prev = p.prev + sb;
-    const float *__restrict__ uim = IMG ? p.u_img + sb : nullptr;
+    const int afmt = p.aux_fmt;
+    const char *__restrict__ auxb =
+        IMG ? (const char *)p.aux + (size_t)shot * p.aux_stride * (afmt ? 2 : 4) : nullptr;
+    const float ainv = (IMG && p.aux_scale) ? 1.0f / p.aux_scale[2 * shot] : 1.0f;
 
     float4 q[Q];
 #pragma unroll
@@ -131,7 +135,11 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
             }
             if (IMG) {
                 // g += u^m (L mu^{m+1});  at the source point g -= dt^2 w[m] mu^{m+1} / W
-                const float4 uv = __ldg((const float4 *)(uim + row + x0));
+                const float4 uv =
+                    afmt == 0 ? __ldg((const float4 *)((const float *)auxb + row + x0))
+                              : unpack_code4(__ldg((const uint2 *)((const unsigned short *)auxb +
+                                                                   row + x0)),
+                                             afmt, ainv);
                 const float4 gv = *(const float4 *)(p.gacc + sb + row + x0);
                 float2 g0 = __ffma2_rn(lo2(uv), l0, lo2(gv));
                 float2 g1 = __ffma2_rn(hi2(uv), l1, hi2(gv));

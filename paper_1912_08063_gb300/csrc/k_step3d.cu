@@ -56,7 +56,7 @@ int step3d_resident_ctas(int M)
     return (sms > 0 ? sms : 152) * per;
 }
 
-cudaError_t launch_step3d_tma(const Step3dParams &p, int nshots, int mode, int nchunks,
+cudaError_t launch_step3d_tma(const Step3dParams &p, int mode, int ctas,
                               const CUtensorMap &mc, const CUtensorMap &ma,
                               const CUtensorMap &mb, const CUtensorMap &md,
                               const CUtensorMap &me, cudaStream_t s)
@@ -66,10 +66,8 @@ cudaError_t launch_step3d_tma(const Step3dParams &p, int nshots, int mode, int n
     cudaError_t e = cudaFuncSetAttribute((const void *)k.fn,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem);
     if (e != cudaSuccess) return e;
-    const int TY = step3d_variant(p.M).ty;
-    const int tiles = ((p.nx + 63) / 64) * ((p.ny + TY - 1) / TY);
-    dim3 grid(tiles, nchunks, nshots);
-    k.fn<<<grid, k.threads, k.smem, s>>>(p, mc, ma, mb, md, me);
+    if (ctas < 1) return cudaErrorInvalidValue;
+    k.fn<<<ctas, k.threads, k.smem, s>>>(p, mc, ma, mb, md, me);
     return cudaGetLastError();
 }
 

@@ -5,7 +5,8 @@
 //              written over prev (Eq. 3 with the sponge: the forward step, c = u^n)
 //   kModeAdj   the same update without the source (the reverse step in the W-weighted
 //              adjoint variable mu = W nu, c = mu^{m+1}), and the imaging condition
-//              g += aux * (L c) with aux = u^m, g -= dt^2 w[m] c / W at the source point
+//              g += aux * (L c) with aux = u^m, g -= dt^2 w[m] c / W at the source point;
+//              aux is an FP32 field or a 16-bit checkpoint read in place
 // where L is the order-2M Laplacian with zero outside the computed grid.  kModeAdj uses
 // the transposed form of the zero-lag imaging sum: substituting the forward recursion
 // for W L u^m in sum_m mu^{m+1} (L u^m) and the reverse recursion for the result gives
@@ -42,6 +43,7 @@
 
 #include <utility>
 
+#include "code16.cuh"
 #include "fwi_internal.h"
 #include "step3d.h"
 
@@ -146,9 +148,10 @@ struct Ctx {
     unsigned char *halo, *pw;
     uint64_t *bar_h, *bar_p;
     int *abort_flag;
+    const float *ainv;         // shared: 1 / scale of a 16-bit aux (kModeAdj)
     int tid, tx, ty, za, nout, niter, shot, bx, by, x0, y0, hx, hy;
-    int h_issued, p_issued;   // loads issued so far (thread 0's view)
-    int cur_it;               // iteration being executed
+    int hbase, pbase;         // halo / pointwise loads of the CTA's earlier segments
+    int h_issued, p_issued;   // loads issued so far, counted like hbase (thread 0's view)
     float sxp[4], syr[C::RY];
     bool xin, sxnz;            // sxnz: some sig_x of this thread's columns is nonzero
     int64_t sb;
@@ -159,7 +162,7 @@ struct Ctx {
 
     __device__ __forceinline__ void issue_halo(int it)
     {
-        const int st = it % C::SH;
+        const int st = (hbase + it) % C::SH;
         uint64_t *b = bar_h + st;
         mbar_expect_tx(b, C::HALO_BYTES);
         tma_load4(halo + st * C::HALO_STRIDE, mc, hx, hy, za - C::M + it, shot, b);
@@ -167,10 +170,11 @@ struct Ctx {
 
     __device__ __forceinline__ void issue_pw(int o)
     {
-        const int st = o % C::SP;
+        const int st = (pbase + o) % C::SP;
         uint64_t *b = bar_p + st;
         unsigned char *d = pw + st * C::PW_STRIDE;
-        mbar_expect_tx(b, C::NPW * C::TILE_BYTES);
+        mbar_expect_tx(b, C::NPW == 4 && p->aux_fmt != 0 ? 3 * C::TILE_BYTES + C::TILE_BYTES / 2
+                                                          : C::NPW * C::TILE_BYTES);
         tma_load4(d, ma, bx * C::TX, by * C::TY, za + o, shot, b);
         tma_load4(d + C::TILE_BYTES, mb, bx * C::TX, by * C::TY, za + o, 0, b);
         if (C::NPW == 4) {
@@ -188,7 +192,6 @@ struct Ctx {
         constexpr int M = C::M, SX = C::SX, SH = C::SH, SP = C::SP, TX = C::TX, RY = C::RY;
         static_assert(R >= 2 * M && R < C::L, "queue slot");
         if (it >= niter) return false;
-        cur_it = it;
         // every thread passes this barrier in every iteration, so an abort raised by any
         // thread in iteration it is seen by all of them here, in iteration it + 1
         __syncthreads();
@@ -197,31 +200,33 @@ struct Ctx {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             if (it + C::P < niter) {
                 issue_halo(it + C::P);
-                h_issued = it + C::P + 1;
+                h_issued = hbase + it + C::P + 1;
             }
             const int op = it - 2 * M + C::P;
             if (op >= 0 && op < nout) {
                 issue_pw(op);
-                p_issued = op + 1;
+                p_issued = pbase + op + 1;
             }
         }
-        if (!mbar_wait(bar_h + it % SH, (it / SH) & 1)) {
+        const int kh = hbase + it;   // this CTA's halo load count
+        if (!mbar_wait(bar_h + kh % SH, (kh / SH) & 1)) {
             atomicExch(abort_flag, 1);
             return true;
         }
-        const float *hk = (const float *)(halo + (it % SH) * C::HALO_STRIDE);
+        const float *hk = (const float *)(halo + (kh % SH) * C::HALO_STRIDE);
 #pragma unroll
         for (int r = 0; r < RY; ++r)
             q[R][r] = *(const float4 *)(hk + (ty * RY + r + M) * SX + tx * 4 + M);
         if (it < 2 * M) return true;
 
         const int o = it - 2 * M, j = za + o;
-        if (!mbar_wait(bar_p + o % SP, (o / SP) & 1)) {
+        const int ko = pbase + o;
+        if (!mbar_wait(bar_p + ko % SP, (ko / SP) & 1)) {
             atomicExch(abort_flag, 1);
             return true;
         }
-        const float *hj = (const float *)(halo + ((it - M) % SH) * C::HALO_STRIDE);
-        const float *ta = (const float *)(pw + (o % SP) * C::PW_STRIDE);
+        const float *hj = (const float *)(halo + ((kh - M) % SH) * C::HALO_STRIDE);
+        const float *ta = (const float *)(pw + (ko % SP) * C::PW_STRIDE);
         const float *tb = ta + TX * C::TY;
         const float sz = p->sig_z[j];
 
@@ -367,7 +372,11 @@ struct Ctx {
             if (MODE == kModeAdj) {
                 // g += u^m * (L mu^{m+1});  at the source point g -= dt^2 w[m] mu^{m+1} / W
                 const float *td = ta + 2 * TX * C::TY, *te = ta + 3 * TX * C::TY;
-                const float4 Ua = *(const float4 *)(td + toff);
+                const float4 Ua =
+                    p->aux_fmt == 0
+                        ? *(const float4 *)(td + toff)
+                        : unpack_code4(*(const uint2 *)((const unsigned short *)td + toff),
+                                       p->aux_fmt, *ainv);
                 const float4 G = *(const float4 *)(te + toff);
                 float2 g0 = __ffma2_rn(lo2(Ua), l0, lo2(G));
                 float2 g1 = __ffma2_rn(hi2(Ua), l1, hi2(G));
@@ -388,49 +397,21 @@ __device__ __forceinline__ bool plane_group(Ctx<C, MODE> &c, int it)
     return true;
 }
 
-template <int M, int TY, int RY, int P, int U, int F, int MODE>
-__global__ void __launch_bounds__(Cfg<M, TY, RY, P, U, F, 2>::NT, (M == 4 ? 2 : 1))
-k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUtensorMap map_c,
-             const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
-             const __grid_constant__ CUtensorMap map_d, const __grid_constant__ CUtensorMap map_e)
+// Streams output planes z0 .. z1 - 1 of tile column `col` (columns are numbered shot by
+// shot, tiles row-major within a shot).  Ring indices continue from the CTA's earlier
+// segments (hbase, pbase), so stages and barrier phases stay in step across segments.
+template <class C, int MODE>
+__device__ __forceinline__ void run_segment(Ctx<C, MODE> &c, int col, int z0, int z1,
+                                            int tiles_x, int tiles)
 {
-    using C = Cfg<M, TY, RY, P, U, F, MODE == kModeAdj ? 4 : 2>;
-    constexpr int L = C::L;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-
-    Ctx<C, MODE> c;
-    c.p = &p;
-    c.mc = &map_c;
-    c.ma = &map_a;
-    c.mb = &map_b;
-    c.md = &map_d;
-    c.me = &map_e;
-    c.halo = smem;
-    c.pw = smem + C::SH * C::HALO_STRIDE;
-    c.bar_h = (uint64_t *)(c.pw + C::SP * C::PW_STRIDE);
-    c.bar_p = c.bar_h + C::SH;
-    c.abort_flag = (int *)(c.bar_p + C::SP);
-    c.tid = threadIdx.x;
-    c.tx = c.tid % C::NTX;
-    c.ty = c.tid / C::NTX;
-
-    if (c.tid == 0) {
-        for (int i = 0; i < C::SH; ++i) mbar_init(c.bar_h + i, 1);
-        for (int i = 0; i < C::SP; ++i) mbar_init(c.bar_p + i, 1);
-        *c.abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-
-    const int tiles_x = (p.nx + C::TX - 1) / C::TX;
-    c.bx = blockIdx.x % tiles_x;
-    c.by = blockIdx.x / tiles_x;
-    c.shot = blockIdx.z;
-    c.za = blockIdx.y * p.zchunk;
-    const int zb = min(p.nz, c.za + p.zchunk);
-    if (c.za >= zb) return;
-    c.nout = zb - c.za;
+    constexpr int M = C::M, RY = C::RY, L = C::L;
+    const Step3dParams &p = *c.p;
+    c.shot = col / tiles;
+    const int tile = col - c.shot * tiles;
+    c.bx = tile % tiles_x;
+    c.by = tile / tiles_x;
+    c.za = z0;
+    c.nout = z1 - z0;
     c.niter = c.nout + 2 * M;
     c.x0 = c.bx * C::TX + c.tx * C::RX;
     c.y0 = c.by * C::TY + c.ty * RY;
@@ -446,7 +427,6 @@ k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUt
     c.src_j = -1;
     c.src_r = c.src_e = 0;
     c.srcv = 0.0f;
-    c.mxa = c.mxd = 0u;
     if (p.src_off) {
         const int64_t s = p.src_off[c.shot];
         const int sz = (int)(s / p.plane), rem = (int)(s - (int64_t)sz * p.plane);
@@ -463,14 +443,15 @@ k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUt
 #pragma unroll
         for (int r = 0; r < RY; ++r) c.q[i][r] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-    c.h_issued = C::P < c.niter ? C::P : c.niter;
-    c.cur_it = 0;
-    c.p_issued = 0;
+    if (c.tid == 0 && MODE == kModeAdj)
+        *(float *)c.ainv = p.aux_scale ? 1.0f / p.aux_scale[2 * c.shot] : 1.0f;
+    // every thread is past the previous segment: its stages may be refilled
+    __syncthreads();
     if (c.tid == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         for (int it = 0; it < C::P && it < c.niter; ++it) c.issue_halo(it);
+        c.h_issued = c.hbase + (C::P < c.niter ? C::P : c.niter);
     }
-
     for (int it = 0; it < c.niter; it += C::U) {
         // shift the queue by U: slots L - U .. L - 1 receive the planes of this group
 #pragma unroll
@@ -480,24 +461,96 @@ k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUt
         if (!plane_group<C, MODE, 0>(c, it)) break;
     }
     if (MODE == kModeStep && p.maxbits) {
-        // every thread reaches this point (the loop above has no early return)
+        // the codec's maxima of this segment's shot (every thread gets here)
         const unsigned a = __reduce_max_sync(0xffffffffu, c.mxa);
         const unsigned d = __reduce_max_sync(0xffffffffu, c.mxd);
         if ((c.tid & 31) == 0) {
             if (a) atomicMax(p.maxbits + 2 * c.shot, a);
             if (d) atomicMax(p.maxbits + 2 * c.shot + 1, d);
         }
+        c.mxa = c.mxd = 0u;
     }
+    c.hbase += c.niter;
+    c.pbase += c.nout;
+}
+
+// Persistent launch: gridDim.x CTAs.  The first p.rounds rounds give every CTA of
+// p.round_ctas one whole tile column (all CTAs stream z in step, so neighbouring tiles'
+// halos are read while still in L2); the leftover columns are cut along z into
+// p.rem_ctas equal pieces, one per CTA (a piece may end one column and start the next).
+template <int M, int TY, int RY, int P, int U, int F, int MODE>
+__global__ void __launch_bounds__(Cfg<M, TY, RY, P, U, F, 2>::NT, (M == 4 ? 2 : 1))
+k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUtensorMap map_c,
+             const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+             const __grid_constant__ CUtensorMap map_d, const __grid_constant__ CUtensorMap map_e)
+{
+    using C = Cfg<M, TY, RY, P, U, F, MODE == kModeAdj ? 4 : 2>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+
+    Ctx<C, MODE> c;
+    c.p = &p;
+    c.mc = &map_c;
+    c.ma = &map_a;
+    c.mb = &map_b;
+    c.md = &map_d;
+    c.me = &map_e;
+    c.halo = smem;
+    c.pw = smem + C::SH * C::HALO_STRIDE;
+    c.bar_h = (uint64_t *)(c.pw + C::SP * C::PW_STRIDE);
+    c.bar_p = c.bar_h + C::SH;
+    c.abort_flag = (int *)(c.bar_p + C::SP);
+    c.ainv = (const float *)(c.abort_flag + 1);
+    c.tid = threadIdx.x;
+    c.tx = c.tid % C::NTX;
+    c.ty = c.tid / C::NTX;
+    c.hbase = c.pbase = 0;
+    c.h_issued = c.p_issued = 0;
+    c.mxa = c.mxd = 0u;
+
+    if (c.tid == 0) {
+        for (int i = 0; i < C::SH; ++i) mbar_init(c.bar_h + i, 1);
+        for (int i = 0; i < C::SP; ++i) mbar_init(c.bar_p + i, 1);
+        *c.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+
+    const int tiles_x = (p.nx + C::TX - 1) / C::TX;
+    const int tiles = tiles_x * ((p.ny + C::TY - 1) / C::TY);
+    const int k = blockIdx.x;
+    bool go = true;
+    for (int i = 0; go && i < p.rounds; ++i) {
+        if (k < p.round_ctas) run_segment(c, i * p.round_ctas + k, 0, p.nz, tiles_x, tiles);
+        __syncthreads();
+        go = !*(volatile int *)c.abort_flag;
+    }
+    const int first = p.rounds * p.round_ctas;
+    const int rem = tiles * p.nshots - first;
+    if (go && rem > 0 && k < p.rem_ctas) {
+        const int64_t total = (int64_t)rem * p.nz;
+        const int64_t len = (total + p.rem_ctas - 1) / p.rem_ctas;
+        int64_t s0 = (int64_t)k * len;
+        const int64_t s1 = s0 + len < total ? s0 + len : total;
+        while (go && s0 < s1) {
+            const int col = first + (int)(s0 / p.nz);
+            const int z0 = (int)(s0 % p.nz);
+            const int z1 = (int)(z0 + (s1 - s0) < p.nz ? z0 + (s1 - s0) : p.nz);
+            run_segment(c, col, z0, z1, tiles_x, tiles);
+            s0 += z1 - z0;
+            __syncthreads();
+            go = !*(volatile int *)c.abort_flag;
+        }
+    }
+    __syncthreads();
     if (*(volatile int *)c.abort_flag && c.tid == 0) {
-        // a bounded wait gave up in iteration cur_it - 1 (seen by all in cur_it): report,
-        // then give the copies issued and not yet consumed a bounded chance to land before
-        // the CTA's shared memory is released
+        // a bounded wait gave up: report, then give every copy still in flight (at most the
+        // last load of each stage) a bounded chance to land before the CTA's shared memory
+        // is released
         atomicOr(p.err, 2u);
-        const int failed = c.cur_it - 1 > 0 ? c.cur_it - 1 : 0;
-        for (int k = failed; k < c.h_issued; ++k)
-            (void)mbar_wait(c.bar_h + k % C::SH, (k / C::SH) & 1);
-        for (int o = failed - 2 * M > 0 ? failed - 2 * M : 0; o < c.p_issued; ++o)
-            (void)mbar_wait(c.bar_p + o % C::SP, (o / C::SP) & 1);
+        for (int q = c.h_issued - C::SH > 0 ? c.h_issued - C::SH : 0; q < c.h_issued; ++q)
+            (void)mbar_wait(c.bar_h + q % C::SH, (q / C::SH) & 1);
+        for (int q = c.p_issued - C::SP > 0 ? c.p_issued - C::SP : 0; q < c.p_issued; ++q)
+            (void)mbar_wait(c.bar_p + q % C::SP, (q / C::SP) & 1);
     }
 }
 

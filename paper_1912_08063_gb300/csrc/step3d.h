@@ -18,7 +18,9 @@ struct Step3dParams {
     int M;
     int nx, ny, nz, px;           // computed extents and row pitch (floats)
     int64_t plane, field;         // floats per z-plane and per shot
-    int zchunk;                   // output planes per CTA
+    int nshots;
+    int rounds, round_ctas;       // whole-column rounds and the CTAs each round uses
+    int rem_ctas;                 // CTAs sharing the leftover columns along z
     float cx[kMaxM + 1], cy[kMaxM + 1], cz[kMaxM + 1], c0;
     float2 cy2[kMaxM + 1], cz2[kMaxM + 1], c02;   // the same weights as packed pairs
     const float *sig_x, *sig_y, *sig_z;
@@ -29,6 +31,9 @@ struct Step3dParams {
     int nt, n;
     float dt2;
     unsigned *err;                // status word: bit 1 (value 2) = a bounded wait gave up
+    int aux_fmt;                  // kModeAdj: aux tile of FP32 (0) or BF16 (1) / FP16 (2)
+                                  // checkpoint codes
+    const float *aux_scale;       // kModeAdj with codes: per shot at [2 s] (u = code / scale)
     unsigned *maxbits;            // kModeStep, nullable: per shot, raise [2s] to the bits of
                                   // max|out| and [2s+1] to max|out - c| (the checkpoint
                                   // codec's scales of the new state pair)
@@ -51,7 +56,7 @@ int step3d_resident_ctas(int M);
 // map_a, map_b, map_d, map_e: maps of the pointwise fields prev, W, aux, g with the
 // 64 x TY tile box (map_d and map_e are read in kModeAdj only).  W's map has a shot
 // extent of 1.
-cudaError_t launch_step3d_tma(const Step3dParams &p, int nshots, int mode, int nchunks,
+cudaError_t launch_step3d_tma(const Step3dParams &p, int mode, int ctas,
                               const CUtensorMap &map_c, const CUtensorMap &map_a,
                               const CUtensorMap &map_b, const CUtensorMap &map_d,
                               const CUtensorMap &map_e, cudaStream_t s);
@@ -66,13 +71,16 @@ struct Step3dKernelInfo {
 Step3dKernelInfo step3d_kernel_m4(const Step3dVariant &v, int mode);
 Step3dKernelInfo step3d_kernel_m8(const Step3dVariant &v, int mode);
 
-// Encodes a 4-D FP32 tensor map over shots of a field laid out as in Geom, with box
-// (bx, by, 1, 1) and zero fill outside [0, nx) x [0, ny) x [0, nz) x [0, nshots).
+// Encodes a 4-D tensor map over shots of a field laid out as in Geom (elements of
+// `elem_bytes` = 4 or 2, shots `shot_stride` elements apart), with box (bx, by, 1, 1) and
+// zero fill outside [0, nx) x [0, ny) x [0, nz) x [0, nshots).
 int encode_field_map(CUtensorMap *map, const void *base, const Geom &g, int nshots, int bx,
-                     int by);
+                     int by, int elem_bytes, int64_t shot_stride);
 
-// Number of z-chunks per (tile, shot) that best fills whole waves of resident CTAs,
-// weighing the 2M warm-up planes each chunk adds.
-int plan_zchunks(int nz, int M, int tiles_per_shot, int nshots, int resident_ctas);
+// Persistent schedule of one launch over `columns` tile columns of nz planes on
+// `resident` CTAs: whole-column rounds, then the leftover columns cut along z into
+// pieces of at least 4M planes (each piece streams 2M warm-up planes).  Fills p.rounds,
+// p.round_ctas, p.rem_ctas and returns the grid size.
+int plan_persistent(Step3dParams &p, int columns, int resident);
 
 }  // namespace fwi

@@ -1,5 +1,5 @@
 // Host helpers of the TMA-staged 3-D step: tensor-map encoding (through the driver entry
-// point, so the library needs no libcuda link) and the z-chunk planner.
+// point, so the library needs no libcuda link) and the persistent schedule.
 #include <cudaTypedefs.h>
 
 #include "step3d.h"
@@ -7,8 +7,9 @@
 namespace fwi {
 
 int encode_field_map(CUtensorMap *map, const void *base, const Geom &g, int nshots, int bx,
-                     int by)
+                     int by, int elem_bytes, int64_t shot_stride)
 {
+    if (elem_bytes != 4 && elem_bytes != 2) return -1;
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void *f = nullptr;
@@ -23,38 +24,32 @@ int encode_field_map(CUtensorMap *map, const void *base, const Geom &g, int nsho
     }
     const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz,
                                 (cuuint64_t)nshots};
-    const cuuint64_t strides[3] = {(cuuint64_t)g.px * 4, (cuuint64_t)g.plane * 4,
-                                   (cuuint64_t)g.field * 4};
+    const cuuint64_t eb = (cuuint64_t)elem_bytes;
+    const cuuint64_t strides[3] = {(cuuint64_t)g.px * eb, (cuuint64_t)g.plane * eb,
+                                   (cuuint64_t)shot_stride * eb};
     const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(base), dims,
+    // 16-bit codes are moved as raw 16-bit words (zero fill = +0 in either format)
+    const CUtensorMapDataType dt =
+        elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    CUresult r = encode(map, dt, 4, const_cast<void *>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : -1;
 }
 
-int plan_zchunks(int nz, int M, int tiles_per_shot, int nshots, int resident)
+int plan_persistent(Step3dParams &p, int columns, int resident)
 {
     if (resident < 1) resident = 1;
-    double best = -1.0;
-    int best_c = 1;
-    for (int c = 1; c <= 64 && c <= nz; ++c) {
-        const int zc = (nz + c - 1) / c;
-        const int cn = (nz + zc - 1) / zc;
-        const long long ctas = (long long)tiles_per_shot * nshots * cn;
-        const long long waves = (ctas + resident - 1) / resident;
-        const double fill = (double)ctas / ((double)waves * resident);
-        // each chunk streams 2M extra planes that produce no output; they cost about
-        // half an output plane (loads and queue pushes, no stencil)
-        const double cost = 1.0 + 0.5 * (2.0 * M) / zc;
-        const double score = fill / cost;
-        if (score > best + 1e-9) {
-            best = score;
-            best_c = cn;
-        }
-    }
-    return best_c;
+    p.round_ctas = resident;
+    p.rounds = columns / resident;
+    const long long rem_planes = (long long)(columns - p.rounds * resident) * p.nz;
+    long long pieces = rem_planes / (4LL * p.M);
+    if (pieces < 1) pieces = 1;
+    if (pieces > resident) pieces = resident;
+    p.rem_ctas = rem_planes > 0 ? (int)pieces : 0;
+    return p.rounds > 0 ? resident : (p.rem_ctas > 0 ? p.rem_ctas : 1);
 }
 
 }  // namespace fwi
