@@ -70,12 +70,25 @@ typedef struct {
     int32_t reserved;
 } fwi_opts;
 
-/* Acquisition geometry of one call: shot s has one source node and nrec receivers. */
+/* Acquisition geometry of one call: shot s has one source and nrec receivers, each a
+ * grid node (Eq. 3's point source; samples of Eq. 1's d) or, as an extension the paper
+ * does not have, an off-grid position.  An off-grid point is a Kaiser-windowed sinc
+ * point (Hicks 2002, Geophysics 67(1): along each axis the 8 nodes x nearest to p weigh
+ * sinc(x - p) I0(6.31 sqrt(1 - ((x - p)/4)^2)) / I0(6.31), a point weighs the product
+ * over axes): traces sample the weighted nodes and sources and adjoint residuals are
+ * spread over the same nodes with the same weights, so injection stays the exact
+ * transpose of sampling.  Its nodes must lie inside the computed grid: within the
+ * physical grid, 4 cells from an edge with nb = 0, anywhere with nb >= 4.  Integer
+ * positions give exactly the node results. */
 typedef struct {
     int32_t nshots;
     int32_t nrec;               /* receivers per shot (>= 1)                            */
-    const int32_t *src;         /* HOST [nshots][3] (iz, iy, ix) physical-grid nodes    */
-    const int32_t *rec;         /* HOST [nshots][nrec][3]                                */
+    const int32_t *src;         /* HOST [nshots][3] (iz, iy, ix) physical-grid nodes;
+                                   ignored (may be NULL) when src_pos is given          */
+    const int32_t *rec;         /* HOST [nshots][nrec][3]; ignored when rec_pos is given */
+    const double *src_pos;      /* HOST, nullable: [nshots][3] (z, y, x) positions in
+                                   physical-grid index units (fractional; y = 0 in 2-D) */
+    const double *rec_pos;      /* HOST, nullable: [nshots][nrec][3]                     */
 } fwi_acq;
 
 /* Read-only facts about a model (sizes, memory and the checkpoint schedule). */

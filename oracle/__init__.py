@@ -92,14 +92,16 @@ def _configure(lib):
     lib.oracle_laplacian.argtypes = [i, i64p, P, i, P, P]
     lib.oracle_laplacian.restype = i
     common = [i, i64p, P, P, d, i, i, i, d, d]
-    lib.oracle_forward.argtypes = common + [i, P, P, i, P, P, P]
+    lib.oracle_forward.argtypes = common + [i, P, P, P, i, P, P, P, P]
     lib.oracle_forward.restype = i
     lib.oracle_misfit.argtypes = [P, P, ctypes.c_int64]
     lib.oracle_misfit.restype = d
-    lib.oracle_gradient.argtypes = common + [i, P, P, i, P, P, P, P, P, P, i]
+    lib.oracle_gradient.argtypes = common + [i, P, P, P, i, P, P, P, P, P, P, P, i]
     lib.oracle_gradient.restype = i
-    lib.oracle_source_adjoint.argtypes = common + [i, P, i, P, P, P]
+    lib.oracle_source_adjoint.argtypes = common + [i, P, P, i, P, P, P, P]
     lib.oracle_source_adjoint.restype = i
+    lib.oracle_point_taps.argtypes = [i, i64p, i, P, P, P]
+    lib.oracle_point_taps.restype = i
     lib.oracle_model_fields.argtypes = [i, i64p, P, P, d, i, i, d, d, i64p, P, P, P]
     lib.oracle_model_fields.restype = i
     f = ctypes.c_float
@@ -185,11 +187,31 @@ def laplacian(u, h, M):
     return out
 
 
+def point_taps(shape, pos, nb=20):
+    """(cell indices on the computed grid, weights) of the Kaiser-windowed sinc point at
+    `pos` ((z, x) or (z, y, x) physical-grid index units) for a grid of physical
+    `shape`."""
+    ndim = len(shape)
+    shp, _ = _shape3(ndim, shape)
+    p = _f64(pos)
+    if ndim == 2:
+        p = np.array([p[0], 0.0, p[1]])
+    idx = np.zeros(512, dtype=np.int64)
+    w = np.zeros(512)
+    T = _load().oracle_point_taps(ndim, shp, int(nb), _ptr(p), _ptr(idx), _ptr(w))
+    if T < 0:
+        raise ValueError("point outside the grid")
+    return idx[:T], w[:T]
+
+
 class Problem:
     """Arguments shared by every oracle call (physical grid, numerics, acquisition)."""
 
     def __init__(self, v, h, dt, nt, order=8, nb=20, r0=1e-3, vref=0.0,
-                 src=None, rec=None, wavelet=None):
+                 src=None, rec=None, wavelet=None, src_pos=None, rec_pos=None):
+        """src/rec: grid nodes (z, y, x); src_pos/rec_pos, when given, are fractional
+        positions in the same index units (Kaiser-windowed sinc points) and replace
+        the nodes."""
         self.v = _f64(v)
         self.ndim = self.v.ndim
         self.shape_c, self.shape = _shape3(self.ndim, self.v.shape)
@@ -200,6 +222,10 @@ class Problem:
         self.nb = int(nb)
         self.r0 = float(r0)
         self.vref = float(vref)
+        if src is None:
+            src = np.rint(np.asarray(src_pos, dtype=np.float64))
+        if rec is None:
+            rec = np.rint(np.asarray(rec_pos, dtype=np.float64))
         self.src = _i32(src).reshape(-1, 3)
         self.nshots = self.src.shape[0]
         rec = _i32(rec)
@@ -207,6 +233,13 @@ class Problem:
             rec = np.broadcast_to(rec, (self.nshots,) + rec.shape)
         self.rec = _i32(rec).reshape(self.nshots, -1, 3)
         self.nrec = self.rec.shape[1]
+        self.src_pos = None if src_pos is None else _f64(src_pos).reshape(self.nshots, 3)
+        if rec_pos is not None:
+            rp = _f64(rec_pos)
+            if rp.ndim == 2:
+                rp = np.broadcast_to(rp, (self.nshots,) + rp.shape)
+            rec_pos = _f64(rp).reshape(self.nshots, self.nrec, 3)
+        self.rec_pos = rec_pos
         w = _f64(wavelet)
         if w.ndim == 1:
             w = np.broadcast_to(w, (self.nshots, w.shape[0]))
@@ -230,8 +263,9 @@ class Problem:
         tr = np.zeros((self.nshots, self.nt, self.nrec))
         cs = self.computed_shape()
         fin = np.zeros((self.nshots, 2) + cs) if final else None
-        rc = _load().oracle_forward(*self._common(v), self.nshots, _ptr(self.src), _ptr(w),
-                                    self.nrec, _ptr(self.rec), _ptr(tr), _ptr(fin))
+        rc = _load().oracle_forward(*self._common(v), self.nshots, _ptr(self.src),
+                                    _ptr(self.src_pos), _ptr(w), self.nrec, _ptr(self.rec),
+                                    _ptr(self.rec_pos), _ptr(tr), _ptr(fin))
         _check(rc, "forward")
         return (tr, fin) if final else tr
 
@@ -246,7 +280,8 @@ class Problem:
         if dobs_a is None and adj_a is None:
             raise ValueError("need dobs or adjsrc")
         rc = _load().oracle_gradient(*self._common(v), self.nshots, _ptr(self.src),
-                                     _ptr(self.wavelet), self.nrec, _ptr(self.rec),
+                                     _ptr(self.src_pos), _ptr(self.wavelet), self.nrec,
+                                     _ptr(self.rec), _ptr(self.rec_pos),
                                      _ptr(dobs_a), _ptr(adj_a), ctypes.byref(phi),
                                      _ptr(grad), _ptr(gW), int(seg))
         _check(rc, "gradient")
@@ -258,7 +293,8 @@ class Problem:
         y = _f64(y).reshape(self.nshots, self.nt, self.nrec)
         x = np.zeros((self.nshots, self.nt))
         rc = _load().oracle_source_adjoint(*self._common(), self.nshots, _ptr(self.src),
-                                           self.nrec, _ptr(self.rec), _ptr(y), _ptr(x))
+                                           _ptr(self.src_pos), self.nrec, _ptr(self.rec),
+                                           _ptr(self.rec_pos), _ptr(y), _ptr(x))
         _check(rc, "source_adjoint")
         return x
 

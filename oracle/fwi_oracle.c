@@ -29,6 +29,9 @@
  *   - source: dt^2 w[n] added at one node (Eq. 3's dt^2 s term), divided by the same
  *     a+ factor as the rest of the update;
  *   - receivers: sample n of a trace is the field after step n, u^{n+1};
+ *   - off-grid sources and receivers (an extension; the paper places them on nodes):
+ *     Kaiser-windowed sinc interpolation (Hicks 2002, Geophysics 67(1), 156-166),
+ *     half-width 4 and b = 6.31, used for sampling and, transposed, for injection;
  *   - quiescent start u^{-1} = u^0 = 0;
  *   - gradient: exact derivative of the discrete phi with respect to the physical
  *     velocity grid, with the sponge strength held fixed; sponge cells take the
@@ -192,6 +195,161 @@ static int64_t og_index(const og_grid *g, const int32_t *p)
     return (iz * g->n[1] + iy) * g->n[2] + ix;
 }
 
+/* ------------------------------------------------------------------ points */
+
+/* A source or receiver is a list of (node, weight) taps on the computed grid.  A grid
+ * node is one tap of weight 1.  An off-grid position p (physical-grid index units,
+ * fractional) uses Kaiser-windowed sinc interpolation (Hicks 2002): along each axis the
+ * 2R nodes x nearest to p get
+ *     w(x) = sinc(x - p) I0(b sqrt(1 - ((x - p) / R)^2)) / I0(b),
+ * sinc(t) = sin(pi t) / (pi t), R = 4, b = 6.31, and a point takes the product of its
+ * per-axis weights.  At an integer p the weights are 1 at p and 0 elsewhere (sinc
+ * vanishes at the other integers), so a node given as a position is the node itself. */
+#define OG_HW 4
+#define OG_KB 6.31
+#define OG_PI 3.14159265358979323846
+
+typedef struct {
+    int T;            /* taps per point */
+    int64_t *idx;     /* [count][T] computed-grid cell indices */
+    double *w;        /* [count][T] weights */
+} og_pts;
+
+/* modified Bessel function of the first kind, order 0: sum_k ((x/2)^k / k!)^2 */
+static double og_i0(double x)
+{
+    double term = 1.0, sum = 1.0, q = 0.25 * x * x;
+    for (int k = 1; k < 500; ++k) {
+        term *= q / ((double)k * (double)k);
+        sum += term;
+        if (term < 1e-17 * sum) break;
+    }
+    return sum;
+}
+
+static double og_sinc(double t)
+{
+    if (t == floor(t)) return t == 0.0 ? 1.0 : 0.0;   /* sin(pi k) = 0 exactly */
+    return sin(OG_PI * t) / (OG_PI * t);
+}
+
+/* weights of the 2R nodes first .. first + 2R - 1 along one axis for position p */
+static void og_axis_weights(double p, int64_t *first, double *w)
+{
+    const int64_t i0 = (int64_t)floor(p);
+    *first = i0 - OG_HW + 1;
+    const double norm = og_i0(OG_KB);
+    for (int k = 0; k < 2 * OG_HW; ++k) {
+        const double t = (double)(*first + k) - p;
+        const double r = t / OG_HW;
+        const double win = fabs(r) <= 1.0 ? og_i0(OG_KB * sqrt(1.0 - r * r)) / norm : 0.0;
+        w[k] = og_sinc(t) * win;
+    }
+}
+
+static void og_pts_free(og_pts *p)
+{
+    free(p->idx);
+    free(p->w);
+    p->idx = NULL;
+    p->w = NULL;
+}
+
+/* Taps of `count` points given as nodes (pos == NULL) or as positions ([count][3],
+ * (z, y, x) physical-grid index units; y = 0 in 2-D).  Returns -1 when a node or a tap
+ * falls outside its grid. */
+static int og_points(const og_grid *g, int64_t count, const int32_t *nodes, const double *pos,
+                     og_pts *out)
+{
+    const int two = 2 * OG_HW;
+    out->T = pos ? (g->ndim == 3 ? two * two * two : two * two) : 1;
+    const int64_t nalloc = (count > 0 ? count : 1) * out->T;
+    out->idx = malloc(sizeof(int64_t) * nalloc);
+    out->w = malloc(sizeof(double) * nalloc);
+    if (!out->idx || !out->w) { og_pts_free(out); return -3; }
+    const int nby = (g->ndim == 3) ? g->nb : 0;
+    for (int64_t c = 0; c < count; ++c) {
+        int64_t *ix = out->idx + c * out->T;
+        double *wt = out->w + c * out->T;
+        if (!pos) {
+            ix[0] = og_index(g, nodes + 3 * c);
+            wt[0] = 1.0;
+            if (ix[0] < 0) return -1;
+            continue;
+        }
+        const double *p = pos + 3 * c;
+        if (!(p[0] >= 0.0 && p[0] <= (double)(g->np[0] - 1) && p[2] >= 0.0 &&
+              p[2] <= (double)(g->np[2] - 1)))
+            return -1;
+        if (g->ndim == 3 && !(p[1] >= 0.0 && p[1] <= (double)(g->np[1] - 1))) return -1;
+        if (g->ndim == 2 && p[1] != 0.0) return -1;
+        int64_t fz, fy = 0, fx;
+        double wz[2 * OG_HW], wy[2 * OG_HW], wx[2 * OG_HW];
+        og_axis_weights(p[0] + g->nb, &fz, wz);
+        og_axis_weights(p[2] + g->nb, &fx, wx);
+        int ty = 1;
+        if (g->ndim == 3) {
+            og_axis_weights(p[1] + nby, &fy, wy);
+            ty = two;
+        } else {
+            wy[0] = 1.0;
+        }
+        int t = 0;
+        for (int a = 0; a < two; ++a)
+            for (int b = 0; b < ty; ++b)
+                for (int d = 0; d < two; ++d, ++t) {
+                    const int64_t iz = fz + a, iy = fy + b, jx = fx + d;
+                    if (iz < 0 || iz >= g->n[0] || iy < 0 || iy >= g->n[1] || jx < 0 ||
+                        jx >= g->n[2])
+                        return -1;
+                    ix[t] = (iz * g->n[1] + iy) * g->n[2] + jx;
+                    wt[t] = wz[a] * wy[b] * wx[d];
+                }
+    }
+    return 0;
+}
+
+/* sum_t w_t u[idx_t] over the taps of point c */
+static double og_sample(const og_pts *p, int64_t c, const double *u)
+{
+    double acc = 0.0;
+    for (int t = 0; t < p->T; ++t) acc += p->w[c * p->T + t] * u[p->idx[c * p->T + t]];
+    return acc;
+}
+
+/* u[idx_t] += w_t x over the taps of point c (the transpose of og_sample) */
+static void og_spread(const og_pts *p, int64_t c, double x, double *u)
+{
+    for (int t = 0; t < p->T; ++t) u[p->idx[c * p->T + t]] += p->w[c * p->T + t] * x;
+}
+
+/* Taps of one point at position pos (physical-grid index units) on the computed grid of
+ * the given shape and sponge width: writes up to (2R)^ndim cell indices and weights,
+ * returns the tap count, or -1 outside the grid.  (For the interpolation pins.) */
+int oracle_point_taps(int ndim, const int64_t *shape, int nb, const double *pos,
+                      int64_t *idx, double *w)
+{
+    og_grid g;
+    memset(&g, 0, sizeof(g));
+    g.ndim = ndim;
+    g.nb = nb;
+    g.np[0] = shape[0];
+    g.np[1] = ndim == 3 ? shape[1] : 1;
+    g.np[2] = shape[2];
+    g.n[0] = g.np[0] + 2 * nb;
+    g.n[1] = ndim == 3 ? g.np[1] + 2 * nb : 1;
+    g.n[2] = g.np[2] + 2 * nb;
+    og_pts p;
+    int rc = og_points(&g, 1, NULL, pos, &p);
+    int T = p.T;
+    if (rc == 0) {
+        memcpy(idx, p.idx, sizeof(int64_t) * T);
+        memcpy(w, p.w, sizeof(double) * T);
+    }
+    og_pts_free(&p);
+    return rc == 0 ? T : -1;
+}
+
 /* ------------------------------------------------------------------ Laplacian */
 
 static double og_at(const og_grid *g, const double *u, int64_t iz, int64_t iy, int64_t ix)
@@ -250,63 +408,76 @@ int oracle_laplacian(int ndim, const int64_t *shape, const double *h, int M,
 /* One damped leapfrog step (Eq. 3 with the sponge reading):
  *   a+ u^{n+1} = 2 u^n + W L u^n - a- u^{n-1} + dt^2 w[n] e_src
  * lap is scratch of the grid's size. */
+/* a+ u^{n+1} = 2 u^n + W L u^n - a- u^{n-1} + dt^2 w[n] (source taps) */
 static void og_step(const og_grid *g, const double *ucur, const double *uprev,
-                    double *unext, double *lap, int64_t src, double srcval)
+                    double *unext, double *lap, const og_pts *src, int64_t s, double srcval)
 {
     og_laplacian(g, ucur, lap);
     #pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < g->ncell; ++i) {
-        double rhs = 2.0 * ucur[i] + g->W[i] * lap[i] - g->am[i] * uprev[i];
-        if (i == src) rhs += srcval;
-        unext[i] = rhs / g->ap[i];
-    }
+    for (int64_t i = 0; i < g->ncell; ++i)
+        unext[i] = 2.0 * ucur[i] + g->W[i] * lap[i] - g->am[i] * uprev[i];
+    og_spread(src, s, srcval, unext);
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < g->ncell; ++i) unext[i] /= g->ap[i];
 }
 
 typedef struct {
     int nshots, nrec, nt;
-    const int32_t *src;     /* [nshots][3] */
     const double *wavelet;  /* [nshots][nt] */
-    const int32_t *rec;     /* [nshots][nrec][3] */
+    og_pts src;             /* [nshots] points */
+    og_pts rec;             /* [nshots][nrec] points */
 } og_acq;
 
-static int og_acq_index(const og_grid *g, const og_acq *q, int s, int64_t *src, int64_t *rec)
+/* Source and receiver points from nodes (src, rec) or positions (src_pos, rec_pos) */
+static int og_acq_build(const og_grid *g, og_acq *q, int nshots, const int32_t *src,
+                        const double *src_pos, const double *wavelet, int nrec,
+                        const int32_t *rec, const double *rec_pos, int nt)
 {
-    *src = og_index(g, q->src + 3 * s);
-    if (*src < 0) return -1;
-    for (int r = 0; r < q->nrec; ++r) {
-        rec[r] = og_index(g, q->rec + 3 * ((int64_t)s * q->nrec + r));
-        if (rec[r] < 0) return -1;
-    }
-    return 0;
+    q->nshots = nshots;
+    q->nrec = nrec;
+    q->nt = nt;
+    q->wavelet = wavelet;
+    q->src.idx = q->rec.idx = NULL;
+    q->src.w = q->rec.w = NULL;
+    int rc = og_points(g, nshots, src, src_pos, &q->src);
+    if (rc == 0) rc = og_points(g, (int64_t)nshots * nrec, rec, rec_pos, &q->rec);
+    return rc;
+}
+
+static void og_acq_free(og_acq *q)
+{
+    og_pts_free(&q->src);
+    og_pts_free(&q->rec);
 }
 
 /* Forward modelling of every shot.  traces[s][n][r] = u^{n+1}(rec_r).  final_u, when
  * given, receives per shot the last two states (u^nt, u^{nt-1}) on the computed grid. */
 int oracle_forward(int ndim, const int64_t *shape, const double *h, const double *v,
                    double dt, int nt, int M, int nb, double r0, double vref,
-                   int nshots, const int32_t *src, const double *wavelet,
-                   int nrec, const int32_t *rec, double *traces, double *final_u)
+                   int nshots, const int32_t *src, const double *src_pos,
+                   const double *wavelet, int nrec, const int32_t *rec,
+                   const double *rec_pos, double *traces, double *final_u)
 {
     og_grid g;
     int rc = og_build(&g, ndim, shape, h, v, dt, M, nb, r0, vref);
     if (rc) return rc;
-    og_acq q = {nshots, nrec, nt, src, wavelet, rec};
+    og_acq q;
+    rc = og_acq_build(&g, &q, nshots, src, src_pos, wavelet, nrec, rec, rec_pos, nt);
     double *a = calloc(g.ncell, sizeof(double));
     double *b = calloc(g.ncell, sizeof(double));
     double *c = calloc(g.ncell, sizeof(double));
     double *lap = malloc(sizeof(double) * g.ncell);
-    int64_t *ri = malloc(sizeof(int64_t) * (nrec > 0 ? nrec : 1));
-    if (!a || !b || !c || !lap || !ri) { rc = -3; goto done; }
+    if (rc) goto done;
+    if (!a || !b || !c || !lap) { rc = -3; goto done; }
     for (int s = 0; s < nshots; ++s) {
-        int64_t si;
-        if (og_acq_index(&g, &q, s, &si, ri)) { rc = -1; goto done; }
         memset(a, 0, sizeof(double) * g.ncell);  /* u^{n-1} */
         memset(b, 0, sizeof(double) * g.ncell);  /* u^n */
         for (int n = 0; n < nt; ++n) {
             double w = wavelet[(int64_t)s * nt + n];
-            og_step(&g, b, a, c, lap, si, dt * dt * w);
+            og_step(&g, b, a, c, lap, &q.src, s, dt * dt * w);
             for (int r = 0; r < nrec; ++r)
-                traces[((int64_t)s * nt + n) * nrec + r] = c[ri[r]];
+                traces[((int64_t)s * nt + n) * nrec + r] =
+                    og_sample(&q.rec, (int64_t)s * nrec + r, c);
             double *t = a; a = b; b = c; c = t;   /* (prev, cur) <- (cur, next) */
         }
         if (final_u) {
@@ -315,7 +486,8 @@ int oracle_forward(int ndim, const int64_t *shape, const double *h, const double
         }
     }
 done:
-    free(a); free(b); free(c); free(lap); free(ri);
+    free(a); free(b); free(c); free(lap);
+    og_acq_free(&q);
     og_free(&g);
     return rc;
 }
@@ -353,8 +525,6 @@ static int og_adjoint(const og_grid *g, const og_acq *q, int s, const double *ad
     if (seg < 1) seg = 1;
     int nseg = (nt + seg - 1) / seg;
     int rc = 0;
-    int64_t si;
-    int64_t *ri = malloc(sizeof(int64_t) * (nrec > 0 ? nrec : 1));
     double *ck = malloc(sizeof(double) * g->ncell * 2 * (size_t)nseg);
     double *hist = malloc(sizeof(double) * g->ncell * (size_t)(seg + 2));
     double *lap = malloc(sizeof(double) * g->ncell);
@@ -365,10 +535,9 @@ static int og_adjoint(const og_grid *g, const og_acq *q, int s, const double *ad
     double *ua = calloc(g->ncell, sizeof(double));
     double *ub = calloc(g->ncell, sizeof(double));
     double *uc = calloc(g->ncell, sizeof(double));
-    if (!ri || !ck || !hist || !lap || !tmp || !n1 || !n2 || !n0 || !ua || !ub || !uc) {
+    if (!ck || !hist || !lap || !tmp || !n1 || !n2 || !n0 || !ua || !ub || !uc) {
         rc = -3; goto done;
     }
-    if (og_acq_index(g, q, s, &si, ri)) { rc = -1; goto done; }
     const double *w = q->wavelet + (int64_t)s * nt;
 
     /* forward sweep: checkpoint (u^{k seg}, u^{k seg - 1}) for k = 0..nseg-1 */
@@ -378,7 +547,7 @@ static int og_adjoint(const og_grid *g, const og_acq *q, int s, const double *ad
             memcpy(ck + (2 * (size_t)k) * g->ncell, ub, sizeof(double) * g->ncell);
             memcpy(ck + (2 * (size_t)k + 1) * g->ncell, ua, sizeof(double) * g->ncell);
         }
-        og_step(g, ub, ua, uc, lap, si, dt * dt * w[n]);
+        og_step(g, ub, ua, uc, lap, &q->src, s, dt * dt * w[n]);
         double *t = ua; ua = ub; ub = uc; uc = t;
     }
 
@@ -393,7 +562,7 @@ static int og_adjoint(const og_grid *g, const og_acq *q, int s, const double *ad
         for (int j = 1; j <= top - a; ++j) {
             const double *cur = hist + (size_t)(j - 1) * g->ncell;
             const double *prev = (j == 1) ? ua : hist + (size_t)(j - 2) * g->ncell;
-            og_step(g, cur, prev, hist + (size_t)j * g->ncell, lap, si,
+            og_step(g, cur, prev, hist + (size_t)j * g->ncell, lap, &q->src, s,
                     dt * dt * w[a + j - 1]);
         }
         for (; m > a; --m) {
@@ -405,7 +574,7 @@ static int og_adjoint(const og_grid *g, const og_acq *q, int s, const double *ad
             for (int64_t i = 0; i < g->ncell; ++i)
                 n0[i] = 2.0 * n1[i] + lap[i] - g->am[i] * n2[i];
             const double *qm = adjsrc + ((int64_t)s * nt + (m - 1)) * nrec;
-            for (int r = 0; r < nrec; ++r) n0[ri[r]] += qm[r];
+            for (int r = 0; r < nrec; ++r) og_spread(&q->rec, (int64_t)s * nrec + r, qm[r], n0);
             #pragma omp parallel for schedule(static)
             for (int64_t i = 0; i < g->ncell; ++i) n0[i] /= g->ap[i];
             /* imaging: nu^{m+1} L u^m (nu^{nt+1} = 0 makes the m = nt term vanish) */
@@ -414,12 +583,12 @@ static int og_adjoint(const og_grid *g, const og_acq *q, int s, const double *ad
                 #pragma omp parallel for schedule(static)
                 for (int64_t i = 0; i < g->ncell; ++i) gW[i] += n1[i] * lap[i];
             }
-            if (xadj) xadj[(int64_t)s * nt + (m - 1)] = dt * dt * n0[si];
+            if (xadj) xadj[(int64_t)s * nt + (m - 1)] = dt * dt * og_sample(&q->src, s, n0);
             double *t = n2; n2 = n1; n1 = n0; n0 = t;
         }
     }
 done:
-    free(ri); free(ck); free(hist); free(lap); free(tmp);
+    free(ck); free(hist); free(lap); free(tmp);
     free(n1); free(n2); free(n0); free(ua); free(ub); free(uc);
     return rc;
 }
@@ -431,25 +600,27 @@ done:
  * (summed over shots).  seg is the checkpoint interval of the reverse sweep. */
 int oracle_gradient(int ndim, const int64_t *shape, const double *h, const double *v,
                     double dt, int nt, int M, int nb, double r0, double vref,
-                    int nshots, const int32_t *src, const double *wavelet,
-                    int nrec, const int32_t *rec, const double *dobs,
-                    const double *adjsrc, double *misfit, double *grad,
-                    double *gW_out, int seg)
+                    int nshots, const int32_t *src, const double *src_pos,
+                    const double *wavelet, int nrec, const int32_t *rec,
+                    const double *rec_pos, const double *dobs, const double *adjsrc,
+                    double *misfit, double *grad, double *gW_out, int seg)
 {
     og_grid g;
     int rc = og_build(&g, ndim, shape, h, v, dt, M, nb, r0, vref);
     if (rc) return rc;
-    og_acq q = {nshots, nrec, nt, src, wavelet, rec};
+    og_acq q;
+    rc = og_acq_build(&g, &q, nshots, src, src_pos, wavelet, nrec, rec, rec_pos, nt);
     int64_t ntr = (int64_t)nshots * nt * nrec;
     double *gW = calloc(g.ncell, sizeof(double));
     double *res = NULL;
+    if (rc) goto done;
     if (!gW) { rc = -3; goto done; }
     if (!adjsrc) {
         double *dmod = malloc(sizeof(double) * (ntr > 0 ? ntr : 1));
         res = malloc(sizeof(double) * (ntr > 0 ? ntr : 1));
         if (!dmod || !res) { free(dmod); rc = -3; goto done; }
         rc = oracle_forward(ndim, shape, h, v, dt, nt, M, nb, r0, vref, nshots, src,
-                            wavelet, nrec, rec, dmod, NULL);
+                            src_pos, wavelet, nrec, rec, rec_pos, dmod, NULL);
         if (rc) { free(dmod); goto done; }
         if (misfit) *misfit = oracle_misfit(dmod, dobs, ntr);
         for (int64_t i = 0; i < ntr; ++i) res[i] = 2.0 * (dmod[i] - dobs[i]);
@@ -477,6 +648,7 @@ int oracle_gradient(int ndim, const int64_t *shape, const double *h, const doubl
             }
 done:
     free(gW); free(res);
+    og_acq_free(&q);
     og_free(&g);
     return rc;
 }
@@ -485,17 +657,20 @@ done:
  * x[s][n] = dt^2 nu^{n+1}(src_s), with y injected at the receivers. */
 int oracle_source_adjoint(int ndim, const int64_t *shape, const double *h, const double *v,
                           double dt, int nt, int M, int nb, double r0, double vref,
-                          int nshots, const int32_t *src, int nrec, const int32_t *rec,
-                          const double *y, double *x)
+                          int nshots, const int32_t *src, const double *src_pos, int nrec,
+                          const int32_t *rec, const double *rec_pos, const double *y,
+                          double *x)
 {
     og_grid g;
     int rc = og_build(&g, ndim, shape, h, v, dt, M, nb, r0, vref);
     if (rc) return rc;
     double *zero = calloc((size_t)nshots * nt, sizeof(double));
     if (!zero) { og_free(&g); return -3; }
-    og_acq q = {nshots, nrec, nt, src, zero, rec};
+    og_acq q;
+    rc = og_acq_build(&g, &q, nshots, src, src_pos, zero, nrec, rec, rec_pos, nt);
     for (int s = 0; s < nshots && rc == 0; ++s)
         rc = og_adjoint(&g, &q, s, y, NULL, x, nt);
+    og_acq_free(&q);
     free(zero);
     og_free(&g);
     return rc;

@@ -154,13 +154,15 @@ struct fwi_model {
     // workspace
     int cap_shots = 0, cap_nrec = 0;
     DevBuf u[2], mu[2], g32, g64, traces, src_off, rec_off, inj, src_scale, maxbits, partials,
-        phi, snaps, scales;
+        phi, snaps, scales, src_pts, rec_pts;
     DevBuf stage_in[3], stage_out[2];
     int nslots = 0;
     size_t slot_bytes = 0;
-    // cached geometry
+    // cached geometry (nodes, or positions of off-grid points)
     std::vector<int32_t> geo_src, geo_rec;
+    std::vector<double> geo_src_pos, geo_rec_pos;
     int geo_shots = -1, geo_nrec = -1;
+    bool og_src = false, og_rec = false;   // current acquisition uses off-grid points
     // cached schedule
     int sched_nslots = -1;
     std::vector<int32_t> sched;
@@ -303,21 +305,99 @@ int set_velocity(fwi_model *m, const float *vp, cudaStream_t s)
     return FWI_OK;
 }
 
+// Kaiser-windowed sinc weights of an off-grid point along one axis (Hicks 2002,
+// Geophysics 67(1)): the 8 nodes first .. first + 7 around the computed-grid coordinate p
+// get sinc(x - p) I0(6.31 sqrt(1 - ((x - p) / 4)^2)) / I0(6.31).  At integer p the weights
+// are the delta at p.
+void sinc_weights(double p, int32_t *first, float *w)
+{
+    auto i0 = [](double x) {   // modified Bessel function of order 0, power series
+        double term = 1.0, total = 1.0;
+        const double q = x * x / 4.0;
+        for (int k = 1; k < 400 && term > 1e-18 * total; ++k) {
+            term = term * q / ((double)k * k);
+            total += term;
+        }
+        return total;
+    };
+    const double kb = 6.31, half = kTaps / 2, pi = 3.14159265358979323846;
+    const double fl = std::floor(p);
+    *first = (int32_t)fl - (int32_t)half + 1;
+    const double norm = i0(kb);
+    for (int k = 0; k < kTaps; ++k) {
+        const double t = (double)(*first + k) - p;
+        double sinc;
+        if (t == std::floor(t)) sinc = (t == 0.0) ? 1.0 : 0.0;
+        else sinc = std::sin(pi * t) / (pi * t);
+        const double r = t / half;
+        const double win = (r >= -1.0 && r <= 1.0) ? i0(kb * std::sqrt(1.0 - r * r)) / norm : 0.0;
+        w[k] = (float)(sinc * win);
+    }
+}
+
+// Taps of the off-grid point at physical-grid position pos (z, y, x); false when a tap
+// would fall outside the computed grid.
+bool point_taps(const fwi_model *m, const double *pos, PointTaps *out)
+{
+    const int nby = m->ndim == 3 ? m->nb : 0;
+    const double c[3] = {pos[0] + m->nb, pos[1] + nby, pos[2] + m->nb};
+    const int64_t n[3] = {m->g.nz, m->g.ny, m->g.nx};
+    int32_t first[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) {
+        if (a == 1 && m->ndim == 2) {
+            out->w[kTaps] = 1.0f;
+            for (int k = 1; k < kTaps; ++k) out->w[kTaps + k] = 0.0f;
+            continue;
+        }
+        sinc_weights(c[a], &first[a], out->w + a * kTaps);
+        if (first[a] < 0 || first[a] + kTaps > n[a]) return false;
+    }
+    out->z0 = first[0];
+    out->y0 = first[1];
+    out->x0 = first[2];
+    out->pad = 0;
+    return true;
+}
+
 int validate_acq(const fwi_model *m, const fwi_acq *a)
 {
-    if (!a || a->nshots < 1 || a->nrec < 1 || !a->src || !a->rec)
-        return fail(FWI_ERR_ARG, "acquisition needs nshots >= 1, nrec >= 1, src and rec");
+    if (!a || a->nshots < 1 || a->nrec < 1 || (!a->src && !a->src_pos) ||
+        (!a->rec && !a->rec_pos))
+        return fail(FWI_ERR_ARG, "acquisition needs nshots >= 1, nrec >= 1, sources and "
+                                 "receivers (nodes or positions)");
     if ((int64_t)a->nshots * 65535 < a->nshots)
         return fail(FWI_ERR_ARG, "too many shots");
+    auto inside_pos = [&](const double *p) {
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(p[k])) return false;
+        if (!(p[0] >= 0.0 && p[0] <= (double)(m->np[0] - 1) && p[2] >= 0.0 &&
+              p[2] <= (double)(m->np[2] - 1)))
+            return false;
+        if (m->ndim == 3) return p[1] >= 0.0 && p[1] <= (double)(m->np[1] - 1);
+        return p[1] == 0.0;
+    };
+    PointTaps t;
+    if (a->src_pos)
+        for (int s = 0; s < a->nshots; ++s)
+            if (!inside_pos(a->src_pos + 3 * s) || !point_taps(m, a->src_pos + 3 * s, &t))
+                return fail(FWI_ERR_ARG, "source position " + std::to_string(s) +
+                                             " outside the grid or its taps outside the "
+                                             "sponge (nb >= 4 needed near the edges)");
+    if (a->rec_pos)
+        for (int64_t i = 0; i < (int64_t)a->nshots * a->nrec; ++i)
+            if (!inside_pos(a->rec_pos + 3 * i) || !point_taps(m, a->rec_pos + 3 * i, &t))
+                return fail(FWI_ERR_ARG, "receiver position " + std::to_string(i) +
+                                             " outside the grid or its taps outside the "
+                                             "sponge (nb >= 4 needed near the edges)");
     auto inside = [&](const int32_t *p) {
         if (p[0] < 0 || p[0] >= m->np[0] || p[2] < 0 || p[2] >= m->np[2]) return false;
         if (m->ndim == 3) return p[1] >= 0 && p[1] < m->np[1];
         return p[1] == 0;
     };
     for (int s = 0; s < a->nshots; ++s) {
-        if (!inside(a->src + 3 * s))
+        if (!a->src_pos && !inside(a->src + 3 * s))
             return fail(FWI_ERR_ARG, "source " + std::to_string(s) + " outside the grid");
-        for (int r = 0; r < a->nrec; ++r)
+        for (int r = 0; r < a->nrec && !a->rec_pos; ++r)
             if (!inside(a->rec + 3 * ((int64_t)s * a->nrec + r)))
                 return fail(FWI_ERR_ARG, "receiver " + std::to_string(r) + " of shot " +
                                              std::to_string(s) + " outside the grid");
@@ -356,22 +436,55 @@ int ensure_workspace(fwi_model *m, const fwi_acq *a, bool grad, cudaStream_t s)
     if (ns > m->cap_shots) m->cap_shots = ns;
     if (nr > m->cap_nrec) m->cap_nrec = nr;
     const size_t nsrc = (size_t)ns * 3, nrec3 = (size_t)ns * nr * 3;
+    auto same_i = [](const std::vector<int32_t> &v, const int32_t *p, size_t n) {
+        return p ? (v.size() == n && std::memcmp(v.data(), p, n * sizeof(int32_t)) == 0)
+                 : v.empty();
+    };
+    auto same_d = [](const std::vector<double> &v, const double *p, size_t n) {
+        return p ? (v.size() == n && std::memcmp(v.data(), p, n * sizeof(double)) == 0)
+                 : v.empty();
+    };
+    const bool og_s = a->src_pos != nullptr, og_r = a->rec_pos != nullptr;
     bool same = m->geo_shots == ns && m->geo_nrec == nr &&
-                std::memcmp(m->geo_src.data(), a->src, nsrc * sizeof(int32_t)) == 0 &&
-                std::memcmp(m->geo_rec.data(), a->rec, nrec3 * sizeof(int32_t)) == 0;
+                (og_s ? same_d(m->geo_src_pos, a->src_pos, nsrc) : same_i(m->geo_src, a->src, nsrc)) &&
+                (og_r ? same_d(m->geo_rec_pos, a->rec_pos, nrec3) : same_i(m->geo_rec, a->rec, nrec3)) &&
+                m->og_src == og_s && m->og_rec == og_r;
     if (!same) {
-        std::vector<int64_t> so(ns), ro((size_t)ns * nr);
-        for (int i = 0; i < ns; ++i) so[i] = node_offset(m, a->src + 3 * i);
-        for (size_t i = 0; i < (size_t)ns * nr; ++i) ro[i] = node_offset(m, a->rec + 3 * i);
+        std::vector<int64_t> so(ns, 0), ro((size_t)ns * nr, 0);
+        std::vector<PointTaps> sp, rp;
+        if (og_s) {
+            sp.resize(ns);
+            for (int i = 0; i < ns; ++i) point_taps(m, a->src_pos + 3 * i, &sp[i]);
+            FWI_TRY(m->src_pts.ensure(sp.size() * sizeof(PointTaps)));
+        } else {
+            for (int i = 0; i < ns; ++i) so[i] = node_offset(m, a->src + 3 * i);
+        }
+        if (og_r) {
+            rp.resize((size_t)ns * nr);
+            for (size_t i = 0; i < rp.size(); ++i) point_taps(m, a->rec_pos + 3 * i, &rp[i]);
+            FWI_TRY(m->rec_pts.ensure(rp.size() * sizeof(PointTaps)));
+        } else {
+            for (size_t i = 0; i < (size_t)ns * nr; ++i) ro[i] = node_offset(m, a->rec + 3 * i);
+        }
         FWI_CU(cudaMemcpyAsync(m->src_off.p, so.data(), ns * sizeof(int64_t),
                                cudaMemcpyHostToDevice, s));
         FWI_CU(cudaMemcpyAsync(m->rec_off.p, ro.data(), ro.size() * sizeof(int64_t),
                                cudaMemcpyHostToDevice, s));
-        FWI_CU(cudaStreamSynchronize(s));   // so / ro are host temporaries
-        m->geo_src.assign(a->src, a->src + nsrc);
-        m->geo_rec.assign(a->rec, a->rec + nrec3);
+        if (og_s)
+            FWI_CU(cudaMemcpyAsync(m->src_pts.p, sp.data(), sp.size() * sizeof(PointTaps),
+                                   cudaMemcpyHostToDevice, s));
+        if (og_r)
+            FWI_CU(cudaMemcpyAsync(m->rec_pts.p, rp.data(), rp.size() * sizeof(PointTaps),
+                                   cudaMemcpyHostToDevice, s));
+        FWI_CU(cudaStreamSynchronize(s));   // host temporaries
+        if (og_s) { m->geo_src.clear(); m->geo_src_pos.assign(a->src_pos, a->src_pos + nsrc); }
+        else { m->geo_src_pos.clear(); m->geo_src.assign(a->src, a->src + nsrc); }
+        if (og_r) { m->geo_rec.clear(); m->geo_rec_pos.assign(a->rec_pos, a->rec_pos + nrec3); }
+        else { m->geo_rec_pos.clear(); m->geo_rec.assign(a->rec, a->rec + nrec3); }
         m->geo_shots = ns;
         m->geo_nrec = nr;
+        m->og_src = og_s;
+        m->og_rec = og_r;
     }
     return FWI_OK;
 }
@@ -448,8 +561,14 @@ int step3d_launch(fwi_model *m, const StepParams &p, int ns, int mode, cudaStrea
     q.nt = p.nt;
     q.n = p.n;
     q.dt2 = p.dt2;
-    if (mode == kModeStep) {
+    if (mode == kModeStep && p.st_code) mode = kModeStepStore;
+    if (mode == kModeStep || mode == kModeStepStore) {
         q.maxbits = p.maxbits;
+        q.st_code = p.st_code;
+        q.st_scale = p.st_scale;
+        q.st_dtype = p.st_dtype;
+        q.st_comps = p.st_comps;
+        q.st_cstride = p.st_cstride;
         md = ma;
         me = ma;
     } else {
@@ -577,10 +696,31 @@ int fwd_setup(FwdJob &j, fwi_model *m, int ns, int nr, const float *wav, float *
     FWI_CU(cudaMemsetAsync(m->u[0].p, 0, ns * fb, s));
     FWI_CU(cudaMemsetAsync(m->u[1].p, 0, ns * fb, s));
     j.p = base_params(m);
-    j.p.src_off = m->src_off.as<int64_t>();
+    // an on-grid source is injected inside the step; off-grid taps right after it
+    j.p.src_off = m->og_src ? nullptr : m->src_off.as<int64_t>();
     j.p.wavelet = wav;
     j.cur = 0;
     j.n = 0;
+    return FWI_OK;
+}
+
+// The point work after forward step n has written u^{n+1} into `next`: the off-grid
+// source taps, then the receiver samples (when traces are recorded).
+int after_forward_step(fwi_model *m, const StepParams &p, float *next, int ns, int nr, int n,
+                       float *traces, cudaStream_t s)
+{
+    const Geom &g = m->g;
+    if (m->og_src)
+        FWI_LAUNCH(m, launch_inject_pts(g, next, m->src_pts.as<PointTaps>(), ns, 1,
+                                        m->W.as<float>(), sig_z(m), sig_y(m), sig_x(m),
+                                        p.wavelet, m->nt, n, p.dt2, 0.0f, 0, s));
+    if (!traces) return FWI_OK;
+    if (m->og_rec)
+        FWI_LAUNCH(m, launch_sample_pts(g, next, m->rec_pts.as<PointTaps>(), ns, nr, m->nt, n,
+                                        traces, s));
+    else
+        FWI_LAUNCH(m, launch_sample(g, next, m->rec_off.as<int64_t>(), ns, nr, m->nt, n, traces,
+                                    s));
     return FWI_OK;
 }
 
@@ -593,9 +733,7 @@ int fwd_advance(FwdJob &j, int64_t units, bool *done)
         j.p.prev = m->u[1 - j.cur].as<float>();
         j.p.n = j.n;
         FWI_TRY(step_launch(m, j.p, j.ns, false, 0, j.s));
-        if (j.tr)
-            FWI_LAUNCH(m, launch_sample(m->g, j.p.prev, m->rec_off.as<int64_t>(), j.ns, j.nr,
-                                        m->nt, j.n, j.tr, j.s));
+        FWI_TRY(after_forward_step(m, j.p, j.p.prev, j.ns, j.nr, j.n, j.tr, j.s));
         j.cur = 1 - j.cur;
     }
     *done = j.n >= m->nt;
@@ -621,6 +759,7 @@ struct GradJob {
     size_t ia = 0;    // next schedule action
     int kdone = 0;    // forward steps already issued of the current ADVANCE action
     int aux_slot = -1;   // checkpoint the next reverse step reads u^m from in place
+    int st_slot = -1, st_comps = 0;   // store the next forward step writes (3-D)
 };
 
 // Checkpoint slots for the budget, the schedule and its per-action component counts,
@@ -655,6 +794,8 @@ int grad_setup(GradJob &j, fwi_model *m, const fwi_acq *acq, const float *wavele
     if ((size_t)slots * per_slot > m->snaps.bytes) {
         // shrink on failure rather than fail: fewer slots only cost recomputation
         while (slots > 0 && m->snaps.ensure((size_t)slots * per_slot) != FWI_OK) slots /= 2;
+        // zero codes in the padding columns, which stores written by the step kernel skip
+        if (m->snaps.p) FWI_CU(cudaMemsetAsync(m->snaps.p, 0, m->snaps.bytes, s));
     }
     FWI_TRY(m->scales.ensure((size_t)(slots > 0 ? slots : 1) * 2 * ns * sizeof(float)));
     if (slots != m->sched_nslots) {
@@ -703,7 +844,7 @@ int grad_setup(GradJob &j, fwi_model *m, const fwi_acq *acq, const float *wavele
     FWI_CU(cudaMemsetAsync(m->g64.p, 0, ns * 2 * j.fb, s));
 
     j.pf = base_params(m);
-    j.pf.src_off = m->src_off.as<int64_t>();
+    j.pf.src_off = m->og_src ? nullptr : m->src_off.as<int64_t>();
     j.pf.wavelet = (const float *)wav;
     j.pa = base_params(m);   // reverse sweep: receivers injected after each step; the
                              // wavelet enters only the imaging term at the source point
@@ -712,7 +853,9 @@ int grad_setup(GradJob &j, fwi_model *m, const fwi_acq *acq, const float *wavele
     j.res = j.tr;            // residuals replace the traces in place
     j.slot_step.assign(slots > 0 ? slots : 1, -1);
     j.codes = m->snaps.as<char>();
-    j.fused_max = true;   // the step kernels compute the checkpoint max-abs when asked
+    // the step kernels compute the checkpoint max-abs when asked, unless off-grid source
+    // taps are added after the step (then a separate max-abs pass sees the final state)
+    j.fused_max = !m->og_src;
     return FWI_OK;
 }
 
@@ -735,16 +878,24 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
                 j.pf.prev = m->u[1 - j.cur].as<float>();
                 j.pf.n = (int)j.step;
                 j.pf.maxbits = nullptr;
+                j.pf.st_code = nullptr;
+                if (j.st_slot >= 0) {   // the deferred checkpoint of this step's input pair
+                    j.pf.st_code = (void *)(j.codes + (size_t)j.st_slot * j.per_slot);
+                    j.pf.st_scale = m->scales.as<float>() + (size_t)j.st_slot * 2 * ns;
+                    j.pf.st_dtype = m->opts.snap_dtype;
+                    j.pf.st_comps = j.st_comps;
+                    j.pf.st_cstride = 2 * g.field;
+                    j.st_slot = -1;
+                }
                 if (j.fused_max && next_store && j.kdone == arg - 1) {
                     FWI_CU(cudaMemsetAsync(m->maxbits.p, 0, 2 * ns * sizeof(unsigned), s));
                     j.pf.maxbits = m->maxbits.as<unsigned>();
                 }
                 FWI_TRY(step_launch(m, j.pf, ns, false, 0, s));
-                if (j.step >= j.recorded) {
-                    FWI_LAUNCH(m, launch_sample(g, j.pf.prev, m->rec_off.as<int64_t>(), ns, nr,
-                                                nt, (int)j.step, j.tr, s));
-                    j.recorded = j.step + 1;
-                }
+                const bool rec_now = j.step >= j.recorded;
+                FWI_TRY(after_forward_step(m, j.pf, j.pf.prev, ns, nr, (int)j.step,
+                                           rec_now ? j.tr : nullptr, s));
+                if (rec_now) j.recorded = j.step + 1;
                 j.cur = 1 - j.cur;
                 ++j.step;
                 ++j.nfwd;
@@ -755,6 +906,21 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
             j.kdone = 0;
         } else if (kind == 2) {   // STORE the pair (u^step, u^{step-1}), or u^step alone
             const bool have_max = j.fused_max && ia > 0 && m->sched[2 * (ia - 1)] == 1;
+            const bool next_adv = ia + 1 < nact && m->sched[2 * (ia + 1)] == 1;
+            if (have_max && next_adv && use_step3d(m)) {
+                // the next forward step reads exactly this pair: it writes the checkpoint
+                // from its epilogue with the scales derived here
+                FWI_LAUNCH(m, launch_snap_scales(m->maxbits.as<unsigned>(), ns,
+                                                 m->opts.snap_dtype,
+                                                 m->scales.as<float>() + (size_t)arg * 2 * ns,
+                                                 m->d_flag, s));
+                j.st_slot = arg;
+                j.st_comps = comps;
+                j.slot_step[arg] = j.step;
+                ++j.nstore;
+                ++j.ia;
+                continue;
+            }
             if (!have_max) {
                 FWI_CU(cudaMemsetAsync(m->maxbits.p, 0, 2 * ns * sizeof(unsigned), s));
                 FWI_LAUNCH(m, launch_maxabs(m->u[j.cur].as<float>(), m->u[1 - j.cur].as<float>(),
@@ -795,9 +961,10 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
             if (j.first_adj) {
                 // the receiver term of the imaging sum, from the traces before the misfit
                 // turns them into residuals
-                FWI_LAUNCH(m, launch_rec_image(g, j.tr, (const float *)j.dobs,
-                                               m->rec_off.as<int64_t>(), ns, nr, nt,
-                                               m->g64.as<double>(), s));
+                if (!m->og_rec)
+                    FWI_LAUNCH(m, launch_rec_image(g, j.tr, (const float *)j.dobs,
+                                                   m->rec_off.as<int64_t>(), ns, nr, nt,
+                                                   m->g64.as<double>(), s));
                 ++m->launches;   // the misfit is two launches
                 FWI_LAUNCH(m, launch_misfit(j.tr, (const float *)j.dobs, j.res,
                                             (int64_t)ns * nt * nr, m->partials.as<double>(),
@@ -823,15 +990,40 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
             }
             j.aux_slot = -1;
             j.pa.gacc = m->g32.as<float>();
-            j.pa.src_off = img ? m->src_off.as<int64_t>() : nullptr;
+            j.pa.src_off = (img && !m->og_src) ? m->src_off.as<int64_t>() : nullptr;
             j.pa.n = mm;
             FWI_TRY(step_launch(m, j.pa, ns, img, 1, s));
-            FWI_LAUNCH(m, launch_inject(g, j.pa.prev, m->rec_off.as<int64_t>(),
-                                        m->inj.as<float>(), j.res, ns, nr, nt, mm - 1, s));
-            if (mm == 1)   // mu^1 is complete: the m = 0 source term of the imaging sum
-                FWI_LAUNCH(m, launch_src_image(g, j.pa.prev, m->src_off.as<int64_t>(),
-                                               m->W.as<float>(), j.pa.wavelet, j.pa.dt2, ns,
-                                               nt, m->g64.as<double>(), s));
+            if (img && m->og_src)   // source term of the imaging sum at the source taps
+                FWI_LAUNCH(m, launch_image_pts(g, m->g32.as<float>(), j.pa.cur, 0, g.field,
+                                               nullptr, m->src_pts.as<PointTaps>(), ns, 1,
+                                               m->W.as<float>(), j.pa.wavelet, nt, mm,
+                                               j.pa.dt2, 0, s));
+            if (m->og_rec) {
+                // receiver term of the imaging sum (u^m at the taps), then the injection
+                FWI_LAUNCH(m, launch_image_pts(g, m->g32.as<float>(), j.pa.aux, j.pa.aux_fmt,
+                                               j.pa.aux_stride, j.pa.aux_scale,
+                                               m->rec_pts.as<PointTaps>(), ns * nr, nr,
+                                               m->W.as<float>(), j.res, nt, mm - 1, j.pa.dt2,
+                                               1, s));
+                FWI_LAUNCH(m, launch_inject_pts(g, j.pa.prev, m->rec_pts.as<PointTaps>(),
+                                                ns * nr, nr, m->W.as<float>(), sig_z(m),
+                                                sig_y(m), sig_x(m), j.res, nt, mm - 1,
+                                                j.pa.dt2, 2.0f, 1, s));
+            } else {
+                FWI_LAUNCH(m, launch_inject(g, j.pa.prev, m->rec_off.as<int64_t>(),
+                                            m->inj.as<float>(), j.res, ns, nr, nt, mm - 1, s));
+            }
+            if (mm == 1) {   // mu^1 is complete: the m = 0 source term of the imaging sum
+                if (m->og_src)
+                    FWI_LAUNCH(m, launch_image_pts(g, m->g32.as<float>(), j.pa.prev, 0, g.field,
+                                                   nullptr, m->src_pts.as<PointTaps>(), ns, 1,
+                                                   m->W.as<float>(), j.pa.wavelet, nt, 0,
+                                                   j.pa.dt2, 0, s));
+                else
+                    FWI_LAUNCH(m, launch_src_image(g, j.pa.prev, m->src_off.as<int64_t>(),
+                                                   m->W.as<float>(), j.pa.wavelet, j.pa.dt2, ns,
+                                                   nt, m->g64.as<double>(), s));
+            }
             j.mcur = 1 - j.mcur;
             ++j.nadj;
             ++used;
@@ -1158,10 +1350,21 @@ int fwi_source_adjoint(fwi_model *m, const fwi_acq *acq, const float *y, float *
         pa.cur = m->mu[mcur].as<float>();
         pa.prev = m->mu[1 - mcur].as<float>();
         FWI_TRY(step_launch(m, pa, ns, false, 1, s));
-        FWI_LAUNCH(m, launch_inject(g, pa.prev, m->rec_off.as<int64_t>(), m->inj.as<float>(),
-                             (const float *)ydev, ns, nr, nt, mm - 1, s));
-        FWI_LAUNCH(m, launch_gather_src(g, pa.prev, m->src_off.as<int64_t>(), m->src_scale.as<float>(),
-                                 ns, nt, mm - 1, (float *)xdev, s));
+        if (m->og_rec)
+            FWI_LAUNCH(m, launch_inject_pts(g, pa.prev, m->rec_pts.as<PointTaps>(), ns * nr, nr,
+                                            m->W.as<float>(), sig_z(m), sig_y(m), sig_x(m),
+                                            (const float *)ydev, nt, mm - 1, pa.dt2, 1.0f, 1, s));
+        else
+            FWI_LAUNCH(m, launch_inject(g, pa.prev, m->rec_off.as<int64_t>(), m->inj.as<float>(),
+                                        (const float *)ydev, ns, nr, nt, mm - 1, s));
+        if (m->og_src)
+            FWI_LAUNCH(m, launch_gather_src_pts(g, pa.prev, m->src_pts.as<PointTaps>(), ns,
+                                                m->W.as<float>(), pa.dt2, nt, mm - 1,
+                                                (float *)xdev, s));
+        else
+            FWI_LAUNCH(m, launch_gather_src(g, pa.prev, m->src_off.as<int64_t>(),
+                                            m->src_scale.as<float>(), ns, nt, mm - 1,
+                                            (float *)xdev, s));
         mcur = 1 - mcur;
     }
     FWI_TRY(finish_output(x, xdev, (size_t)ns * nt * sizeof(float), xhost, s));

@@ -60,10 +60,46 @@ struct StepParams {
     float *gacc;              // imaging only: gradient accumulator
     int zchunk;               // planes per CTA along z
     int nzchunks;
+    // nullable, 3-D forward step only: a checkpoint store of this step's input pair
+    // (cur = u^n, prev = u^{n-1}) written from the epilogue before prev is overwritten, in
+    // the encode kernel's format (component a = u^n, d = u^n - u^{n-1}, or the FP32 pair)
+    void *st_code;
+    const float *st_scale;    // per shot at [2s] (a) and [2s+1] (d), set by launch_snap_scales
+    int st_dtype, st_comps;
+    int64_t st_cstride;       // code elements per shot (both components)
     unsigned *maxbits;        // nullable, forward step only: per shot, raise [2s] / [2s+1]
                               // to the bits of max|out| / max|out - cur| (the checkpoint
                               // codec's scales of the new state pair)
 };
+
+// An off-grid source or receiver (Kaiser-windowed sinc point): taps at the computed-grid
+// nodes (z0 + a, y0 + b, x0 + c), a, c < kTaps, b < kTaps in 3-D (b = 0 in 2-D), with
+// weight w[a] * w[kTaps + b] * w[2 kTaps + c].
+constexpr int kTaps = 8;
+struct PointTaps {
+    int32_t z0, y0, x0, pad;
+    float w[3 * kTaps];
+};
+
+// ---- off-grid points (k_points.cu) ----
+cudaError_t launch_sample_pts(const Geom &g, const float *f, const PointTaps *pts, int nshots,
+                              int nrec, int nt, int n, float *traces, cudaStream_t s);
+// kind 0: f += dt^2 q[s][n] wt / a+ (source; q = wavelets, per_shot = 1);
+// kind 1: f += factor (W / a+) wt q[s][n][r] (adjoint injection; per_shot = nrec)
+cudaError_t launch_inject_pts(const Geom &g, float *f, const PointTaps *pts, int npts,
+                              int per_shot, const float *W, const float *sig_z,
+                              const float *sig_y, const float *sig_x, const float *q, int nt,
+                              int n, float dt2, float factor, int kind, cudaStream_t s);
+// transposed-imaging point terms: kind 0 g -= dt^2 q[s][n] wt x / W (x = mu^{m+1});
+// kind 1 g += 2 wt x q[s][n][r] (x = u^m as FP32 or a 16-bit code, see StepParams::aux)
+cudaError_t launch_image_pts(const Geom &g, float *gacc, const void *x, int xfmt,
+                             int64_t xstride, const float *xscale, const PointTaps *pts,
+                             int npts, int per_shot, const float *W, const float *q, int nt,
+                             int n, float dt2, int kind, cudaStream_t s);
+// x[s][n] = dt^2 sum_t wt f[t] / W[t]
+cudaError_t launch_gather_src_pts(const Geom &g, const float *f, const PointTaps *pts,
+                                  int nshots, const float *W, float dt2, int nt, int n,
+                                  float *x, cudaStream_t s);
 
 // 2-D step (k_step2d.cu); the 3-D step has its own launcher (step3d.h)
 cudaError_t launch_step2d(const StepParams &p, int nshots, bool imaging, cudaStream_t s);
@@ -99,6 +135,10 @@ cudaError_t launch_misfit(const float *d, const float *dobs, float *r_out, int64
                           double *partials, int nblocks, double *result, unsigned *flag,
                           cudaStream_t s);
 int misfit_blocks(int64_t n);
+// per shot: scale[2s], scale[2s+1] from maxbits as the encode kernel derives them (flag
+// raised for a non-finite maximum)
+cudaError_t launch_snap_scales(const unsigned *maxbits, int nshots, int dtype, float *scale,
+                               unsigned *flag, cudaStream_t s);
 cudaError_t launch_maxabs(const float *a, const float *b, int64_t n, int64_t stride,
                           int nshots, unsigned *maxbits, cudaStream_t s);
 // comps = 2: the pair (a, b); comps = 1: a only (a checkpoint restored only for imaging)

@@ -225,6 +225,18 @@ __device__ float snap_scale(unsigned mb, int dtype)
     return __int_as_float((k + 127) << 23);
 }
 
+// One thread per shot: the checkpoint scales from the max-abs bits (as k_encode derives
+// them), for a store that the next forward step writes from its epilogue.
+__global__ void k_snap_scales(const unsigned *__restrict__ maxbits, int nshots, int dtype,
+                              float *__restrict__ scale, unsigned *flag)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nshots) return;
+    scale[2 * s] = snap_scale(maxbits[2 * s], dtype);
+    scale[2 * s + 1] = snap_scale(maxbits[2 * s + 1], dtype);
+    if (flag && maxbits[2 * s] >= 0x7f800000u) atomicOr(flag, 1u);
+}
+
 // One value of the codec: FP32 copy, or x * scale rounded to the 16-bit format.
 __device__ __forceinline__ void put_code(void *code, int64_t i, int dtype, float x, float sc)
 {
@@ -453,6 +465,15 @@ cudaError_t launch_src_image(const Geom &g, const float *mu1, const int64_t *src
     if (nshots <= 0) return cudaSuccess;
     k_src_image<<<(nshots + kThreads - 1) / kThreads, kThreads, 0, s>>>(
         g.field, mu1, src_off, W, wavelet, dt2, nshots, nt, gacc64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_snap_scales(const unsigned *maxbits, int nshots, int dtype, float *scale,
+                               unsigned *flag, cudaStream_t s)
+{
+    if (nshots <= 0) return cudaSuccess;
+    k_snap_scales<<<(nshots + kThreads - 1) / kThreads, kThreads, 0, s>>>(maxbits, nshots, dtype,
+                                                                         scale, flag);
     return cudaGetLastError();
 }
 

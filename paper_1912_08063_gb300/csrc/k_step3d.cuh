@@ -1,8 +1,11 @@
 // 3-D time step on GB300 (sm_103a): TMA-staged z-streaming stencil (kernel template).
 //
-// One template serves two modes on the same stencil machinery:
+// One template serves three modes on the same stencil machinery:
 //   kModeStep  out = (2 c + W (L c) - (1 - s) prev [+ dt^2 w[n] at the source]) / (1 + s),
 //              written over prev (Eq. 3 with the sponge: the forward step, c = u^n)
+//   kModeStepStore  kModeStep that also writes a checkpoint of its input pair (c, prev)
+//              in the codec's format from the epilogue (the store the schedule asks for
+//              right before this step)
 //   kModeAdj   the same update without the source (the reverse step in the W-weighted
 //              adjoint variable mu = W nu, c = mu^{m+1}), and the imaging condition
 //              g += aux * (L c) with aux = u^m, g -= dt^2 w[m] c / W at the source point;
@@ -31,8 +34,9 @@
 // Measured on GB300 (radius 8, 512^3): this layout beat a variant that unrolls the
 // plane loop so the queue rotates at compile time (larger code, slower), a variant that
 // reads the forward z-neighbours from the resident stages instead of registers (more
-// shared-memory loads, slower), and one thread per 4 x 1 points (more y loads, slower);
-// U = 2 or 3 beat U = 1 by 7 %.
+// shared-memory loads, 15-20 % slower even with the freed registers spent on the options
+// below), and one thread per 4 x 1 points (more y loads, slower); U = 2 or 3 beat U = 1
+// by 7 %.
 // DRAM traffic per point and step: c once (halo re-reads hit L2), the pointwise fields
 // once, the writes once: 16 bytes (kModeStep) or 28 bytes (kModeAdj: + aux, g read and
 // written).
@@ -149,6 +153,7 @@ struct Ctx {
     uint64_t *bar_h, *bar_p;
     int *abort_flag;
     const float *ainv;         // shared: 1 / scale of a 16-bit aux (kModeAdj)
+    const float *sts;          // shared: the segment shot's checkpoint scales (st_code)
     int tid, tx, ty, za, nout, niter, shot, bx, by, x0, y0, hx, hy;
     int hbase, pbase;         // halo / pointwise loads of the CTA's earlier segments
     int h_issued, p_issued;   // loads issued so far, counted like hbase (thread 0's view)
@@ -341,7 +346,7 @@ struct Ctx {
             const float2 r1 = __ffma2_rn(hi2(B), l1, __fmul2_rn(two, hi2(cz4)));
             float rhs[4] = {r0.x, r0.y, r1.x, r1.y};
             const float pv[4] = {A.x, A.y, A.z, A.w};
-            const bool inj = MODE == kModeStep && at_src;
+            const bool inj = MODE != kModeAdj && at_src;
             if (!(C::F & kInterior) || sxnz || syr[r] != 0.0f || sz != 0.0f) {
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
@@ -359,7 +364,7 @@ struct Ctx {
                     rhs[e] = v;
                 }
             }
-            if (MODE == kModeStep && p->maxbits) {
+            if (MODE != kModeAdj && p->maxbits) {
                 // |x| as bits: unsigned order is magnitude order, NaN above infinity
                 const float cz[4] = {cz4.x, cz4.y, cz4.z, cz4.w};
 #pragma unroll
@@ -369,6 +374,22 @@ struct Ctx {
                 }
             }
             if (store) *(float4 *)(p->out + sb + base) = make_float4(rhs[0], rhs[1], rhs[2], rhs[3]);
+            if (MODE == kModeStepStore && store) {
+                // checkpoint of the input pair (c = u^n, prev = u^{n-1}) in the encode
+                // kernel's format: FP32 pair, or 16-bit a = c s_a and d = (c - prev) s_d
+                const int64_t ci = (int64_t)shot * p->st_cstride + base;
+                if (p->st_dtype == 0) {
+                    *(float4 *)((float *)p->st_code + ci) = cz4;
+                    if (p->st_comps == 2) *(float4 *)((float *)p->st_code + ci + p->field) = A;
+                } else {
+                    unsigned short *cc = (unsigned short *)p->st_code + ci;
+                    *(uint2 *)cc = pack_code4(cz4, p->st_dtype, sts[0]);
+                    if (p->st_comps == 2)
+                        *(uint2 *)(cc + p->field) =
+                            pack_code4(make_float4(cz4.x - A.x, cz4.y - A.y, cz4.z - A.z, cz4.w - A.w),
+                                       p->st_dtype, sts[1]);
+                }
+            }
             if (MODE == kModeAdj) {
                 // g += u^m * (L mu^{m+1});  at the source point g -= dt^2 w[m] mu^{m+1} / W
                 const float *td = ta + 2 * TX * C::TY, *te = ta + 3 * TX * C::TY;
@@ -445,6 +466,10 @@ __device__ __forceinline__ void run_segment(Ctx<C, MODE> &c, int col, int z0, in
 
     if (c.tid == 0 && MODE == kModeAdj)
         *(float *)c.ainv = p.aux_scale ? 1.0f / p.aux_scale[2 * c.shot] : 1.0f;
+    if (c.tid == 0 && MODE == kModeStepStore) {
+        ((float *)c.sts)[0] = p.st_scale[2 * c.shot];
+        ((float *)c.sts)[1] = p.st_scale[2 * c.shot + 1];
+    }
     // every thread is past the previous segment: its stages may be refilled
     __syncthreads();
     if (c.tid == 0) {
@@ -460,7 +485,7 @@ __device__ __forceinline__ void run_segment(Ctx<C, MODE> &c, int col, int z0, in
             for (int r = 0; r < RY; ++r) c.q[i][r] = c.q[i + C::U][r];
         if (!plane_group<C, MODE, 0>(c, it)) break;
     }
-    if (MODE == kModeStep && p.maxbits) {
+    if (MODE != kModeAdj && p.maxbits) {
         // the codec's maxima of this segment's shot (every thread gets here)
         const unsigned a = __reduce_max_sync(0xffffffffu, c.mxa);
         const unsigned d = __reduce_max_sync(0xffffffffu, c.mxd);
@@ -501,6 +526,7 @@ k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUt
     c.bar_p = c.bar_h + C::SH;
     c.abort_flag = (int *)(c.bar_p + C::SP);
     c.ainv = (const float *)(c.abort_flag + 1);
+    c.sts = c.ainv + 1;
     c.tid = threadIdx.x;
     c.tx = c.tid % C::NTX;
     c.ty = c.tid / C::NTX;
@@ -570,9 +596,10 @@ template <int M, int TY, int RY, int P, int U, int F>
 Step3dKernelInfo kernel_info(int mode)
 {
     Step3dKernelInfo k;
-    if (mode == kModeStep) {
+    if (mode == kModeStep || mode == kModeStepStore) {
         using C = Cfg<M, TY, RY, P, U, F, 2>;
-        k.fn = (Step3dKernel)k_step3d_tma<M, TY, RY, P, U, F, kModeStep>;
+        k.fn = mode == kModeStep ? (Step3dKernel)k_step3d_tma<M, TY, RY, P, U, F, kModeStep>
+                                 : (Step3dKernel)k_step3d_tma<M, TY, RY, P, U, F, kModeStepStore>;
         k.threads = C::NT;
         k.smem = C::SMEM;
     } else {

@@ -11,6 +11,9 @@
 namespace fwi {
 
 constexpr int kModeStep = 0;   // out = damped leapfrog update, written over prev
+constexpr int kModeStepStore = 2;   // kModeStep that also writes a checkpoint of its input
+                                    // pair (st_code); a separate instantiation, so the plain
+                                    // step's code is unchanged
 constexpr int kModeAdj = 1;    // the same update (no source) and g += aux * (L c), with the
                                // source-point term g -= dt^2 w[n] c / W
 
@@ -34,6 +37,10 @@ struct Step3dParams {
     int aux_fmt;                  // kModeAdj: aux tile of FP32 (0) or BF16 (1) / FP16 (2)
                                   // checkpoint codes
     const float *aux_scale;       // kModeAdj with codes: per shot at [2 s] (u = code / scale)
+    void *st_code;                // kModeStep, nullable: checkpoint of the input pair (c, prev)
+    const float *st_scale;        //   written from the epilogue (see StepParams)
+    int st_dtype, st_comps;
+    int64_t st_cstride;
     unsigned *maxbits;            // kModeStep, nullable: per shot, raise [2s] to the bits of
                                   // max|out| and [2s+1] to max|out - c| (the checkpoint
                                   // codec's scales of the new state pair)

@@ -38,7 +38,8 @@ class fwi_opts(ctypes.Structure):
 
 
 class fwi_acq(ctypes.Structure):
-    _fields_ = [("nshots", c_i32), ("nrec", c_i32), ("src", c_vp), ("rec", c_vp)]
+    _fields_ = [("nshots", c_i32), ("nrec", c_i32), ("src", c_vp), ("rec", c_vp),
+                ("src_pos", c_vp), ("rec_pos", c_vp)]
 
 
 class fwi_info(ctypes.Structure):
@@ -301,16 +302,34 @@ def fwi_last_error() -> str:
 # ---------------------------------------------------------------- convenience wrapper
 
 class Acquisition:
-    """Host-side source/receiver nodes kept alive for the duration of calls."""
+    """Host-side source/receiver geometry kept alive for the duration of calls: grid nodes
+    (src, rec as (z, y, x) integers) or off-grid positions (src_pos, rec_pos as
+    fractional (z, y, x) index coordinates, Kaiser-windowed sinc points); a position
+    array replaces the corresponding node array."""
 
-    def __init__(self, src, rec):
+    def __init__(self, src=None, rec=None, src_pos=None, rec_pos=None):
+        if src is None:
+            src = np.rint(np.asarray(src_pos, dtype=np.float64))
+        if rec is None:
+            rec = np.rint(np.asarray(rec_pos, dtype=np.float64))
         self.src = np.ascontiguousarray(np.asarray(src, dtype=np.int32).reshape(-1, 3))
         ns = self.src.shape[0]
         rec = np.asarray(rec, dtype=np.int32)
         if rec.ndim == 2:
             rec = np.broadcast_to(rec, (ns,) + rec.shape)
         self.rec = np.ascontiguousarray(rec.reshape(ns, -1, 3))
-        self.c = fwi_acq(ns, self.rec.shape[1], self.src.ctypes.data, self.rec.ctypes.data)
+        nr = self.rec.shape[1]
+        self.src_pos = None if src_pos is None else np.ascontiguousarray(
+            np.asarray(src_pos, dtype=np.float64).reshape(ns, 3))
+        self.rec_pos = None
+        if rec_pos is not None:
+            rp = np.asarray(rec_pos, dtype=np.float64)
+            if rp.ndim == 2:
+                rp = np.broadcast_to(rp, (ns,) + rp.shape)
+            self.rec_pos = np.ascontiguousarray(rp.reshape(ns, nr, 3))
+        self.c = fwi_acq(ns, nr, self.src.ctypes.data, self.rec.ctypes.data,
+                         None if self.src_pos is None else self.src_pos.ctypes.data,
+                         None if self.rec_pos is None else self.rec_pos.ctypes.data)
 
     @property
     def nshots(self):

@@ -21,10 +21,10 @@ MUTATIONS = {
     "stencil drops z": ("double lap = sz * iz2 + sx * ix2;", "double lap = sx * ix2;"),
     "update sign of u^{n-1}": ("2.0 * ucur[i] + g->W[i] * lap[i] - g->am[i] * uprev[i]",
                                "2.0 * ucur[i] + g->W[i] * lap[i] + g->am[i] * uprev[i]"),
-    "source without dt^2": ("og_step(&g, b, a, c, lap, si, dt * dt * w);",
-                            "og_step(&g, b, a, c, lap, si, dt * w);"),
-    "trace one step early": ("traces[((int64_t)s * nt + n) * nrec + r] = c[ri[r]];",
-                             "traces[((int64_t)s * nt + n) * nrec + r] = b[ri[r]];"),
+    "source without dt^2": ("og_step(&g, b, a, c, lap, &q.src, s, dt * dt * w);",
+                            "og_step(&g, b, a, c, lap, &q.src, s, dt * w);"),
+    "trace one step early": ("og_sample(&q.rec, (int64_t)s * nrec + r, c);",
+                             "og_sample(&q.rec, (int64_t)s * nrec + r, b);"),
     "adjoint applies L before W": ("for (int64_t i = 0; i < g->ncell; ++i) tmp[i] = g->W[i] * n1[i];",
                                    "for (int64_t i = 0; i < g->ncell; ++i) tmp[i] = n1[i];"),
     "imaging with u^{m-1}": ("og_laplacian(g, hist + (size_t)(m - a) * g->ncell, lap);",
@@ -33,6 +33,9 @@ MUTATIONS = {
     "sponge a- sign": ("g->am[i] = 1.0 - eta * dt / 2.0;", "g->am[i] = 1.0 + eta * dt / 2.0;"),
     "misfit not squared": ("phi += r * r;", "phi += fabs(r);"),
     "bf16 rounding truncates": ("x += 0x7fffu + lsb;", "x += 0u * lsb;"),
+    "off-grid window dropped": ("const double win = fabs(r) <= 1.0 ? og_i0(OG_KB * sqrt(1.0 - r * r)) / norm : 0.0;",
+                                "const double win = fabs(r) <= 1.0 ? 1.0 : 0.0;"),
+    "off-grid taps shifted": ("*first = i0 - OG_HW + 1;", "*first = i0 - OG_HW;"),
 }
 
 # the pins run against each mutant (fast ones; each is a plain function of the module)
@@ -50,6 +53,11 @@ PINS = [
 ]
 
 
+def _offgrid_pin():
+    import test_offgrid_pins as offgrid
+    offgrid.test_weights_interpolate_sampled_cosines((30, 40))
+
+
 def _codec_pin():
     import test_oracle_codec as codec
     codec.test_bf16_conversion_is_nearest_even()
@@ -63,7 +71,7 @@ def test_a_pin_catches_the_mutation(name, tmp_path):
     lib = oracle.compile_source(text.replace(old, new), str(tmp_path / "mutant.so"))
     caught = []
     with oracle.use_library(lib):
-        for pin in PINS + [_codec_pin]:
+        for pin in PINS + [_codec_pin, _offgrid_pin]:
             try:
                 pin()
             except (AssertionError, RuntimeError, FloatingPointError, ValueError):
