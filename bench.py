@@ -33,8 +33,11 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 HBM_FALLBACK_GBS = 6800.0
-BYTES_FWD = 16   # read u^n, u^{n-1}, W; write u^{n+1} (per point)
-BYTES_ADJ = 28   # + read u^m, read and write the FP32 gradient accumulator
+BYTES_FWD = 16     # read u^n, u^{n-1}, W; write u^{n+1} (per point)
+BYTES_STORE = 18   # the forward step that also writes the FP16/BF16 checkpoint of u^n
+BYTES_ADJ = 26     # reverse step + imaging: read mu^{m+1}, mu^{m+2}, W, g and u^m (as the
+                   # 2-byte checkpoint code, read in place); write mu^m, g.  (28 with an
+                   # FP32 u^m.)
 
 
 def parse():
@@ -77,7 +80,8 @@ def workload(name, nt_override, n=0):
     return w
 
 
-STEP3D_SOURCES = ["k_step3d.cuh", "k_step3d_m8.cu", "k_step3d_m4.cu", "k_step3d.cu", "step3d.h"]
+STEP3D_SOURCES = ["k_step3d.cuh", "k_step3d_m8.cu", "k_step3d_m4.cu", "k_step3d.cu", "step3d.h",
+                  "code16.cuh"]
 
 
 def kernel_source_hash():
@@ -298,6 +302,22 @@ def batched_section(dev, nt=3000):
             "seconds": round(tb, 3), "seconds_per_shot_calls": round(t1, 3), "kernels": kern}
 
 
+def replica_rate(ms_local, units_local, world, dist=None, device="cpu"):
+    """Whole-job timing of N independent replicas: the step time is the maximum over
+    ranks, the rate the units all ranks processed per second of that time.  Returns
+    (ms, units per second); without a process group (world 1) the local values."""
+    import torch
+    t = torch.tensor([float(ms_local), float(units_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        tmax = t[:1].clone()
+        tsum = t[1:].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        t = torch.cat([tmax, tsum])
+    ms, units = float(t[0].item()), float(t[1].item())
+    return ms, units / (ms * 1e-3)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -375,37 +395,34 @@ def main():
     torch.cuda.synchronize()
     barrier()
     ck = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms_local = e0.elapsed_time(e1) / args.steps
     info1 = model.info()
 
     pts = info1["points"]
     units = pts * w.nt * w.nshots
-    value = gpts_per_s(pts * w.nshots * world, w.nt, ms * 1e-3)
-    fwd_n = info1["fwd_step_launches"] - info0["fwd_step_launches"]
-    adj_n = info1["adj_step_launches"] - info0["adj_step_launches"]
-    fwd_ms = info1["fwd_step_ms"] - info0["fwd_step_ms"]
-    adj_ms = info1["adj_step_ms"] - info0["adj_step_ms"]
-    launches = (info1["kernel_launches"] - info0["kernel_launches"])
+    ms, rate = replica_rate(ms_local, units, world, dist, dev)
+    value = rate / 1e9   # Gpts/s over all ranks
     peak, peak_kind = measured_hbm()
-    if fwd_ms >= adj_ms:
-        kname, kbytes, kms, kn = "fwd_step_3d", BYTES_FWD * pts * w.nshots, fwd_ms, fwd_n
-    else:
-        kname, kbytes, kms, kn = "adj_step_3d", BYTES_ADJ * pts * w.nshots, adj_ms, adj_n
-    achieved = kbytes / (kms / kn * 1e-3) / 1e9 if kn else 0.0
+    kern = {}
+    for key, nkey, mkey, bpp in (("fwd_step_3d", "fwd_step_launches", "fwd_step_ms", BYTES_FWD),
+                                 ("store_step_3d", "store_step_launches", "store_step_ms", BYTES_STORE),
+                                 ("adj_step_3d", "adj_step_launches", "adj_step_ms", BYTES_ADJ)):
+        n = info1[nkey] - info0[nkey]
+        tot = info1[mkey] - info0[mkey]
+        avg = tot / n if n else 0.0
+        kern[key] = {"launches": n, "total_ms": tot, "avg_ms": avg, "bytes_per_point": bpp,
+                     "GB/s": bpp * pts * w.nshots / (avg * 1e-3) / 1e9 if n else None,
+                     "traffic": recorded_traffic(key)}
+    launches = (info1["kernel_launches"] - info0["kernel_launches"])
+    # the dominant kernel: the largest share of the step's device time
+    kname = max(kern, key=lambda k: kern[k]["total_ms"])
+    kd = kern[kname]
+    achieved = kd["GB/s"] or 0.0
     roof = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
             "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-            "traffic": recorded_traffic(kname),
-            "algorithmic_bytes_per_launch": kbytes,
-            "fwd_step": {"launches": fwd_n, "avg_ms": fwd_ms / max(fwd_n, 1),
-                         "GB/s": BYTES_FWD * pts * w.nshots / (fwd_ms / max(fwd_n, 1) * 1e-3) / 1e9
-                         if fwd_n else None},
-            "adj_step": {"launches": adj_n, "avg_ms": adj_ms / max(adj_n, 1),
-                         "GB/s": BYTES_ADJ * pts * w.nshots / (adj_ms / max(adj_n, 1) * 1e-3) / 1e9
-                         if adj_n else None}}
+            "traffic": kd["traffic"],
+            "algorithmic_bytes_per_launch": kd["bytes_per_point"] * pts * w.nshots,
+            "kernels": kern}
 
     # end to end through the C ABI with pinned host buffers, copies inside the timing
     e2e = None
@@ -421,14 +438,12 @@ def main():
         for _ in range(args.e2e_steps):
             fwi.fwi_update_velocity(model.handle, v_h)
             fwi.fwi_adjoint_gradient(model.handle, acq.c, wav_h, dobs_h, phi_h, grad_h)
-        te = (time.perf_counter() - t0) / args.e2e_steps
-        tt = torch.tensor([te], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
+        te_ms, e2e_rate = replica_rate((time.perf_counter() - t0) / args.e2e_steps * 1e3, units,
+                                       world, dist, dev)
+        te = te_ms * 1e-3
         h2d = v_h.numel() * 4 + wav_h.numel() * 4 + dobs_h.numel() * 4
         d2h = grad_h.numel() * 4 + 8
-        e2e = {"value": gpts_per_s(pts * w.nshots * world, w.nt, te), "unit": "Gpts/s",
+        e2e = {"value": e2e_rate / 1e9, "unit": "Gpts/s",
                "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": te * 1e3, "misfit": float(phi_h[0])}
 

@@ -108,10 +108,13 @@ typedef struct {
     float   sponge_eta_max[3];  /* per axis (z, y, x), 1/s                              */
     float   cfl;                /* stability number (< 1 is stable)                     */
     int64_t kernel_launches;    /* library kernel launches since creation               */
-    int64_t fwd_step_launches;  /* timed forward-step launches (opts.timing)            */
+    int64_t fwd_step_launches;  /* timed forward-step launches (opts.timing), not counting
+                                   those that also write a checkpoint                   */
     int64_t adj_step_launches;  /* timed reverse-step launches (opts.timing)            */
     double  fwd_step_ms;        /* their summed CUDA-event durations                    */
     double  adj_step_ms;
+    int64_t store_step_launches; /* timed forward steps that also wrote a checkpoint    */
+    double  store_step_ms;
 } fwi_info;
 
 /* Creates a model: the velocity grid v (physical, [nz][ny][nx] FP32, host or device,

@@ -176,7 +176,8 @@ struct fwi_model {
     // launch count and kernel timing (opts.timing)
     int64_t launches = 0;
     std::vector<cudaEvent_t> ev;
-    std::vector<int> ev_kind;   // per event pair: 0 forward step, 1 reverse step
+    std::vector<int> ev_kind;   // per event pair: 0 forward step, 1 reverse step, 2 forward
+                                // step that also writes a checkpoint
     size_t ev_used = 0;
     // TMA tensor maps of the 3-D step, keyed by buffer, shot count and box
     struct MapEntry {
@@ -187,8 +188,8 @@ struct fwi_model {
     };
     std::vector<MapEntry> maps;
     int resident = 0;   // resident CTAs of the 3-D step kernel
-    int64_t t_fwd_n = 0, t_adj_n = 0;
-    double t_fwd_ms = 0.0, t_adj_ms = 0.0;
+    int64_t t_fwd_n = 0, t_adj_n = 0, t_st_n = 0;
+    double t_fwd_ms = 0.0, t_adj_ms = 0.0, t_st_ms = 0.0;
 
     int64_t device_bytes() const
     {
@@ -629,6 +630,9 @@ int collect_timing(fwi_model *m)
         if (m->ev_kind[i] == 0) {
             m->t_fwd_ms += ms;
             ++m->t_fwd_n;
+        } else if (m->ev_kind[i] == 2) {
+            m->t_st_ms += ms;
+            ++m->t_st_n;
         } else {
             m->t_adj_ms += ms;
             ++m->t_adj_n;
@@ -891,7 +895,7 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
                     FWI_CU(cudaMemsetAsync(m->maxbits.p, 0, 2 * ns * sizeof(unsigned), s));
                     j.pf.maxbits = m->maxbits.as<unsigned>();
                 }
-                FWI_TRY(step_launch(m, j.pf, ns, false, 0, s));
+                FWI_TRY(step_launch(m, j.pf, ns, false, j.pf.st_code ? 2 : 0, s));
                 const bool rec_now = j.step >= j.recorded;
                 FWI_TRY(after_forward_step(m, j.pf, j.pf.prev, ns, nr, (int)j.step,
                                            rec_now ? j.tr : nullptr, s));
@@ -1440,6 +1444,8 @@ int fwi_model_info(const fwi_model *m, fwi_info *o)
     o->adj_step_launches = m->t_adj_n;
     o->fwd_step_ms = m->t_fwd_ms;
     o->adj_step_ms = m->t_adj_ms;
+    o->store_step_launches = m->t_st_n;
+    o->store_step_ms = m->t_st_ms;
     return FWI_OK;
 }
 

@@ -50,7 +50,8 @@ class fwi_info(ctypes.Structure):
                 ("last_adjoint_steps", c_i64), ("last_snap_stores", c_i64),
                 ("last_snap_restores", c_i64), ("sponge_eta_max", c_f32 * 3), ("cfl", c_f32),
                 ("kernel_launches", c_i64), ("fwd_step_launches", c_i64),
-                ("adj_step_launches", c_i64), ("fwd_step_ms", c_f64), ("adj_step_ms", c_f64)]
+                ("adj_step_launches", c_i64), ("fwd_step_ms", c_f64), ("adj_step_ms", c_f64),
+                ("store_step_launches", c_i64), ("store_step_ms", c_f64)]
 
 
 class fwi_request(ctypes.Structure):
