@@ -154,7 +154,7 @@ struct fwi_model {
     // workspace
     int cap_shots = 0, cap_nrec = 0;
     DevBuf u[2], mu[2], g32, g64, traces, src_off, rec_off, inj, src_scale, maxbits, partials,
-        phi, snaps, scales, src_pts, rec_pts;
+        phi, snaps, scales, src_pts, rec_pts, step_ctr;
     DevBuf stage_in[3], stage_out[2];
     int nslots = 0;
     size_t slot_bytes = 0;
@@ -561,6 +561,7 @@ int step3d_launch(fwi_model *m, const StepParams &p, int ns, int mode, cudaStrea
     q.wavelet = p.wavelet;
     q.nt = p.nt;
     q.n = p.n;
+    q.n_dev = p.n_dev;
     q.dt2 = p.dt2;
     if (mode == kModeStep && p.st_code) mode = kModeStepStore;
     if (mode == kModeStep || mode == kModeStepStore) {
@@ -686,6 +687,19 @@ struct FwdJob {
     StepParams p{};
     float *tr = nullptr;    // device traces target (may be null)
     int cur = 0, n = 0;
+    // CUDA graph of one turn: g_units steps from buffer parity g_cur, replayed with the
+    // device step counter m->step_ctr (dev_n: its value as the host last set it)
+    cudaGraphExec_t gexec = nullptr;
+    int g_units = 0, g_cur = -1, dev_n = -1;
+    int64_t g_kernels = 0;
+    bool g_failed = false;
+    FwdJob() = default;
+    FwdJob(const FwdJob &) = delete;
+    FwdJob &operator=(const FwdJob &) = delete;
+    ~FwdJob()
+    {
+        if (gexec) cudaGraphExecDestroy(gexec);
+    }
 };
 
 int fwd_setup(FwdJob &j, fwi_model *m, int ns, int nr, const float *wav, float *tr,
@@ -717,21 +731,93 @@ int after_forward_step(fwi_model *m, const StepParams &p, float *next, int ns, i
     if (m->og_src)
         FWI_LAUNCH(m, launch_inject_pts(g, next, m->src_pts.as<PointTaps>(), ns, 1,
                                         m->W.as<float>(), sig_z(m), sig_y(m), sig_x(m),
-                                        p.wavelet, m->nt, n, p.dt2, 0.0f, 0, s));
+                                        p.wavelet, m->nt, n, p.dt2, 0.0f, 0, s, p.n_dev));
     if (!traces) return FWI_OK;
     if (m->og_rec)
         FWI_LAUNCH(m, launch_sample_pts(g, next, m->rec_pts.as<PointTaps>(), ns, nr, m->nt, n,
-                                        traces, s));
+                                        traces, s, p.n_dev));
     else
         FWI_LAUNCH(m, launch_sample(g, next, m->rec_off.as<int64_t>(), ns, nr, m->nt, n, traces,
-                                    s));
+                                    s, p.n_dev));
     return FWI_OK;
 }
 
 // On completion u[cur] holds u^nt and u[1-cur] holds u^{nt-1}.
+// Captures `units` forward steps (with their point work) from the current buffer parity
+// into a graph that reads the step index from m->step_ctr and advances it.  On any
+// failure the job falls back to issuing steps one by one.
+int fwd_capture(FwdJob &j, int units)
+{
+    fwi_model *m = j.m;
+    if (j.gexec) {
+        cudaGraphExecDestroy(j.gexec);
+        j.gexec = nullptr;
+    }
+    FWI_TRY(m->step_ctr.ensure(sizeof(int)));
+    if (use_step3d(m) && m->resident <= 0) m->resident = step3d_resident_ctas(m->g.M);
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(j.s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        j.g_failed = true;
+        return FWI_OK;
+    }
+    const int64_t l0 = m->launches;
+    int rc = FWI_OK;
+    StepParams p = j.p;
+    p.n_dev = m->step_ctr.as<int>();
+    int cur = j.cur;
+    for (int i = 0; i < units && rc == FWI_OK; ++i) {
+        p.cur = m->u[cur].as<float>();
+        p.prev = m->u[1 - cur].as<float>();
+        p.n = i;
+        ++m->launches;
+        rc = raw_step(m, p, j.ns, false, j.s);
+        if (rc == FWI_OK) rc = after_forward_step(m, p, p.prev, j.ns, j.nr, i, j.tr, j.s);
+        cur = 1 - cur;
+    }
+    if (rc == FWI_OK) {
+        ++m->launches;
+        if (launch_tick(m->step_ctr.as<int>(), units, j.s) != cudaSuccess) rc = FWI_ERR_CUDA;
+    }
+    const cudaError_t ec = cudaStreamEndCapture(j.s, &graph);
+    const int64_t nk = m->launches - l0;
+    m->launches = l0;   // counted when the graph runs
+    if (rc != FWI_OK || ec != cudaSuccess || !graph ||
+        cudaGraphInstantiate(&j.gexec, graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        j.gexec = nullptr;
+        j.g_failed = true;
+    } else {
+        j.g_units = units;
+        j.g_cur = j.cur;
+        j.g_kernels = nk;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    return FWI_OK;
+}
+
 int fwd_advance(FwdJob &j, int64_t units, bool *done)
 {
     fwi_model *m = j.m;
+    // a turn of an even number of steps (the serving loop's unit of work) replays one
+    // captured graph: the buffer parity repeats after it and the step index comes from
+    // the device counter
+    if (units >= 2 && units <= 64 && units % 2 == 0 && m->nt - j.n >= units &&
+        !m->opts.timing && !j.g_failed) {
+        if (!j.gexec || j.g_units != units || j.g_cur != j.cur) FWI_TRY(fwd_capture(j, (int)units));
+        if (j.gexec) {
+            if (j.dev_n != j.n) {
+                FWI_LAUNCH(m, launch_set_counter(m->step_ctr.as<int>(), j.n, j.s));
+                j.dev_n = j.n;
+            }
+            FWI_CU(cudaGraphLaunch(j.gexec, j.s));
+            m->launches += j.g_kernels;
+            j.n += (int)units;
+            j.dev_n += (int)units;
+            *done = j.n >= m->nt;
+            return FWI_OK;
+        }
+    }
     for (int64_t u = 0; u < units && j.n < m->nt; ++u, ++j.n) {
         j.p.cur = m->u[j.cur].as<float>();
         j.p.prev = m->u[1 - j.cur].as<float>();

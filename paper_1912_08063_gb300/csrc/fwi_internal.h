@@ -49,6 +49,8 @@ struct StepParams {
     const int64_t *src_off;   // [nshots] offsets within a shot's field, or nullptr
     const float *wavelet;     // [nshots][nt]
     int nt, n;
+    const int *n_dev;         // nullable: the step index is *n_dev + n (a captured CUDA graph
+                              // replays its steps with a device-side step counter)
     float dt2;
     // imaging only: u^m, an FP32 field (aux_fmt 0, aux_scale null) or the first component
     // of a checkpoint slot read in place (aux_fmt = its FWI_SNAP_* type, u^m = code /
@@ -83,13 +85,15 @@ struct PointTaps {
 
 // ---- off-grid points (k_points.cu) ----
 cudaError_t launch_sample_pts(const Geom &g, const float *f, const PointTaps *pts, int nshots,
-                              int nrec, int nt, int n, float *traces, cudaStream_t s);
+                              int nrec, int nt, int n, float *traces, cudaStream_t s,
+                              const int *n_dev = nullptr);
 // kind 0: f += dt^2 q[s][n] wt / a+ (source; q = wavelets, per_shot = 1);
 // kind 1: f += factor (W / a+) wt q[s][n][r] (adjoint injection; per_shot = nrec)
 cudaError_t launch_inject_pts(const Geom &g, float *f, const PointTaps *pts, int npts,
                               int per_shot, const float *W, const float *sig_z,
                               const float *sig_y, const float *sig_x, const float *q, int nt,
-                              int n, float dt2, float factor, int kind, cudaStream_t s);
+                              int n, float dt2, float factor, int kind, cudaStream_t s,
+                              const int *n_dev = nullptr);
 // transposed-imaging point terms: kind 0 g -= dt^2 q[s][n] wt x / W (x = mu^{m+1});
 // kind 1 g += 2 wt x q[s][n][r] (x = u^m as FP32 or a 16-bit code, see StepParams::aux)
 cudaError_t launch_image_pts(const Geom &g, float *gacc, const void *x, int xfmt,
@@ -117,9 +121,14 @@ cudaError_t launch_rec_image(const Geom &g, const float *d, const float *dobs,
 cudaError_t launch_src_image(const Geom &g, const float *mu1, const int64_t *src_off,
                              const float *W, const float *wavelet, float dt2, int nshots,
                              int nt, double *gacc64, cudaStream_t s);
+// n_dev (nullable): the trace row is *n_dev + n
 cudaError_t launch_sample(const Geom &g, const float *field, const int64_t *rec_off,
                           int nshots, int nrec, int nt, int n, float *traces,
-                          cudaStream_t s);
+                          cudaStream_t s, const int *n_dev = nullptr);
+// *counter += add (one thread; the step counter of a captured graph)
+cudaError_t launch_tick(int *counter, int add, cudaStream_t s);
+// *counter = value
+cudaError_t launch_set_counter(int *counter, int value, cudaStream_t s);
 cudaError_t launch_inject(const Geom &g, float *field, const int64_t *rec_off,
                           const float *scale, const float *q, int nshots, int nrec, int nt,
                           int sample, cudaStream_t s);

@@ -68,11 +68,13 @@ __global__ void k_rec_scale(Geom g, const float *__restrict__ W, const float *__
 // ---------------------------------------------------------------- receivers
 
 __global__ void k_sample(int64_t fs, const float *__restrict__ f, const int64_t *__restrict__ off,
-                         int nshots, int nrec, int nt, int n, float *__restrict__ traces)
+                         int nshots, int nrec, int nt, int n, float *__restrict__ traces,
+                         const int *__restrict__ n_dev)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nshots * nrec) return;
     const int s = i / nrec, r = i - s * nrec;
+    if (n_dev) n += *n_dev;
     traces[((int64_t)s * nt + n) * nrec + r] = f[(int64_t)s * fs + off[i]];
 }
 
@@ -427,12 +429,31 @@ cudaError_t launch_build_W(const Geom &g, int nb, const int64_t np[3], const flo
     return cudaGetLastError();
 }
 
+__global__ void k_tick(int *counter, int add, int set)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *counter = set ? add : *counter + add;
+}
+
+cudaError_t launch_tick(int *counter, int add, cudaStream_t s)
+{
+    k_tick<<<1, 32, 0, s>>>(counter, add, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_counter(int *counter, int value, cudaStream_t s)
+{
+    k_tick<<<1, 32, 0, s>>>(counter, value, 1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sample(const Geom &g, const float *field, const int64_t *rec_off,
-                          int nshots, int nrec, int nt, int n, float *traces, cudaStream_t s)
+                          int nshots, int nrec, int nt, int n, float *traces, cudaStream_t s,
+                          const int *n_dev)
 {
     int cnt = nshots * nrec;
     k_sample<<<(cnt + kThreads - 1) / kThreads, kThreads, 0, s>>>(g.field, field, rec_off,
-                                                                 nshots, nrec, nt, n, traces);
+                                                                 nshots, nrec, nt, n, traces,
+                                                                 n_dev);
     return cudaGetLastError();
 }
 

@@ -36,10 +36,12 @@ __device__ __forceinline__ int rows_per_point(const Geom &g) { return kTaps * (g
 
 // traces[s][n][r] = sum over taps of w * f (FP32)
 __global__ void k_sample_pts(Geom g, const float *__restrict__ f, const PointTaps *__restrict__ pts,
-                             int nshots, int nrec, int nt, int n, float *__restrict__ traces)
+                             int nshots, int nrec, int nt, int n, float *__restrict__ traces,
+                             const int *__restrict__ n_dev)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nshots * nrec) return;
+    if (n_dev) n += *n_dev;
     const int s = i / nrec, r = i - s * nrec;
     const PointTaps &p = pts[i];
     const float *fs = f + (int64_t)s * g.field;
@@ -62,11 +64,12 @@ __global__ void k_inject_pts(Geom g, float *__restrict__ f, const PointTaps *__r
                              int npts, int per_shot, const float *__restrict__ W,
                              const float *__restrict__ sz, const float *__restrict__ sy,
                              const float *__restrict__ sx, const float *__restrict__ q, int nt,
-                             int n, float dt2, float factor, int kind)
+                             int n, float dt2, float factor, int kind, const int *__restrict__ n_dev)
 {
     const int rows = rows_per_point(g);
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= (int64_t)npts * rows) return;
+    if (n_dev) n += *n_dev;
     const int pi = (int)(i / rows), ab = (int)(i - (int64_t)pi * rows);
     const int ty = g.ndim == 3 ? kTaps : 1;
     const int a = ab / ty, b = ab - a * ty;
@@ -145,21 +148,23 @@ unsigned blocks(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 }  // namespace
 
 cudaError_t launch_sample_pts(const Geom &g, const float *f, const PointTaps *pts, int nshots,
-                              int nrec, int nt, int n, float *traces, cudaStream_t s)
+                              int nrec, int nt, int n, float *traces, cudaStream_t s,
+                              const int *n_dev)
 {
     k_sample_pts<<<blocks((int64_t)nshots * nrec), kThreads, 0, s>>>(g, f, pts, nshots, nrec, nt,
-                                                                     n, traces);
+                                                                     n, traces, n_dev);
     return cudaGetLastError();
 }
 
 cudaError_t launch_inject_pts(const Geom &g, float *f, const PointTaps *pts, int npts,
                               int per_shot, const float *W, const float *sig_z,
                               const float *sig_y, const float *sig_x, const float *q, int nt,
-                              int n, float dt2, float factor, int kind, cudaStream_t s)
+                              int n, float dt2, float factor, int kind, cudaStream_t s,
+                              const int *n_dev)
 {
     const int64_t rows = (int64_t)npts * kTaps * (g.ndim == 3 ? kTaps : 1);
     k_inject_pts<<<blocks(rows), kThreads, 0, s>>>(g, f, pts, npts, per_shot, W, sig_z, sig_y,
-                                                   sig_x, q, nt, n, dt2, factor, kind);
+                                                   sig_x, q, nt, n, dt2, factor, kind, n_dev);
     return cudaGetLastError();
 }
 

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
         if (sxx >= x0 && sxx < x0 + 4) {
             src_z = sz;
             src_e = sxx - x0;
-            srcv = p.dt2 * p.wavelet[(int64_t)shot * p.nt + p.n];
+            srcv = p.dt2 * p.wavelet[(int64_t)shot * p.nt + (p.n_dev ? *p.n_dev : 0) + p.n];
         }
     }
     const float2 two = make_float2(2.0f, 2.0f);

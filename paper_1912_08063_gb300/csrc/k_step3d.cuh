@@ -456,7 +456,7 @@ __device__ __forceinline__ void run_segment(Ctx<C, MODE> &c, int col, int z0, in
             c.src_j = sz;
             c.src_r = sy - c.y0;
             c.src_e = sx - c.x0;
-            c.srcv = p.dt2 * p.wavelet[(int64_t)c.shot * p.nt + p.n];
+            c.srcv = p.dt2 * p.wavelet[(int64_t)c.shot * p.nt + (p.n_dev ? *p.n_dev : 0) + p.n];
         }
     }
 #pragma unroll

@@ -58,7 +58,7 @@ int64_t estimate_bytes(const fwi_request &r, int nb, int snap_slots)
 {
     const int64_t nz = r.shape[0] + 2 * nb, ny = r.ndim == 3 ? r.shape[1] + 2 * nb : 1,
                   nx = r.shape[2] + 2 * nb;
-    const int64_t field = round_up(nz * ny * round_up(nx, 4), 64) * 4;
+    const int64_t field = round_up(nz * ny * round_up(nx, 8), 64) * 4;
     const int64_t phys = r.shape[0] * r.shape[1] * r.shape[2] * 4;
     const int64_t traces = (int64_t)r.nt * r.nrec * 4;
     int64_t b = field + 2 * phys + 2 * traces + (int64_t)r.nt * 4 + (8 << 20);
@@ -97,7 +97,7 @@ int admit(Slot &s, int idx, const fwi_request &r, const fwi_serve_opts &o)
     const int esz = r.snap_dtype == FWI_SNAP_FP32 ? 4 : 2;
     const int64_t nz = r.shape[0] + 2 * o.nb, ny = r.ndim == 3 ? r.shape[1] + 2 * o.nb : 1,
                   nx = r.shape[2] + 2 * o.nb;
-    mo.snap_budget_bytes = (int64_t)o.snap_slots * 2 * round_up(nz * ny * round_up(nx, 4), 64) * esz;
+    mo.snap_budget_bytes = (int64_t)o.snap_slots * 2 * round_up(nz * ny * round_up(nx, 8), 64) * esz;
     if (mo.snap_budget_bytes <= 0) mo.snap_budget_bytes = 1;
     int rc = fwi_create_model(&s.model, r.ndim, r.shape, r.spacing, r.vp, r.dt, r.nt, &mo,
                               s.stream);

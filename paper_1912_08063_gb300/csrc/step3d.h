@@ -32,6 +32,7 @@ struct Step3dParams {
     const int64_t *src_off;       // may be null (kModeStep: injection; kModeAdj: g term)
     const float *wavelet;
     int nt, n;
+    const int *n_dev;             // nullable: the step index is *n_dev + n
     float dt2;
     unsigned *err;                // status word: bit 1 (value 2) = a bounded wait gave up
     int aux_fmt;                  // kModeAdj: aux tile of FP32 (0) or BF16 (1) / FP16 (2)

@@ -72,3 +72,23 @@ def test_admission_respects_the_budget():
         assert held <= budget
     # and requests were admitted as memory freed up, not all at once
     assert len({round(x["t_admit"], 6) for x in res}) > 1
+
+
+def test_graph_replayed_forward_equals_direct_call():
+    """Forward requests in the serving loop run their turns as captured CUDA graphs that
+    read the step index from a device counter (turns of 6 steps here; nt not a multiple
+    of 6, so the last steps run one by one); the traces equal a direct forward call bit
+    for bit."""
+    from paper_1912_08063_gb300 import fwi
+    reqs = [r for r in _requests(10, seed=5) if r["kind"] == "forward"][:4]
+    assert reqs
+    for r in reqs:
+        r["arrival"] = 0.0
+    res, out = fwi.fwi_serve(reqs, max_active=4, steps_per_turn=6, snap_slots=4)
+    for r, x, o in zip(reqs, res, out):
+        assert x["status"] == 0
+        m = fwi.FwiModel(torch.from_numpy(r["v"]).cuda(), r["h"], r["dt"], r["nt"])
+        acq = fwi.Acquisition([r["src"]], r["rec"])
+        direct = m.forward(acq, torch.from_numpy(r["wavelet"][None]).cuda())[0].cpu().numpy()
+        m.close()
+        assert np.array_equal(np.asarray(o).reshape(direct.shape), direct)
