@@ -295,7 +295,23 @@ def batched_section(dev, nt=3000):
     t1 = time.perf_counter() - t0
     pts = m.info()["points"]
     m.close()
-    return {"workload": w.name, "shots": w.nshots, "nt": w.nt,
+    # forward only, the same 64 shots: single steps against two steps per pass (temporal
+    # blocking, fwi_opts.temporal_blocking)
+    fwd = {}
+    for tbk in (False, True):
+        mf = fwi.FwiModel(torch.from_numpy(w.v).to(dev), w.h, w.dt, w.nt, order=w.order,
+                          sponge_vref=4500.0, temporal_blocking=tbk)
+        mf.forward(acq, wav)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mf.forward(acq, wav)
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t0
+        mf.close()
+        key = "two_step_pass" if tbk else "single_step"
+        fwd[key] = {"seconds": round(tf, 4),
+                    "gpts_per_s": round(gpts_per_s(pts * w.nshots, w.nt, tf), 2)}
+    return {"workload": w.name, "shots": w.nshots, "nt": w.nt, "forward_only": fwd,
             "shots_per_s": round(w.nshots / tb, 3),
             "shots_per_s_per_shot_calls": round(w.nshots / t1, 3),
             "gpts_per_s": round(gpts_per_s(pts * w.nshots, w.nt, tb), 2),

@@ -67,7 +67,10 @@ typedef struct {
     int32_t timing;             /* 1: bracket every time-step launch with CUDA events and
                                    accumulate kernel times (read with fwi_model_info);
                                    the call then waits for its stream at the end        */
-    int32_t reserved;
+    int32_t temporal_blocking;  /* 1: 2-D forward calls whose shots fill the GPU advance
+                                   two time steps per pass (same results bit for bit;
+                                   measured slower than single steps on GB300, see the
+                                   design notes); default 0                             */
 } fwi_opts;
 
 /* Acquisition geometry of one call: shot s has one source and nrec receivers, each a

@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "fwi_internal.h"
@@ -154,7 +155,7 @@ struct fwi_model {
     // workspace
     int cap_shots = 0, cap_nrec = 0;
     DevBuf u[2], mu[2], g32, g64, traces, src_off, rec_off, inj, src_scale, maxbits, partials,
-        phi, snaps, scales, src_pts, rec_pts, step_ctr;
+        phi, snaps, scales, src_pts, rec_pts, step_ctr, ut[2];   // ut: spare forward states
     DevBuf stage_in[3], stage_out[2];
     int nslots = 0;
     size_t slot_bytes = 0;
@@ -686,11 +687,14 @@ struct FwdJob {
     int ns = 0, nr = 0;
     StepParams p{};
     float *tr = nullptr;    // device traces target (may be null)
-    int cur = 0, n = 0;
-    // CUDA graph of one turn: g_units steps from buffer parity g_cur, replayed with the
-    // device step counter m->step_ctr (dev_n: its value as the host last set it)
+    float *uc = nullptr, *up = nullptr;   // u^n and u^{n-1}
+    int n = 0;
+    int tb_chunks = 0;      // z-chunks of the two-step pass (0: single steps only)
+    // CUDA graph of one turn: g_units steps from the state buffers (g_uc, g_up), replayed
+    // with the device step counter m->step_ctr (dev_n: its value as the host last set it)
     cudaGraphExec_t gexec = nullptr;
-    int g_units = 0, g_cur = -1, dev_n = -1;
+    const float *g_uc = nullptr;
+    int g_units = 0, dev_n = -1;
     int64_t g_kernels = 0;
     bool g_failed = false;
     FwdJob() = default;
@@ -717,8 +721,19 @@ int fwd_setup(FwdJob &j, fwi_model *m, int ns, int nr, const float *wav, float *
     // an on-grid source is injected inside the step; off-grid taps right after it
     j.p.src_off = m->og_src ? nullptr : m->src_off.as<int64_t>();
     j.p.wavelet = wav;
-    j.cur = 0;
+    j.uc = m->u[0].as<float>();
+    j.up = m->u[1].as<float>();
     j.n = 0;
+    // 2-D batches wide enough to fill the GPU advance two steps per pass when the source
+    // is a node (off-grid source taps are added between steps)
+    j.tb_chunks = (m->og_src || !m->opts.temporal_blocking) ? 0 : step2d_tb2_chunks(m->g, ns);
+    if (j.tb_chunks > 0) {
+        const size_t fbytes = (size_t)ns * m->g.field * sizeof(float);
+        if (m->ut[0].ensure(fbytes) != FWI_OK || m->ut[1].ensure(fbytes) != FWI_OK) {
+            cudaGetLastError();
+            j.tb_chunks = 0;   // no room for the spare states: single steps
+        }
+    }
     return FWI_OK;
 }
 
@@ -765,15 +780,15 @@ int fwd_capture(FwdJob &j, int units)
     int rc = FWI_OK;
     StepParams p = j.p;
     p.n_dev = m->step_ctr.as<int>();
-    int cur = j.cur;
+    float *uc = j.uc, *up = j.up;
     for (int i = 0; i < units && rc == FWI_OK; ++i) {
-        p.cur = m->u[cur].as<float>();
-        p.prev = m->u[1 - cur].as<float>();
+        p.cur = uc;
+        p.prev = up;
         p.n = i;
         ++m->launches;
         rc = raw_step(m, p, j.ns, false, j.s);
         if (rc == FWI_OK) rc = after_forward_step(m, p, p.prev, j.ns, j.nr, i, j.tr, j.s);
-        cur = 1 - cur;
+        std::swap(uc, up);
     }
     if (rc == FWI_OK) {
         ++m->launches;
@@ -789,7 +804,7 @@ int fwd_capture(FwdJob &j, int units)
         j.g_failed = true;
     } else {
         j.g_units = units;
-        j.g_cur = j.cur;
+        j.g_uc = j.uc;
         j.g_kernels = nk;
     }
     if (graph) cudaGraphDestroy(graph);
@@ -803,8 +818,8 @@ int fwd_advance(FwdJob &j, int64_t units, bool *done)
     // captured graph: the buffer parity repeats after it and the step index comes from
     // the device counter
     if (units >= 2 && units <= 64 && units % 2 == 0 && m->nt - j.n >= units &&
-        !m->opts.timing && !j.g_failed) {
-        if (!j.gexec || j.g_units != units || j.g_cur != j.cur) FWI_TRY(fwd_capture(j, (int)units));
+        !m->opts.timing && !j.g_failed && j.tb_chunks == 0) {
+        if (!j.gexec || j.g_units != units || j.g_uc != j.uc) FWI_TRY(fwd_capture(j, (int)units));
         if (j.gexec) {
             if (j.dev_n != j.n) {
                 FWI_LAUNCH(m, launch_set_counter(m->step_ctr.as<int>(), j.n, j.s));
@@ -818,13 +833,32 @@ int fwd_advance(FwdJob &j, int64_t units, bool *done)
             return FWI_OK;
         }
     }
-    for (int64_t u = 0; u < units && j.n < m->nt; ++u, ++j.n) {
-        j.p.cur = m->u[j.cur].as<float>();
-        j.p.prev = m->u[1 - j.cur].as<float>();
+    for (int64_t u = 0; u < units && j.n < m->nt;) {
+        j.p.cur = j.uc;
+        j.p.prev = j.up;
         j.p.n = j.n;
+        if (j.tb_chunks > 0 && u + 2 <= units && j.n + 2 <= m->nt) {
+            // two steps in one pass into the spare pair, which becomes the state
+            float *o1 = (j.uc == m->u[0].as<float>() || j.uc == m->u[1].as<float>())
+                            ? m->ut[0].as<float>() : m->u[0].as<float>();
+            float *o2 = (o1 == m->ut[0].as<float>()) ? m->ut[1].as<float>() : m->u[1].as<float>();
+            ++m->launches;
+            FWI_CU(launch_step2d_tb2(j.p, j.ns, o1, o2, j.tb_chunks, j.s));
+            FWI_TRY(after_forward_step(m, j.p, o1, j.ns, j.nr, j.n, j.tr, j.s));
+            StepParams p1 = j.p;
+            p1.n = j.n + 1;
+            FWI_TRY(after_forward_step(m, p1, o2, j.ns, j.nr, j.n + 1, j.tr, j.s));
+            j.up = o1;
+            j.uc = o2;
+            j.n += 2;
+            u += 2;
+            continue;
+        }
         FWI_TRY(step_launch(m, j.p, j.ns, false, 0, j.s));
         FWI_TRY(after_forward_step(m, j.p, j.p.prev, j.ns, j.nr, j.n, j.tr, j.s));
-        j.cur = 1 - j.cur;
+        std::swap(j.uc, j.up);
+        ++j.n;
+        ++u;
     }
     *done = j.n >= m->nt;
     return FWI_OK;
@@ -1363,15 +1397,14 @@ int fwi_forward(fwi_model *m, const fwi_acq *acq, const float *wavelets, float *
     FWI_TRY(fwd_setup(job, m, ns, nr, (const float *)wav, (float *)trdev, s));
     bool done = false;
     FWI_TRY(fwd_advance(job, INT64_MAX, &done));
-    const int cur = job.cur;
-    FWI_LAUNCH(m, launch_nonfinite_check(m->u[cur].as<float>(), (int64_t)ns * m->g.field, m->d_flag, s));
+    FWI_LAUNCH(m, launch_nonfinite_check(job.uc, (int64_t)ns * m->g.field, m->d_flag, s));
     bool sync = trhost;
     if (final_state) {
         const bool fhost = !is_device_ptr(final_state);
         const int64_t pts = (int64_t)m->g.nz * m->g.ny * m->g.nx;
         for (int sh = 0; sh < ns; ++sh)
             for (int k = 0; k < 2; ++k) {
-                const float *srcp = m->u[k == 0 ? cur : 1 - cur].as<float>() + (int64_t)sh * m->g.field;
+                const float *srcp = (k == 0 ? job.uc : job.up) + (int64_t)sh * m->g.field;
                 float *dst = final_state + ((int64_t)sh * 2 + k) * pts;
                 FWI_CU(cudaMemcpy2DAsync(dst, m->g.nx * sizeof(float), srcp, m->g.px * sizeof(float),
                                          m->g.nx * sizeof(float), (size_t)m->g.nz * m->g.ny,

@@ -33,6 +33,56 @@ __device__ __forceinline__ float4 ld4(const float *__restrict__ f, int64_t row, 
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 
+// L c at the 4 points of a group: x from the window w (groups x0 - M .. x0 + 3 + M, the
+// centre group at w[M .. M + 3]), z from the queue q (row j + k in q[M + k]).
+template <int M>
+__device__ __forceinline__ void lap4(const float (&w)[4 + 2 * M], const float4 (&q)[2 * M + 1],
+                                     const Coefs &cf, float2 &l0, float2 &l1)
+{
+    float lx[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+        for (int k = 1; k <= M; ++k) {
+            const float s = w[M + e + k] + w[M + e - k];
+            if (k & 1) a0 = fmaf(cf.cx[k], s, a0);
+            else a1 = fmaf(cf.cx[k], s, a1);
+        }
+        lx[e] = a0 + a1;
+    }
+    float2 za = make_float2(0.f, 0.f), zb = za;
+#pragma unroll
+    for (int k = 1; k <= M; ++k) {
+        const float2 cc = make_float2(cf.cz[k], cf.cz[k]);
+        za = __ffma2_rn(cc, __fadd2_rn(lo2(q[M + k]), lo2(q[M - k])), za);
+        zb = __ffma2_rn(cc, __fadd2_rn(hi2(q[M + k]), hi2(q[M - k])), zb);
+    }
+    const float4 c = q[M];
+    const float2 c0 = make_float2(cf.c0, cf.c0);
+    l0 = __ffma2_rn(c0, lo2(c), __fadd2_rn(za, make_float2(lx[0], lx[1])));
+    l1 = __ffma2_rn(c0, hi2(c), __fadd2_rn(zb, make_float2(lx[2], lx[3])));
+}
+
+// The damped update of a group: (2c + W lap - (1 - s) prev [+ srcv at point se]) / (1 + s).
+__device__ __forceinline__ float4 update4(float4 c, float2 l0, float2 l1, float4 pv, float4 Wv,
+                                          const float (&sx)[4], float sz, int se, float srcv)
+{
+    const float2 two = make_float2(2.0f, 2.0f);
+    const float2 r0 = __ffma2_rn(lo2(Wv), l0, __fmul2_rn(two, lo2(c)));
+    const float2 r1 = __ffma2_rn(hi2(Wv), l1, __fmul2_rn(two, hi2(c)));
+    float rhs[4] = {r0.x, r0.y, r1.x, r1.y};
+    const float pp[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float s = sx[e] + sz;
+        float v = fmaf(s - 1.0f, pp[e], rhs[e]);
+        if (e == se) v += srcv;
+        rhs[e] = __fdividef(v, 1.0f + s);
+    }
+    return make_float4(rhs[0], rhs[1], rhs[2], rhs[3]);
+}
+
 // Global operands of one output row: the row entering the z-queue, the x-window groups
 // left and right of the centre, and the pointwise values.
 template <int M, bool IMG>
@@ -81,7 +131,6 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
             srcv = p.dt2 * p.wavelet[(int64_t)shot * p.nt + (p.n_dev ? *p.n_dev : 0) + p.n];
         }
     }
-    const float2 two = make_float2(2.0f, 2.0f);
     unsigned mxa = 0u, mxd = 0u;   // bits of max|out| and max|out - c| (p.maxbits set)
 
     auto load_row = [&](int z, RowIn<M, IMG> &in) {
@@ -125,44 +174,15 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
             const float4 v = (g4 == W4) ? q[M] : in.win[g4 < W4 ? g4 : g4 - 1];
             w[4 * g4] = v.x, w[4 * g4 + 1] = v.y, w[4 * g4 + 2] = v.z, w[4 * g4 + 3] = v.w;
         }
-        float lx[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-            for (int k = 1; k <= M; ++k) {
-                const float s = w[M + e + k] + w[M + e - k];
-                if (k & 1) a0 = fmaf(p.c.cx[k], s, a0);
-                else a1 = fmaf(p.c.cx[k], s, a1);
-            }
-            lx[e] = a0 + a1;
-        }
-        float2 za = make_float2(0.f, 0.f), zb = za;
-#pragma unroll
-        for (int k = 1; k <= M; ++k) {
-            const float2 cc = make_float2(p.c.cz[k], p.c.cz[k]);
-            za = __ffma2_rn(cc, __fadd2_rn(lo2(q[M + k]), lo2(q[M - k])), za);
-            zb = __ffma2_rn(cc, __fadd2_rn(hi2(q[M + k]), hi2(q[M - k])), zb);
-        }
+        float2 l0, l1;
+        lap4<M>(w, q, p.c, l0, l1);
         const float4 c = q[M];
-        const float2 c0 = make_float2(p.c.c0, p.c.c0);
-        const float2 l0 = __ffma2_rn(c0, lo2(c), __fadd2_rn(za, make_float2(lx[0], lx[1])));
-        const float2 l1 = __ffma2_rn(c0, hi2(c), __fadd2_rn(zb, make_float2(lx[2], lx[3])));
         if (xin) {
             const float4 pv = in.pv, Wv = in.Wv;
-            const float2 r0 = __ffma2_rn(lo2(Wv), l0, __fmul2_rn(two, lo2(c)));
-            const float2 r1 = __ffma2_rn(hi2(Wv), l1, __fmul2_rn(two, hi2(c)));
-            float rhs[4] = {r0.x, r0.y, r1.x, r1.y};
-            const float pp[4] = {pv.x, pv.y, pv.z, pv.w};
-            const float sz = p.sig_z[z];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float s = sx[e] + sz;
-                float v = fmaf(s - 1.0f, pp[e], rhs[e]);
-                if (!IMG && z == src_z && e == src_e) v += srcv;
-                rhs[e] = __fdividef(v, 1.0f + s);
-            }
-            *(float4 *)(prev + row + x0) = make_float4(rhs[0], rhs[1], rhs[2], rhs[3]);
+            const float4 o = update4(c, l0, l1, pv, Wv, sx, p.sig_z[z],
+                                     (!IMG && z == src_z) ? src_e : -1, srcv);
+            const float rhs[4] = {o.x, o.y, o.z, o.w};
+            *(float4 *)(prev + row + x0) = o;
             if (!IMG && p.maxbits) {
                 const float cc[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
@@ -203,6 +223,140 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
     }
 }
 
+// Two forward steps per pass (temporal blocking) for 2-D grids whose rows fit one CTA
+// (px <= 4 * tb_max_threads<M>()).  A CTA owns the output rows [z0, z1) of one shot and streams
+// t = z0 - M .. z1 + M - 1: it computes u^{n+1} at row t (from u^n rows t - M .. t + M in
+// the register queue q0, as the single step does) and u^{n+2} at row t - M (from u^{n+1}
+// rows t - 2M .. t in the register queue q1, its x-window from a shared-memory ring of the
+// last M + 2 u^{n+1} rows, and u^n row t - M, which is q0's oldest entry).  u^{n+1} rows
+// within M of the chunk are computed by both neighbouring chunks from the same inputs,
+// so each chunk writes only its own rows, and both new states go to buffers the kernel
+// does not read.  Per point and two steps: read u^n, u^{n-1}, W (W twice, the second
+// time from L2), write u^{n+1} and u^{n+2}: 20 bytes instead of 32.  The arithmetic is
+// the single step's (lap4, update4), so two blocked steps equal two single steps bit for
+// bit.
+// threads per CTA at most: 512 at radius 4 (rows up to 2048 floats, 120 registers), 256
+// at radius 8 (rows up to 1024 floats; its two queues need more than 128 registers)
+template <int M>
+constexpr int tb_max_threads() { return M == 4 ? 512 : 256; }
+
+template <int M>
+__global__ void __launch_bounds__(tb_max_threads<M>()) k_step2d_tb2(const StepParams p,
+                                                                    float *out1, float *out2)
+{
+    constexpr int Q = 2 * M + 1, W4 = M / 4, R = M + 2;
+    extern __shared__ float4 ring4[];   // R rows of px floats (u^{n+1})
+    float *ring = reinterpret_cast<float *>(ring4);
+    const int shot = blockIdx.y;
+    const int nz = p.g.nz, nx = p.g.nx, px = p.g.px;
+    const int z0 = blockIdx.x * p.zchunk, z1 = min(nz, z0 + p.zchunk);
+    const int x0 = threadIdx.x * 4;
+    const bool xin = x0 < nx, xpad = x0 < px;
+    const int64_t plane = p.g.plane;
+    const int64_t sb = (int64_t)shot * p.g.field;
+    const float *__restrict__ cur = p.cur + sb;
+    const float *__restrict__ prev = p.prev + sb;
+    float *__restrict__ o1 = out1 + sb;
+    float *__restrict__ o2 = out2 + sb;
+
+    float sx[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) sx[e] = (x0 + e < nx) ? p.sig_x[x0 + e] : 0.0f;
+    int src_z = -1, src_e = 0;
+    float srcv1 = 0.0f, srcv2 = 0.0f;
+    if (p.src_off) {
+        const int64_t so = p.src_off[shot];
+        const int sz = (int)(so / plane), sxx = (int)(so - (int64_t)sz * plane);
+        if (sxx >= x0 && sxx < x0 + 4) {
+            src_z = sz;
+            src_e = sxx - x0;
+            const int n = (p.n_dev ? *p.n_dev : 0) + p.n;
+            srcv1 = p.dt2 * p.wavelet[(int64_t)shot * p.nt + n];
+            srcv2 = p.dt2 * p.wavelet[(int64_t)shot * p.nt + n + 1];
+        }
+    }
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 q0[Q], q1[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) q1[i] = zero4;
+#pragma unroll
+    for (int i = 0; i < Q - 1; ++i) {
+        const int z = z0 - 2 * M + i;
+        q0[i] = ld4(cur, (int64_t)z * plane, x0, px, z >= 0 && z < nz);
+    }
+
+    for (int t = z0 - M; t < z1 + M; ++t) {
+        const int zn = t + M;
+        q0[Q - 1] = ld4(cur, (int64_t)zn * plane, x0, px, zn >= 0 && zn < nz);
+        // u^{n+1} at row t (zero outside the grid)
+        float4 v1 = zero4;
+        if (t >= 0 && t < nz) {
+            const int64_t row = (int64_t)t * plane;
+            float w[4 + 2 * M];
+#pragma unroll
+            for (int g4 = 0; g4 < 2 * W4 + 1; ++g4) {
+                const float4 v = (g4 == W4) ? q0[M] : ld4(cur, row, x0 + 4 * (g4 - W4), px, true);
+                w[4 * g4] = v.x, w[4 * g4 + 1] = v.y, w[4 * g4 + 2] = v.z, w[4 * g4 + 3] = v.w;
+            }
+            float2 l0, l1;
+            lap4<M>(w, q0, p.c, l0, l1);
+            if (xin) {
+                const float4 pv = __ldg((const float4 *)(prev + row + x0));
+                const float4 Wv = __ldg((const float4 *)(p.W + row + x0));
+                v1 = update4(q0[M], l0, l1, pv, Wv, sx, p.sig_z[t], t == src_z ? src_e : -1,
+                             srcv1);
+                if (t >= z0 && t < z1) *(float4 *)(o1 + row + x0) = v1;
+            }
+        }
+        q1[Q - 1] = v1;
+        if (xpad) *(float4 *)(ring + (t + R) % R * px + x0) = v1;
+        __syncthreads();
+        // u^{n+2} at row zb = t - M
+        const int zb = t - M;
+        if (zb >= z0 && zb < z1) {
+            const float *rrow = ring + (zb + R) % R * px;
+            float w[4 + 2 * M];
+#pragma unroll
+            for (int g4 = 0; g4 < 2 * W4 + 1; ++g4) {
+                const int xc = x0 + 4 * (g4 - W4);
+                const float4 v = (g4 == W4) ? q1[M]
+                                 : (xc >= 0 && xc < px) ? *(const float4 *)(rrow + xc) : zero4;
+                w[4 * g4] = v.x, w[4 * g4 + 1] = v.y, w[4 * g4 + 2] = v.z, w[4 * g4 + 3] = v.w;
+            }
+            float2 l0, l1;
+            lap4<M>(w, q1, p.c, l0, l1);
+            if (xin) {
+                const int64_t row = (int64_t)zb * plane;
+                const float4 Wv = __ldg((const float4 *)(p.W + row + x0));
+                *(float4 *)(o2 + row + x0) = update4(q1[M], l0, l1, q0[0], Wv, sx, p.sig_z[zb],
+                                                     zb == src_z ? src_e : -1, srcv2);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < Q - 1; ++i) {
+            q0[i] = q0[i + 1];
+            q1[i] = q1[i + 1];
+        }
+    }
+}
+
+template <int M>
+cudaError_t launch_tb2(const StepParams &p0, int nshots, float *out1, float *out2, int nch,
+                       cudaStream_t s)
+{
+    StepParams p = p0;
+    p.zchunk = (p.g.nz + nch - 1) / nch;
+    p.nzchunks = (p.g.nz + p.zchunk - 1) / p.zchunk;
+    const int threads = ((p.g.px / 4 + 31) / 32) * 32;
+    const int smem = (M + 2) * p.g.px * (int)sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute((const void *)k_step2d_tb2<M>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(p.nzchunks, nshots);
+    k_step2d_tb2<M><<<grid, threads, smem, s>>>(p, out1, out2);
+    return cudaGetLastError();
+}
+
 template <int M, bool IMG>
 cudaError_t launch2(const StepParams &p0, int nshots, cudaStream_t s)
 {
@@ -224,6 +378,26 @@ cudaError_t launch2(const StepParams &p0, int nshots, cudaStream_t s)
 }
 
 }  // namespace
+
+int step2d_tb2_chunks(const Geom &g, int nshots)
+{
+    const int maxt = g.M == 4 ? tb_max_threads<4>() : tb_max_threads<8>();
+    if (g.ndim != 2 || g.px > 4 * maxt) return 0;
+    // z-chunks of at least 8M rows (the 2M overlap rows cost at most a quarter) and
+    // enough of them for two CTAs on each of the 152 SMs
+    const int maxch = g.nz / (8 * g.M);
+    const int want = (2 * 152 + nshots - 1) / nshots;
+    if (maxch < 1 || (int64_t)maxch * nshots < 152) return 0;
+    return want < maxch ? want : maxch;
+}
+
+cudaError_t launch_step2d_tb2(const StepParams &p, int nshots, float *out1, float *out2,
+                              int nchunks, cudaStream_t s)
+{
+    if (p.g.M == 4) return launch_tb2<4>(p, nshots, out1, out2, nchunks, s);
+    if (p.g.M == 8) return launch_tb2<8>(p, nshots, out1, out2, nchunks, s);
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_step2d(const StepParams &p, int nshots, bool imaging, cudaStream_t s)
 {

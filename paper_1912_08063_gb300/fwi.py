@@ -34,7 +34,7 @@ c_i32, c_i64, c_f32, c_f64, c_vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_flo
 class fwi_opts(ctypes.Structure):
     _fields_ = [("order", c_i32), ("nb", c_i32), ("snap_dtype", c_i32), ("fold_every", c_i32),
                 ("snap_budget_bytes", c_i64), ("sponge_r0", c_f32), ("sponge_vref", c_f32),
-                ("timing", c_i32), ("reserved", c_i32)]
+                ("timing", c_i32), ("temporal_blocking", c_i32)]
 
 
 class fwi_acq(ctypes.Structure):
@@ -346,7 +346,7 @@ class FwiModel:
 
     def __init__(self, v, spacing, dt, nt, order=8, nb=20, snap_dtype="fp32",
                  snap_budget_bytes=0, sponge_r0=1e-3, sponge_vref=0.0, fold_every=64,
-                 timing=False, stream=None):
+                 timing=False, stream=None, temporal_blocking=False):
         import torch
         if isinstance(v, np.ndarray):
             v = torch.from_numpy(np.ascontiguousarray(v, dtype=np.float32))
@@ -364,7 +364,8 @@ class FwiModel:
         self.dt, self.nt, self.order = float(dt), int(nt), int(order)
         self.opts = fwi_opts(int(order), int(nb) if nb else -1, SNAP_DTYPES[snap_dtype],
                              int(fold_every), int(snap_budget_bytes), float(sponge_r0),
-                             float(sponge_vref), int(bool(timing)), 0)
+                             float(sponge_vref), int(bool(timing)),
+                             int(bool(temporal_blocking)))
         self.handle = fwi_create_model(self.ndim, self.shape, sp, v, dt, nt, self.opts,
                                        stream)
 
