@@ -282,10 +282,16 @@ def batched_section(dev, nt=3000):
     na = i1["adj_step_launches"] - i0["adj_step_launches"]
     fms = (i1["fwd_step_ms"] - i0["fwd_step_ms"]) / max(nf, 1)
     ams = (i1["adj_step_ms"] - i0["adj_step_ms"]) / max(na, 1)
+    # W is one field shared by all shots: per point and step the forward step moves
+    # 12 + 4 / shots bytes, the reverse step 22 + 4 / shots (u^m as a 2-byte code)
+    bf = 12.0 + 4.0 / w.nshots
+    ba = BYTES_ADJ - 4.0 + 4.0 / w.nshots
     kern = {"fwd_step_avg_ms": round(fms, 4), "fwd_step_launches": nf,
-            "fwd_step_GB/s": round(BYTES_FWD * i1["points"] * w.nshots / (fms * 1e-3) / 1e9, 1),
+            "fwd_bytes_per_point": round(bf, 3),
+            "fwd_step_GB/s": round(bf * i1["points"] * w.nshots / (fms * 1e-3) / 1e9, 1),
             "adj_step_avg_ms": round(ams, 4), "adj_step_launches": na,
-            "adj_step_GB/s": round(BYTES_ADJ * i1["points"] * w.nshots / (ams * 1e-3) / 1e9, 1),
+            "adj_bytes_per_point": round(ba, 3),
+            "adj_step_GB/s": round(ba * i1["points"] * w.nshots / (ams * 1e-3) / 1e9, 1),
             "kernel_seconds": round((nf * fms + na * ams) / 1e3, 3)}
     singles = [fwi.Acquisition(w.src[i:i + 1], w.rec) for i in range(w.nshots)]
     t0 = time.perf_counter()
