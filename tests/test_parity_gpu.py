@@ -85,6 +85,7 @@ def test_forward_random_models(ndim, shape, order, nb):
     tr, fin = gpu_forward(m, acq, w)
     rtr, rfin = p.forward(final=True)
     e_tr, e_fin = rel(tr, rtr), rel(fin.reshape(rfin.shape), rfin)
+    print(f"forward {ndim}d {shape} o{order} nb{nb}: traces {e_tr:.2e} final {e_fin:.2e}")
     assert e_tr <= TOL_FWD and e_fin <= TOL_FWD, (e_tr, e_fin)
 
 
@@ -94,7 +95,9 @@ def test_forward_batched_shots_2d():
     m, p, acq = make_pair(w)
     tr, fin = gpu_forward(m, acq, w)
     rtr, rfin = p.forward(final=True)
-    assert rel(tr, rtr) <= TOL_FWD and rel(fin.reshape(rfin.shape), rfin) <= TOL_FWD
+    e_tr, e_fin = rel(tr, rtr), rel(fin.reshape(rfin.shape), rfin)
+    print(f"forward 2d 5 batched shots: traces {e_tr:.2e} final {e_fin:.2e}")
+    assert e_tr <= TOL_FWD and e_fin <= TOL_FWD
 
 
 def test_forward_single_step_and_host_buffers():
@@ -126,6 +129,7 @@ def test_misfit_matches_oracle():
         r = (a - b).astype(np.float64)
         ref = oracle.misfit(r, np.zeros_like(r))
         # same terms, different FP64 summation order: |error| <= n eps sum|terms|
+        print(f"misfit n={n}: rel {abs(out.item() - ref) / ref:.2e}")
         assert abs(out.item() - ref) <= n * 2.0 ** -52 * ref
 
 
@@ -166,9 +170,11 @@ def test_source_dot_product_gpu(ndim, shape, order):
     Fx = m.forward(acq, torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
     Fty = m.source_adjoint(acq, torch.from_numpy(y).cuda()).cpu().numpy().astype(np.float64)
     lhs, rhs = np.sum(Fx * y), np.sum(x * Fty)
+    ref = p.source_adjoint(y.astype(np.float64))
+    print(f"dot product {ndim}d o{order}: rel {abs(lhs - rhs) / max(abs(lhs), abs(rhs)):.2e}, "
+          f"source adjoint vs oracle {rel(Fty, ref):.2e}")
     assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs)), (lhs, rhs)
     # and the GPU source adjoint against the oracle's
-    ref = p.source_adjoint(y.astype(np.float64))
     assert rel(Fty, ref) <= TOL_FWD
 
 
