@@ -14,6 +14,15 @@ With N > 1 (torchrun) every rank runs an independent replica of the workload (sh
 are independent units; the library has no multi-GPU path) and rank 0 prints one JSON
 line with the whole-job rate.  ``--impl reference`` times the FP64 CPU oracle on a
 bounded sample of the same workload (rank 0 only).
+
+Besides the contract's keys the line carries: ``roofline.kernels`` (each 3-D step
+instantiation's launches, average CUDA-event time, algorithmic bytes per point, achieved
+GB/s and recorded DRAM traffic per launch; ``roofline`` itself is the one with the most
+device time), ``serving`` (a Poisson stream of mixed 2-D/3-D forward/gradient requests
+through the continuous-batching loop against one request at a time: shots/s, p50/p99
+latency) and ``batched_2d`` (64 shots of the 400 x 1024 faulted model in one gradient
+call against 64 one-shot calls, with the step kernels' times, and the forward-only rate
+with single steps and with two steps per pass).
 """
 from __future__ import annotations
 
