@@ -236,7 +236,7 @@ def serving_section(dev, n_req, seed=4):
         for r, a in zip(reqs, arrivals):
             r["arrival"] = float(a)
         t0 = time.perf_counter()
-        res, _ = fwi.fwi_serve(reqs, max_active=max_active, steps_per_turn=16, snap_slots=16)
+        res, _ = fwi.fwi_serve(reqs, max_active=max_active, steps_per_turn=16, snap_slots=64)
         wall = time.perf_counter() - t0
         lat = np.array([x["t_done"] - a for x, a in zip(res, arrivals)])
         ok = sum(1 for x in res if x["status"] == 0)

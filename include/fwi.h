@@ -268,7 +268,7 @@ typedef struct {
     int64_t hbm_budget_bytes;   /* device memory for admitted requests (0: 80 % free)   */
     int32_t max_active;         /* admitted requests at once (default 16)               */
     int32_t steps_per_turn;     /* time steps issued per request per turn (default 8)   */
-    int32_t snap_slots;         /* checkpoints per gradient request (default 8)         */
+    int32_t snap_slots;         /* checkpoints per gradient request (default 64)        */
     int32_t nb;                 /* sponge width (default 20)                            */
 } fwi_serve_opts;
 

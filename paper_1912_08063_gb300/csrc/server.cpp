@@ -132,7 +132,7 @@ extern "C" int fwi_serve(const fwi_request *reqs, int32_t n, const fwi_serve_opt
     if (opts) o = *opts;
     if (o.max_active <= 0) o.max_active = 16;
     if (o.steps_per_turn <= 0) o.steps_per_turn = 8;
-    if (o.snap_slots <= 0) o.snap_slots = 8;
+    if (o.snap_slots <= 0) o.snap_slots = 64;
     if (o.nb == 0) o.nb = 20;
     if (o.hbm_budget_bytes <= 0) {
         size_t fr = 0, tot = 0;

@@ -235,7 +235,7 @@ def fwi_model_info(model) -> dict:
     return out
 
 
-def fwi_serve(requests, budget_bytes=0, max_active=16, steps_per_turn=8, snap_slots=8, nb=20):
+def fwi_serve(requests, budget_bytes=0, max_active=16, steps_per_turn=8, snap_slots=64, nb=20):
     """Runs a request stream through the serving loop.  `requests` is a list of dicts with
     keys kind ('forward'/'gradient'), v (float32 physical grid), h, dt, nt, order,
     snap_dtype, src (3 ints), rec (int32 [nrec][3]), wavelet (float32 [nt]), d_obs
