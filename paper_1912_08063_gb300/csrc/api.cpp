@@ -884,7 +884,77 @@ struct GradJob {
     int kdone = 0;    // forward steps already issued of the current ADVANCE action
     int aux_slot = -1;   // checkpoint the next reverse step reads u^m from in place
     int st_slot = -1, st_comps = 0;   // store the next forward step writes (3-D)
+    // CUDA graphs of kGradGraphSteps plain forward steps (no checkpoint store or max-abs
+    // among them), keyed by the buffer parity at their start and whether they record
+    // traces, replayed with the device step counter m->step_ctr (dev_n: its value as the
+    // host last set it).  Used for turns of the serving loop.
+    cudaGraphExec_t gx[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int64_t gk[2][2] = {{0, 0}, {0, 0}};
+    bool g_failed = false;
+    int64_t dev_n = -1;
+    GradJob() = default;
+    GradJob(const GradJob &) = delete;
+    GradJob &operator=(const GradJob &) = delete;
+    ~GradJob()
+    {
+        for (auto &row : gx)
+            for (auto &e : row)
+                if (e) cudaGraphExecDestroy(e);
+    }
 };
+
+constexpr int kGradGraphSteps = 8;
+
+// Captures kGradGraphSteps forward steps from buffer parity `par`, recording traces when
+// `rec`, into j.gx[par][rec]; a failed capture turns graphs off for the job.
+int grad_capture(GradJob &j, int par, bool rec)
+{
+    fwi_model *m = j.m;
+    FWI_TRY(m->step_ctr.ensure(sizeof(int)));
+    if (use_step3d(m) && m->resident <= 0) m->resident = step3d_resident_ctas(m->g.M);
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(j.s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        j.g_failed = true;
+        return FWI_OK;
+    }
+    const int64_t l0 = m->launches;
+    int rc = FWI_OK;
+    StepParams p = j.pf;
+    p.n_dev = m->step_ctr.as<int>();
+    p.maxbits = nullptr;
+    p.st_code = nullptr;
+    int cur = par;
+    for (int i = 0; i < kGradGraphSteps && rc == FWI_OK; ++i) {
+        p.cur = m->u[cur].as<float>();
+        p.prev = m->u[1 - cur].as<float>();
+        p.n = i;
+        ++m->launches;
+        rc = raw_step(m, p, j.ns, false, j.s);
+        if (rc == FWI_OK)
+            rc = after_forward_step(m, p, p.prev, j.ns, j.nr, i, rec ? j.tr : nullptr, j.s);
+        cur = 1 - cur;
+    }
+    if (rc == FWI_OK) {
+        ++m->launches;
+        if (launch_tick(m->step_ctr.as<int>(), kGradGraphSteps, j.s) != cudaSuccess)
+            rc = FWI_ERR_CUDA;
+    }
+    const cudaError_t ec = cudaStreamEndCapture(j.s, &graph);
+    const int64_t nk = m->launches - l0;
+    m->launches = l0;
+    cudaGraphExec_t &gx = j.gx[par][rec ? 1 : 0];
+    if (rc != FWI_OK || ec != cudaSuccess || !graph ||
+        cudaGraphInstantiate(&gx, graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        gx = nullptr;
+        j.g_failed = true;
+    } else {
+        j.gk[par][rec ? 1 : 0] = nk;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    return FWI_OK;
+}
 
 // Checkpoint slots for the budget, the schedule and its per-action component counts,
 // staging of the inputs, and the initial state.
@@ -998,6 +1068,32 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
         const bool next_store = ia + 1 < nact && m->sched[2 * (ia + 1)] == 2;
         if (kind == 1) {   // ADVANCE (may span several turns)
             while (j.kdone < arg && used < units) {
+                // a serving turn replays a captured run of plain steps when the next
+                // kGradGraphSteps steps hold no checkpoint store, no max-abs step and no
+                // start or end of trace recording
+                const int G = kGradGraphSteps;
+                const int last_plain = arg - ((j.fused_max && next_store) ? 1 : 0);
+                if (units <= 64 && !m->opts.timing && !j.g_failed && j.st_slot < 0 &&
+                    j.kdone + G <= last_plain && units - used >= G &&
+                    (j.step >= j.recorded) == (j.step + G - 1 >= j.recorded)) {
+                    const int rec = j.step >= j.recorded ? 1 : 0;
+                    if (!j.gx[j.cur][rec]) FWI_TRY(grad_capture(j, j.cur, rec != 0));
+                    if (j.gx[j.cur][rec]) {
+                        if (j.dev_n != j.step) {
+                            FWI_LAUNCH(m, launch_set_counter(m->step_ctr.as<int>(), (int)j.step, s));
+                            j.dev_n = j.step;
+                        }
+                        FWI_CU(cudaGraphLaunch(j.gx[j.cur][rec], s));
+                        m->launches += j.gk[j.cur][rec];
+                        j.step += G;
+                        j.dev_n += G;
+                        if (rec) j.recorded = j.step;
+                        j.nfwd += G;
+                        j.kdone += G;
+                        used += G;
+                        continue;
+                    }
+                }
                 j.pf.cur = m->u[j.cur].as<float>();
                 j.pf.prev = m->u[1 - j.cur].as<float>();
                 j.pf.n = (int)j.step;

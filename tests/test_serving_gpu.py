@@ -92,3 +92,31 @@ def test_graph_replayed_forward_equals_direct_call():
         direct = m.forward(acq, torch.from_numpy(r["wavelet"][None]).cuda())[0].cpu().numpy()
         m.close()
         assert np.array_equal(np.asarray(o).reshape(direct.shape), direct)
+
+
+def test_graph_replayed_gradient_equals_direct_call():
+    """Gradient requests replay runs of plain forward steps as CUDA graphs in turns of 16
+    steps; with the same checkpoint budget the gradient and misfit equal a direct call
+    (steps issued one by one) bit for bit."""
+    from paper_1912_08063_gb300 import fwi
+    reqs = [r for r in _requests(12, seed=6) if r["kind"] == "gradient"][:3]
+    assert reqs
+    for r in reqs:
+        r["arrival"] = 0.0
+    slots = 5
+    res, out = fwi.fwi_serve(reqs, max_active=3, steps_per_turn=16, snap_slots=slots)
+    for r, x, o in zip(reqs, res, out):
+        assert x["status"] == 0
+        shp = r["v"].shape
+        nz = shp[0] + 40
+        ny = shp[1] + 40 if len(shp) == 3 else 1
+        nx = shp[-1] + 40
+        field = -(-(nz * ny * (-(-nx // 8) * 8)) // 64) * 64
+        m = fwi.FwiModel(torch.from_numpy(r["v"]).cuda(), r["h"], r["dt"], r["nt"],
+                         snap_dtype=r["snap_dtype"], snap_budget_bytes=slots * 2 * field * 2)
+        acq = fwi.Acquisition([r["src"]], r["rec"])
+        phi, g = m.gradient(acq, torch.from_numpy(r["wavelet"][None]).cuda(),
+                            torch.from_numpy(r["d_obs"][None]).cuda())
+        m.close()
+        assert x["misfit"] == phi.item()
+        assert np.array_equal(np.asarray(o).reshape(g.shape), g.cpu().numpy())
