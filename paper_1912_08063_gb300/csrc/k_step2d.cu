@@ -363,10 +363,36 @@ cudaError_t launch2(const StepParams &p0, int nshots, cudaStream_t s)
     StepParams p = p0;
     const int bx = (p.g.nx + kTile2 - 1) / kTile2;
     const int64_t ctas = (int64_t)bx * nshots;
-    // enough CTAs for ~16 resident per SM on 152 SMs, chunks of at least 4M rows
-    const int want = (int)((16LL * 152 + ctas - 1) / ctas);
+    // resident CTAs of this instantiation on the device (registers limit it)
+    static const int resident = [] {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step2d_reg<M, IMG, !IMG>,
+                                                          kThreads2, 0) != cudaSuccess ||
+            per < 1) {
+            cudaGetLastError();
+            per = 1;
+        }
+        return (sms > 0 ? sms : 152) * per;
+    }();
+    // z-chunks (at least 4M rows each) that best fill whole waves of resident CTAs; each
+    // chunk streams 2M warm-up rows that cost about a third of an output row
     const int maxch = p.g.nz / (4 * M) > 0 ? p.g.nz / (4 * M) : 1;
-    const int nch = want < 1 ? 1 : (want > maxch ? maxch : want);
+    int nch = 1;
+    double best = -1.0;
+    for (int c = 1; c <= maxch && c <= 64; ++c) {
+        const int zc = (p.g.nz + c - 1) / c;
+        const int64_t cn = (p.g.nz + zc - 1) / zc;
+        const int64_t tot = ctas * cn;
+        const int64_t waves = (tot + resident - 1) / resident;
+        const double fill = (double)tot / ((double)waves * resident);
+        const double score = fill / (1.0 + 0.3 * (2.0 * M) / zc);
+        if (score > best + 1e-9) {
+            best = score;
+            nch = (int)cn;
+        }
+    }
     p.zchunk = (p.g.nz + nch - 1) / nch;
     p.nzchunks = (p.g.nz + p.zchunk - 1) / p.zchunk;
     dim3 grid(bx, 1, p.nzchunks * nshots);
