@@ -69,8 +69,8 @@ typedef struct {
                                    the call then waits for its stream at the end        */
     int32_t temporal_blocking;  /* 1: 2-D forward calls whose shots fill the GPU advance
                                    two time steps per pass (same results bit for bit;
-                                   measured slower than single steps on GB300, see the
-                                   design notes); default 0                             */
+                                   measured at parity with single steps on GB300, 3 %
+                                   slower, see the design notes); default 0             */
 } fwi_opts;
 
 /* Acquisition geometry of one call: shot s has one source and nrec receivers, each a

@@ -109,8 +109,8 @@ cudaError_t launch_gather_src_pts(const Geom &g, const float *f, const PointTaps
 cudaError_t launch_step2d(const StepParams &p, int nshots, bool imaging, cudaStream_t s);
 // Two forward steps in one pass (2-D): from (p.cur = u^n, p.prev = u^{n-1}) write u^{n+1}
 // to out1 and u^{n+2} to out2 (neither may alias cur or prev); sources at steps n and
-// n + 1.  step2d_tb2_chunks gives the z-chunk count to use, 0 when the grid is too wide
-// for one CTA per row or the shots are too few to fill the GPU (then use single steps).
+// n + 1.  step2d_tb2_chunks is 0 when the batch is too small to fill the GPU (then use
+// single steps); the launcher picks its own strips and z-chunks.
 int step2d_tb2_chunks(const Geom &g, int nshots);
 cudaError_t launch_step2d_tb2(const StepParams &p, int nshots, float *out1, float *out2,
                               int nchunks, cudaStream_t s);

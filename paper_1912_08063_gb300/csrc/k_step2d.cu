@@ -223,35 +223,33 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
     }
 }
 
-// Two forward steps per pass (temporal blocking) for 2-D grids whose rows fit one CTA
-// (px <= 4 * tb_max_threads<M>()).  A CTA owns the output rows [z0, z1) of one shot and streams
-// t = z0 - M .. z1 + M - 1: it computes u^{n+1} at row t (from u^n rows t - M .. t + M in
-// the register queue q0, as the single step does) and u^{n+2} at row t - M (from u^{n+1}
-// rows t - 2M .. t in the register queue q1, its x-window from a shared-memory ring of the
-// last M + 2 u^{n+1} rows, and u^n row t - M, which is q0's oldest entry).  u^{n+1} rows
-// within M of the chunk are computed by both neighbouring chunks from the same inputs,
-// so each chunk writes only its own rows, and both new states go to buffers the kernel
-// does not read.  Per point and two steps: read u^n, u^{n-1}, W (W twice, the second
-// time from L2), write u^{n+1} and u^{n+2}: 20 bytes instead of 32.  The arithmetic is
-// the single step's (lap4, update4), so two blocked steps equal two single steps bit for
-// bit.
-// threads per CTA at most: 512 at radius 4 (rows up to 2048 floats, 120 registers), 256
-// at radius 8 (rows up to 1024 floats; its two queues need more than 128 registers)
-template <int M>
-constexpr int tb_max_threads() { return M == 4 ? 512 : 256; }
-
-template <int M>
-__global__ void __launch_bounds__(tb_max_threads<M>()) k_step2d_tb2(const StepParams p,
-                                                                    float *out1, float *out2)
+// Two forward steps per pass (temporal blocking).  A CTA of 64 threads owns a z-chunk
+// [z0, z1) of one shot and a 256-column strip [X0 - M, X0 + 256 - M).  It streams
+// t = z0 - M .. z1 + M - 1, computing u^{n+1} at row t on the whole strip (from the u^n
+// rows t - M .. t + M in the register queue q0, as the single step does) and u^{n+2} at
+// row t - M on the strip's inner 256 - 2M columns [X0, X0 + 256 - 2M).  u^{n+2} takes its
+// z-neighbours from a second register queue of u^{n+1} rows, its x-window from a
+// shared-memory ring of the last M + 2 u^{n+1} strip rows, and its "prev" u^n from q0's
+// oldest entry.  Strips overlap by 2M columns and chunks by 2M rows, so u^{n+1} near a
+// strip or chunk edge is computed by both neighbours from the same inputs.  Each CTA
+// writes only its inner columns and its own rows, and both new states go to buffers the
+// kernel does not read.  Per point and two steps: read u^n, u^{n-1} and W (W twice, the
+// second time from L2), and write u^{n+1} and u^{n+2}.  The arithmetic is the single
+// step's (lap4, update4), so two blocked steps equal two single steps bit for bit.
+template <int M, bool PF>
+__global__ void __launch_bounds__(kThreads2) k_step2d_tb2x(const StepParams p, float *out1,
+                                                            float *out2)
 {
-    constexpr int Q = 2 * M + 1, W4 = M / 4, R = M + 2;
-    extern __shared__ float4 ring4[];   // R rows of px floats (u^{n+1})
-    float *ring = reinterpret_cast<float *>(ring4);
-    const int shot = blockIdx.y;
+    constexpr int Q = 2 * M + 1, W4 = M / 4, R = M + 2, TW = kTile2 - 2 * M;
+    __shared__ float4 ring4[R][kThreads2];
+    const int shot = blockIdx.z / p.nzchunks, zc = blockIdx.z - shot * p.nzchunks;
     const int nz = p.g.nz, nx = p.g.nx, px = p.g.px;
-    const int z0 = blockIdx.x * p.zchunk, z1 = min(nz, z0 + p.zchunk);
-    const int x0 = threadIdx.x * 4;
-    const bool xin = x0 < nx, xpad = x0 < px;
+    const int z0 = zc * p.zchunk, z1 = min(nz, z0 + p.zchunk);
+    const int X0 = blockIdx.x * TW;
+    const int t4 = threadIdx.x;
+    const int x0 = X0 - M + 4 * t4;                       // this thread's 4 columns
+    const bool xg = x0 >= 0 && x0 < nx;                   // inside the grid
+    const bool own = t4 >= W4 && t4 < kThreads2 - W4 && x0 < nx;   // u^{n+2} columns
     const int64_t plane = p.g.plane;
     const int64_t sb = (int64_t)shot * p.g.field;
     const float *__restrict__ cur = p.cur + sb;
@@ -261,10 +259,10 @@ __global__ void __launch_bounds__(tb_max_threads<M>()) k_step2d_tb2(const StepPa
 
     float sx[4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) sx[e] = (x0 + e < nx) ? p.sig_x[x0 + e] : 0.0f;
+    for (int e = 0; e < 4; ++e) sx[e] = (x0 + e >= 0 && x0 + e < nx) ? p.sig_x[x0 + e] : 0.0f;
     int src_z = -1, src_e = 0;
     float srcv1 = 0.0f, srcv2 = 0.0f;
-    if (p.src_off) {
+    if (p.src_off && xg) {
         const int64_t so = p.src_off[shot];
         const int sz = (int)(so / plane), sxx = (int)(so - (int64_t)sz * plane);
         if (sxx >= x0 && sxx < x0 + 4) {
@@ -285,52 +283,70 @@ __global__ void __launch_bounds__(tb_max_threads<M>()) k_step2d_tb2(const StepPa
         q0[i] = ld4(cur, (int64_t)z * plane, x0, px, z >= 0 && z < nz);
     }
 
-    for (int t = z0 - M; t < z1 + M; ++t) {
+    // global operands of iteration t: the u^n row entering q0, level 1's x-window groups,
+    // prev and W of row t, and W of row t - M (level 2)
+    struct In {
+        float4 qn, win[2 * W4], pv, Wv, W2;
+    };
+    auto load = [&](int t, In &in) {
         const int zn = t + M;
-        q0[Q - 1] = ld4(cur, (int64_t)zn * plane, x0, px, zn >= 0 && zn < nz);
-        // u^{n+1} at row t (zero outside the grid)
+        in.qn = ld4(cur, (int64_t)zn * plane, x0, px, zn >= 0 && zn < nz);
+        const bool l1 = t >= 0 && t < nz && xg;
+        const int64_t row = (int64_t)t * plane;
+#pragma unroll
+        for (int j = 0; j < 2 * W4; ++j) {
+            const int g4 = j < W4 ? j : j + 1;
+            in.win[j] = l1 ? ld4(cur, row, x0 + 4 * (g4 - W4), px, true) : zero4;
+        }
+        in.pv = l1 ? __ldg((const float4 *)(prev + row + x0)) : zero4;
+        in.Wv = l1 ? __ldg((const float4 *)(p.W + row + x0)) : zero4;
+        const int zb = t - M;
+        in.W2 = (zb >= z0 && zb < z1 && own) ? __ldg((const float4 *)(p.W + (int64_t)zb * plane + x0))
+                                             : zero4;
+    };
+    In nxt;
+    if (PF) load(z0 - M, nxt);
+    for (int t = z0 - M; t < z1 + M; ++t) {
+        In in;
+        if (PF) {
+            in = nxt;
+            if (t + 1 < z1 + M) load(t + 1, nxt);
+        } else {
+            load(t, in);
+        }
+        q0[Q - 1] = in.qn;
         float4 v1 = zero4;
-        if (t >= 0 && t < nz) {
+        if (t >= 0 && t < nz && xg) {
             const int64_t row = (int64_t)t * plane;
             float w[4 + 2 * M];
 #pragma unroll
             for (int g4 = 0; g4 < 2 * W4 + 1; ++g4) {
-                const float4 v = (g4 == W4) ? q0[M] : ld4(cur, row, x0 + 4 * (g4 - W4), px, true);
+                const float4 v = (g4 == W4) ? q0[M] : in.win[g4 < W4 ? g4 : g4 - 1];
                 w[4 * g4] = v.x, w[4 * g4 + 1] = v.y, w[4 * g4 + 2] = v.z, w[4 * g4 + 3] = v.w;
             }
             float2 l0, l1;
             lap4<M>(w, q0, p.c, l0, l1);
-            if (xin) {
-                const float4 pv = __ldg((const float4 *)(prev + row + x0));
-                const float4 Wv = __ldg((const float4 *)(p.W + row + x0));
-                v1 = update4(q0[M], l0, l1, pv, Wv, sx, p.sig_z[t], t == src_z ? src_e : -1,
-                             srcv1);
-                if (t >= z0 && t < z1) *(float4 *)(o1 + row + x0) = v1;
-            }
+            v1 = update4(q0[M], l0, l1, in.pv, in.Wv, sx, p.sig_z[t], t == src_z ? src_e : -1,
+                         srcv1);
+            if (own && t >= z0 && t < z1) *(float4 *)(o1 + row + x0) = v1;
         }
         q1[Q - 1] = v1;
-        if (xpad) *(float4 *)(ring + (t + R) % R * px + x0) = v1;
+        ring4[(t + R) % R][t4] = v1;
         __syncthreads();
-        // u^{n+2} at row zb = t - M
         const int zb = t - M;
-        if (zb >= z0 && zb < z1) {
-            const float *rrow = ring + (zb + R) % R * px;
+        if (zb >= z0 && zb < z1 && own) {
+            const float4 *rrow = ring4[(zb + R) % R];
             float w[4 + 2 * M];
 #pragma unroll
             for (int g4 = 0; g4 < 2 * W4 + 1; ++g4) {
-                const int xc = x0 + 4 * (g4 - W4);
-                const float4 v = (g4 == W4) ? q1[M]
-                                 : (xc >= 0 && xc < px) ? *(const float4 *)(rrow + xc) : zero4;
+                const float4 v = (g4 == W4) ? q1[M] : rrow[t4 + g4 - W4];
                 w[4 * g4] = v.x, w[4 * g4 + 1] = v.y, w[4 * g4 + 2] = v.z, w[4 * g4 + 3] = v.w;
             }
             float2 l0, l1;
             lap4<M>(w, q1, p.c, l0, l1);
-            if (xin) {
-                const int64_t row = (int64_t)zb * plane;
-                const float4 Wv = __ldg((const float4 *)(p.W + row + x0));
-                *(float4 *)(o2 + row + x0) = update4(q1[M], l0, l1, q0[0], Wv, sx, p.sig_z[zb],
-                                                     zb == src_z ? src_e : -1, srcv2);
-            }
+            const int64_t row = (int64_t)zb * plane;
+            *(float4 *)(o2 + row + x0) = update4(q1[M], l0, l1, q0[0], in.W2, sx, p.sig_z[zb],
+                                                 zb == src_z ? src_e : -1, srcv2);
         }
 #pragma unroll
         for (int i = 0; i < Q - 1; ++i) {
@@ -340,20 +356,47 @@ __global__ void __launch_bounds__(tb_max_threads<M>()) k_step2d_tb2(const StepPa
     }
 }
 
-template <int M>
-cudaError_t launch_tb2(const StepParams &p0, int nshots, float *out1, float *out2, int nch,
-                       cudaStream_t s)
+template <int M, bool PF>
+cudaError_t launch_tb2x(const StepParams &p0, int nshots, float *out1, float *out2,
+                        cudaStream_t s)
 {
     StepParams p = p0;
+    constexpr int TW = kTile2 - 2 * M;
+    const int bx = (p.g.nx + TW - 1) / TW;
+    const int64_t ctas = (int64_t)bx * nshots;
+    static const int resident = [] {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step2d_tb2x<M, PF>, kThreads2, 0) !=
+                cudaSuccess ||
+            per < 1) {
+            cudaGetLastError();
+            per = 1;
+        }
+        return (sms > 0 ? sms : 152) * per;
+    }();
+    // z-chunks of at least 8M rows that best fill whole waves; each chunk streams 2M rows
+    // of u^{n+1} it does not keep and 2M warm-up rows
+    const int maxch = p.g.nz / (8 * M) > 0 ? p.g.nz / (8 * M) : 1;
+    int nch = 1;
+    double best = -1.0;
+    for (int c = 1; c <= maxch && c <= 64; ++c) {
+        const int zc = (p.g.nz + c - 1) / c;
+        const int64_t cn = (p.g.nz + zc - 1) / zc;
+        const int64_t tot = ctas * cn;
+        const int64_t waves = (tot + resident - 1) / resident;
+        const double fill = (double)tot / ((double)waves * resident);
+        const double score = fill / (1.0 + (2.0 * M) / zc);
+        if (score > best + 1e-9) {
+            best = score;
+            nch = (int)cn;
+        }
+    }
     p.zchunk = (p.g.nz + nch - 1) / nch;
     p.nzchunks = (p.g.nz + p.zchunk - 1) / p.zchunk;
-    const int threads = ((p.g.px / 4 + 31) / 32) * 32;
-    const int smem = (M + 2) * p.g.px * (int)sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute((const void *)k_step2d_tb2<M>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid(p.nzchunks, nshots);
-    k_step2d_tb2<M><<<grid, threads, smem, s>>>(p, out1, out2);
+    dim3 grid(bx, 1, p.nzchunks * nshots);
+    k_step2d_tb2x<M, PF><<<grid, kThreads2, 0, s>>>(p, out1, out2);
     return cudaGetLastError();
 }
 
@@ -407,21 +450,23 @@ cudaError_t launch2(const StepParams &p0, int nshots, cudaStream_t s)
 
 int step2d_tb2_chunks(const Geom &g, int nshots)
 {
-    const int maxt = g.M == 4 ? tb_max_threads<4>() : tb_max_threads<8>();
-    if (g.ndim != 2 || g.px > 4 * maxt) return 0;
-    // z-chunks of at least 8M rows (the 2M overlap rows cost at most a quarter) and
-    // enough of them for two CTAs on each of the 152 SMs
+    // worth it only when the batch fills the GPU: z-chunks of at least 8M rows, x-strips
+    // of 256 - 2M columns, and at least one CTA per SM
+    if (g.ndim != 2) return 0;
     const int maxch = g.nz / (8 * g.M);
-    const int want = (2 * 152 + nshots - 1) / nshots;
-    if (maxch < 1 || (int64_t)maxch * nshots < 152) return 0;
-    return want < maxch ? want : maxch;
+    const int64_t strips = (g.nx + kTile2 - 2 * g.M - 1) / (kTile2 - 2 * g.M);
+    if (maxch < 1 || (int64_t)maxch * strips * nshots < 152) return 0;
+    return maxch;
 }
 
 cudaError_t launch_step2d_tb2(const StepParams &p, int nshots, float *out1, float *out2,
                               int nchunks, cudaStream_t s)
 {
-    if (p.g.M == 4) return launch_tb2<4>(p, nshots, out1, out2, nchunks, s);
-    if (p.g.M == 8) return launch_tb2<8>(p, nshots, out1, out2, nchunks, s);
+    (void)nchunks;
+    // PF (the next row's loads in flight, as in the single step) measured slower here:
+    // 283 against 292 Gpts/s on the 64-shot batch
+    if (p.g.M == 4) return launch_tb2x<4, false>(p, nshots, out1, out2, s);
+    if (p.g.M == 8) return launch_tb2x<8, false>(p, nshots, out1, out2, s);
     return cudaErrorInvalidValue;
 }
 
