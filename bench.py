@@ -209,6 +209,26 @@ def cpu_baseline(w, sample_n=320, sample_nt=30):
     return pts * sample_nt / t / 1e9, t, desc, threads
 
 
+def cpu_baseline_one_core(args, sample_n=160, sample_nt=10):
+    """The oracle on one host core (OMP_NUM_THREADS=1, in a child process so the
+    OpenMP runtime of this one is untouched), on a smaller crop.  Returns a dict or
+    None."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "w = bench.workload(%r, %d, %d); "
+            "g, t, desc, thr = bench.cpu_baseline(w, %d, %d); "
+            "print(json.dumps({'value': g, 'seconds': t, 'sample': desc, 'cores': thr}))"
+            % (ROOT, args.workload, args.nt, args.n, sample_n, sample_nt))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True,
+                             text=True, timeout=300, check=True).stdout
+        d = json.loads(out.strip().splitlines()[-1])
+        return {"value": d["value"], "unit": "Gpts/s", "cores": d["cores"],
+                "sample": d["sample"], "seconds": round(d["seconds"], 2)}
+    except Exception:
+        return None
+
+
 def serving_section(dev, n_req, seed=4):
     """Serving workload (Poisson stream of forward/gradient requests, 75 % 2-D / 25 % 3-D,
     sides 128..1024 / 64..192, nt 500..3000): closed-loop capacity with continuous batching
@@ -482,7 +502,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         g, tsec, desc, threads = cpu_baseline(w)
         cpu = {"value": g, "unit": "Gpts/s", "cores": threads, "kind": "oracle",
-               "sample": desc, "seconds": round(tsec, 2)}
+               "sample": desc, "seconds": round(tsec, 2),
+               "one_core": cpu_baseline_one_core(args)}
 
     # the other two workloads of the metric, measured after the timed region
     model.close()
