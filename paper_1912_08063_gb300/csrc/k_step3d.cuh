@@ -105,6 +105,24 @@ __device__ __forceinline__ void tma_load4(void *dst, const CUtensorMap *map, int
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 
+// Approximate reciprocal (PTX rcp.approx), the operation behind the fast division it
+// replaces; the damping factor 1 + s lies in [1, 2).
+__device__ __forceinline__ float rcp_fast(float d)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+    return r;
+}
+
+// max(|a|, |b|) with NaN propagated, as one PTX max; the sign of the result is not
+// meaningful (the caller clears it).
+__device__ __forceinline__ float absmax_nan(float a, float b)
+{
+    float r;
+    asm("max.NaN.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+
 // Source-point term of the transposed imaging sum at point e of a 4-point group:
 // g[e] -= srcv c[e] / W[e]  (srcv = dt^2 w[m]).
 __device__ __forceinline__ void src_image(float2 &g0, float2 &g1, float4 c, float4 W, int e,
@@ -157,12 +175,12 @@ struct Ctx {
     int tid, tx, ty, za, nout, niter, shot, bx, by, x0, y0, hx, hy;
     int hbase, pbase;         // halo / pointwise loads of the CTA's earlier segments
     int h_issued, p_issued;   // loads issued so far, counted like hbase (thread 0's view)
-    float sxp[4], syr[C::RY];
+    float sx1[4], syr[C::RY];  // 1 + sig_x of this thread's columns, sig_y of its rows
     bool xin, sxnz;            // sxnz: some sig_x of this thread's columns is nonzero
     int64_t sb;
     int src_j, src_r, src_e;   // source node in this thread's block (src_j < 0: none)
     float srcv;
-    unsigned mxa, mxd;         // bits of max|out| and max|out - c| (p->maxbits set)
+    float mxa, mxd;            // max|out| and max|out - c| up to sign (p->maxbits set)
     float4 q[C::L][C::RY];
 
     __device__ __forceinline__ void issue_halo(int it)
@@ -214,11 +232,12 @@ struct Ctx {
             }
         }
         const int kh = hbase + it;   // this CTA's halo load count
-        if (!mbar_wait(bar_h + kh % SH, (kh / SH) & 1)) {
+        const int st = kh % SH;
+        if (!mbar_wait(bar_h + st, (kh / SH) & 1)) {
             atomicExch(abort_flag, 1);
             return true;
         }
-        const float *hk = (const float *)(halo + (kh % SH) * C::HALO_STRIDE);
+        const float *hk = (const float *)(halo + st * C::HALO_STRIDE);
 #pragma unroll
         for (int r = 0; r < RY; ++r)
             q[R][r] = *(const float4 *)(hk + (ty * RY + r + M) * SX + tx * 4 + M);
@@ -226,12 +245,15 @@ struct Ctx {
 
         const int o = it - 2 * M, j = za + o;
         const int ko = pbase + o;
-        if (!mbar_wait(bar_p + ko % SP, (ko / SP) & 1)) {
+        const int sp = ko % SP;
+        if (!mbar_wait(bar_p + sp, (ko / SP) & 1)) {
             atomicExch(abort_flag, 1);
             return true;
         }
-        const float *hj = (const float *)(halo + ((kh - M) % SH) * C::HALO_STRIDE);
-        const float *ta = (const float *)(pw + (ko % SP) * C::PW_STRIDE);
+        // the output plane's halo arrived M loads earlier
+        const int sj = st >= M ? st - M : st + SH - M;
+        const float *hj = (const float *)(halo + sj * C::HALO_STRIDE);
+        const float *ta = (const float *)(pw + sp * C::PW_STRIDE);
         const float *tb = ta + TX * C::TY;
         const float sz = p->sig_z[j];
 
@@ -340,37 +362,38 @@ struct Ctx {
             const int64_t base = (int64_t)j * p->plane + (int64_t)y * p->px + x0;
             const bool store = xin && y < p->ny;
             const bool at_src = j == src_j && r == src_r;
-            // out = (2c + W lap - (1 - s) prev [+ dt^2 w at the source]) / (1 + s)
-            const float2 two = make_float2(2.0f, 2.0f);
-            const float2 r0 = __ffma2_rn(lo2(B), l0, __fmul2_rn(two, lo2(cz4)));
-            const float2 r1 = __ffma2_rn(hi2(B), l1, __fmul2_rn(two, hi2(cz4)));
-            float rhs[4] = {r0.x, r0.y, r1.x, r1.y};
-            const float pv[4] = {A.x, A.y, A.z, A.w};
-            const bool inj = MODE != kModeAdj && at_src;
-            if (!(C::F & kInterior) || sxnz || syr[r] != 0.0f || sz != 0.0f) {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float s = sxp[e] + syr[r] + sz;
-                    float v = fmaf(s - 1.0f, pv[e], rhs[e]);
-                    if (inj && e == src_e) v += srcv;
-                    rhs[e] = __fdividef(v, 1.0f + s);
-                }
-            } else {
-                // s = 0: (2c + W lap - prev) / 1
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    float v = rhs[e] - pv[e];
-                    if (inj && e == src_e) v += srcv;
-                    rhs[e] = v;
-                }
+            // (2c + W lap - (1 - s) prev [+ dt^2 w at the source]) / (1 + s), evaluated as
+            // prev + (2 (c - prev) + W lap [+ dt^2 w]) / (1 + s): the division scales only
+            // the increment, and 1 + s = (1 + sig_x) + (sig_y + sig_z) pairs up
+            const float2 m1 = make_float2(-1.0f, -1.0f), two = make_float2(2.0f, 2.0f);
+            const float2 dc0 = __ffma2_rn(lo2(A), m1, lo2(cz4));   // c - prev, exact form
+            const float2 dc1 = __ffma2_rn(hi2(A), m1, hi2(cz4));
+            float2 t0 = __ffma2_rn(lo2(B), l0, __fmul2_rn(two, dc0));
+            float2 t1 = __ffma2_rn(hi2(B), l1, __fmul2_rn(two, dc1));
+            if (MODE != kModeAdj && at_src) {
+                if (src_e == 0) t0.x += srcv;
+                else if (src_e == 1) t0.y += srcv;
+                else if (src_e == 2) t1.x += srcv;
+                else t1.y += srcv;
             }
+            float2 o0, o1;
+            if (!(C::F & kInterior) || sxnz || syr[r] != 0.0f || sz != 0.0f) {
+                const float syz = syr[r] + sz;
+                const float2 d0 = __fadd2_rn(make_float2(sx1[0], sx1[1]), make_float2(syz, syz));
+                const float2 d1 = __fadd2_rn(make_float2(sx1[2], sx1[3]), make_float2(syz, syz));
+                o0 = __ffma2_rn(t0, make_float2(rcp_fast(d0.x), rcp_fast(d0.y)), lo2(A));
+                o1 = __ffma2_rn(t1, make_float2(rcp_fast(d1.x), rcp_fast(d1.y)), hi2(A));
+            } else {
+                o0 = __fadd2_rn(t0, lo2(A));   // s = 0
+                o1 = __fadd2_rn(t1, hi2(A));
+            }
+            const float rhs[4] = {o0.x, o0.y, o1.x, o1.y};
             if (MODE != kModeAdj && p->maxbits) {
-                // |x| as bits: unsigned order is magnitude order, NaN above infinity
                 const float cz[4] = {cz4.x, cz4.y, cz4.z, cz4.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    mxa = max(mxa, __float_as_uint(rhs[e]) & 0x7fffffffu);
-                    mxd = max(mxd, __float_as_uint(rhs[e] - cz[e]) & 0x7fffffffu);
+                    mxa = absmax_nan(mxa, rhs[e]);
+                    mxd = absmax_nan(mxd, rhs[e] - cz[e]);
                 }
             }
             if (store) *(float4 *)(p->out + sb + base) = make_float4(rhs[0], rhs[1], rhs[2], rhs[3]);
@@ -386,8 +409,7 @@ struct Ctx {
                     *(uint2 *)cc = pack_code4(cz4, p->st_dtype, sts[0]);
                     if (p->st_comps == 2)
                         *(uint2 *)(cc + p->field) =
-                            pack_code4(make_float4(cz4.x - A.x, cz4.y - A.y, cz4.z - A.z, cz4.w - A.w),
-                                       p->st_dtype, sts[1]);
+                            pack_code4(make_float4(dc0.x, dc0.y, dc1.x, dc1.y), p->st_dtype, sts[1]);
                 }
             }
             if (MODE == kModeAdj) {
@@ -439,8 +461,8 @@ __device__ __forceinline__ void run_segment(Ctx<C, MODE> &c, int col, int z0, in
     c.hx = c.bx * C::TX - M;
     c.hy = c.by * C::TY - M;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) c.sxp[e] = (c.x0 + e < p.nx) ? p.sig_x[c.x0 + e] : 0.0f;
-    c.sxnz = c.sxp[0] != 0.0f || c.sxp[1] != 0.0f || c.sxp[2] != 0.0f || c.sxp[3] != 0.0f;
+    for (int e = 0; e < 4; ++e) c.sx1[e] = 1.0f + ((c.x0 + e < p.nx) ? p.sig_x[c.x0 + e] : 0.0f);
+    c.sxnz = c.sx1[0] != 1.0f || c.sx1[1] != 1.0f || c.sx1[2] != 1.0f || c.sx1[3] != 1.0f;
 #pragma unroll
     for (int r = 0; r < RY; ++r) c.syr[r] = (c.y0 + r < p.ny) ? p.sig_y[c.y0 + r] : 0.0f;
     c.xin = c.x0 < p.nx;
@@ -487,13 +509,14 @@ __device__ __forceinline__ void run_segment(Ctx<C, MODE> &c, int col, int z0, in
     }
     if (MODE != kModeAdj && p.maxbits) {
         // the codec's maxima of this segment's shot (every thread gets here)
-        const unsigned a = __reduce_max_sync(0xffffffffu, c.mxa);
-        const unsigned d = __reduce_max_sync(0xffffffffu, c.mxd);
+        // magnitudes as bits: unsigned order is magnitude order, NaN above infinity
+        const unsigned a = __reduce_max_sync(0xffffffffu, __float_as_uint(c.mxa) & 0x7fffffffu);
+        const unsigned d = __reduce_max_sync(0xffffffffu, __float_as_uint(c.mxd) & 0x7fffffffu);
         if ((c.tid & 31) == 0) {
             if (a) atomicMax(p.maxbits + 2 * c.shot, a);
             if (d) atomicMax(p.maxbits + 2 * c.shot + 1, d);
         }
-        c.mxa = c.mxd = 0u;
+        c.mxa = c.mxd = 0.0f;
     }
     c.hbase += c.niter;
     c.pbase += c.nout;
@@ -532,7 +555,7 @@ k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUt
     c.ty = c.tid / C::NTX;
     c.hbase = c.pbase = 0;
     c.h_issued = c.p_issued = 0;
-    c.mxa = c.mxd = 0u;
+    c.mxa = c.mxd = 0.0f;
 
     if (c.tid == 0) {
         for (int i = 0; i < C::SH; ++i) mbar_init(c.bar_h + i, 1);

@@ -9,6 +9,11 @@ Step3dKernelInfo step3d_kernel_m8(const Step3dVariant &v, int mode)
         if (v.u == 3) return s3d::kernel_info<8, 32, 2, 2, 3, 0>(mode);
         if (v.u == 1) return s3d::kernel_info<8, 32, 2, 2, 1, 0>(mode);
     }
+    if (v.ty == 32 && v.ry == 1 && v.pf == 2 && v.opt == 0) {
+        if (v.u == 2) return s3d::kernel_info<8, 32, 1, 2, 2, 0>(mode);
+        if (v.u == 3) return s3d::kernel_info<8, 32, 1, 2, 3, 0>(mode);
+        if (v.u == 4) return s3d::kernel_info<8, 32, 1, 2, 4, 0>(mode);
+    }
     return Step3dKernelInfo{nullptr, 0, 0};
 }
 
