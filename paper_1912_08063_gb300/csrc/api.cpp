@@ -278,7 +278,8 @@ int set_velocity(fwi_model *m, const float *vp, cudaStream_t s)
     // the kernels read s = eta dt / 2 per axis
     const int nb = m->nb;
     const int ext[3] = {m->g.nz, m->g.ny, m->g.nx};
-    std::vector<float> sig(ext[0] + ext[1] + ext[2], 0.0f);
+    // 4 floats of padding: the 3-D step copies sig_z in 16-byte aligned groups of four
+    std::vector<float> sig(ext[0] + ext[1] + ext[2] + 4, 0.0f);
     size_t base = 0;
     for (int a = 0; a < 3; ++a) {
         const bool present = !(a == 1 && m->ndim == 2);

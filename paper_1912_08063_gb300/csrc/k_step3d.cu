@@ -9,17 +9,22 @@
 
 namespace fwi {
 
-// Configuration per radius; FWI_STEP3D_VARIANT=<ty>,<ry>,<pf>,<u>,<opt> overrides it for
-// tuning runs (only the instantiated combinations are accepted).
+// Configuration per radius; FWI_STEP3D_VARIANT=<ty>,<ry>,<pf>,<u>,<opt>[,<opt_rev>]
+// overrides it for tuning runs (only the instantiated combinations are accepted).  At
+// radius 8 the store and reverse modes take the packed x-sums (their epilogues are the
+// heavier ones) and the plain forward step the scalar ones, as measured fastest.
 Step3dVariant step3d_variant(int M)
 {
-    Step3dVariant v = M == 8 ? Step3dVariant{32, 2, 2, 3, 0} : Step3dVariant{16, 2, 3, 2, 0};
+    Step3dVariant v = M == 8 ? Step3dVariant{32, 2, 2, 3, 0, 1} : Step3dVariant{16, 2, 3, 2, 0, 0};
     if (const char *e = std::getenv("FWI_STEP3D_VARIANT")) {
-        int ty, ry, pf, un, opt;
-        if (std::sscanf(e, "%d,%d,%d,%d,%d", &ty, &ry, &pf, &un, &opt) == 5) {
-            Step3dVariant w{ty, ry, pf, un, opt};
-            const Step3dKernelInfo k = M == 8 ? step3d_kernel_m8(w, 0) : step3d_kernel_m4(w, 0);
-            if (k.fn) v = w;
+        int ty, ry, pf, un, opt, optr;
+        const int n = std::sscanf(e, "%d,%d,%d,%d,%d,%d", &ty, &ry, &pf, &un, &opt, &optr);
+        if (n == 5 || n == 6) {
+            Step3dVariant w{ty, ry, pf, un, opt, n == 6 ? optr : opt};
+            bool ok = true;
+            for (int mode = 0; mode < 3; ++mode)
+                ok = ok && (M == 8 ? step3d_kernel_m8(w, mode) : step3d_kernel_m4(w, mode)).fn;
+            if (ok) v = w;
         }
     }
     return v;

@@ -139,7 +139,8 @@ __device__ __forceinline__ void src_image(float2 &g0, float2 &g1, float4 c, floa
 
 // Options of the plane loop (bits of Cfg::F):
 //   kPackX     x-sums as packed FP32x2 on register pairs that are 64-bit aligned (even
-//              offsets pair points (0,1) and (2,3), odd offsets pair (1,2))
+//              offsets pair points (0,1) and (2,3) and add into the y accumulators, odd
+//              offsets pair (1,2))
 //   kInterior  rows with no damping (s = 0 at all four points) skip the sponge division
 constexpr int kPackX = 1, kInterior = 2;
 
@@ -172,6 +173,7 @@ struct Ctx {
     int *abort_flag;
     const float *ainv;         // shared: 1 / scale of a 16-bit aux (kModeAdj)
     const float *sts;          // shared: the segment shot's checkpoint scales (st_code)
+    float *szs;                // shared: per pointwise stage, sig_z[j & ~3 .. (j & ~3) + 3]
     int tid, tx, ty, za, nout, niter, shot, bx, by, x0, y0, hx, hy;
     int hbase, pbase;         // halo / pointwise loads of the CTA's earlier segments
     int h_issued, p_issued;   // loads issued so far, counted like hbase (thread 0's view)
@@ -196,8 +198,14 @@ struct Ctx {
         const int st = (pbase + o) % C::SP;
         uint64_t *b = bar_p + st;
         unsigned char *d = pw + st * C::PW_STRIDE;
-        mbar_expect_tx(b, C::NPW == 4 && p->aux_fmt != 0 ? 3 * C::TILE_BYTES + C::TILE_BYTES / 2
-                                                          : C::NPW * C::TILE_BYTES);
+        mbar_expect_tx(b, (C::NPW == 4 && p->aux_fmt != 0 ? 3 * C::TILE_BYTES + C::TILE_BYTES / 2
+                                                           : C::NPW * C::TILE_BYTES) + 16);
+        // the plane's sponge coefficient rides with its pointwise tiles (16-byte copy of
+        // the aligned group of four that holds it; the table is padded past nz)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 16, [%2];"
+            ::"r"(smem_u32(szs + 4 * st)), "l"(p->sig_z + ((za + o) & ~3)), "r"(smem_u32(b))
+            : "memory");
         tma_load4(d, ma, bx * C::TX, by * C::TY, za + o, shot, b);
         tma_load4(d + C::TILE_BYTES, mb, bx * C::TX, by * C::TY, za + o, 0, b);
         if (C::NPW == 4) {
@@ -255,7 +263,7 @@ struct Ctx {
         const float *hj = (const float *)(halo + sj * C::HALO_STRIDE);
         const float *ta = (const float *)(pw + sp * C::PW_STRIDE);
         const float *tb = ta + TX * C::TY;
-        const float sz = p->sig_z[j];
+        const float sz = szs[4 * sp + (j & 3)];
 
         // y: rows ty*RY .. ty*RY + 2M + RY - 1 of the halo tile, two accumulators per half
         float2 ya[RY][2], yb[RY][2];
@@ -297,19 +305,22 @@ struct Ctx {
             }
             float lx[4];
             if (C::F & kPackX) {
-                // offsets k even: pairs (0,1), (2,3) start at even w indices; k odd: the
-                // pair (1,2) does, points 0 and 3 stay scalar
-                float2 xa = make_float2(0.f, 0.f), xb = xa, xm = xa;
+                // offsets k even: the pairs (0,1), (2,3) start at even w indices and add
+                // into the y accumulators; k odd: the pair (1,2) does, points 0 and 3 stay
+                // scalar
+                float2 xm = make_float2(0.f, 0.f);
                 float x0 = 0.0f, x3 = 0.0f;
 #pragma unroll
                 for (int k = 1; k <= M; ++k) {
                     const float ck = p->cx[k];
                     const float2 ck2 = make_float2(ck, ck);
                     if ((k & 1) == 0) {
-                        xa = __ffma2_rn(ck2, __fadd2_rn(make_float2(w[M + k], w[M + k + 1]),
-                                                        make_float2(w[M - k], w[M - k + 1])), xa);
-                        xb = __ffma2_rn(ck2, __fadd2_rn(make_float2(w[M + 2 + k], w[M + 3 + k]),
-                                                        make_float2(w[M + 2 - k], w[M + 3 - k])), xb);
+                        ya[r][0] = __ffma2_rn(ck2, __fadd2_rn(make_float2(w[M + k], w[M + k + 1]),
+                                                              make_float2(w[M - k], w[M - k + 1])),
+                                              ya[r][0]);
+                        ya[r][1] = __ffma2_rn(ck2, __fadd2_rn(make_float2(w[M + 2 + k], w[M + 3 + k]),
+                                                              make_float2(w[M + 2 - k], w[M + 3 - k])),
+                                              ya[r][1]);
                     } else {
                         xm = __ffma2_rn(ck2, __fadd2_rn(make_float2(w[M + 1 + k], w[M + 2 + k]),
                                                         make_float2(w[M + 1 - k], w[M + 2 - k])), xm);
@@ -317,10 +328,10 @@ struct Ctx {
                         x3 = fmaf(ck, w[M + 3 + k] + w[M + 3 - k], x3);
                     }
                 }
-                lx[0] = xa.x + x0;
-                lx[1] = xa.y + xm.x;
-                lx[2] = xb.x + xm.y;
-                lx[3] = xb.y + x3;
+                lx[0] = x0;
+                lx[1] = xm.x;
+                lx[2] = xm.y;
+                lx[3] = x3;
             } else {
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
@@ -550,6 +561,7 @@ k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUt
     c.abort_flag = (int *)(c.bar_p + C::SP);
     c.ainv = (const float *)(c.abort_flag + 1);
     c.sts = c.ainv + 1;
+    c.szs = (float *)((unsigned char *)c.bar_h + 512);
     c.tid = threadIdx.x;
     c.tx = c.tid % C::NTX;
     c.ty = c.tid / C::NTX;

@@ -51,8 +51,10 @@ struct Step3dParams {
 // prefetch depth, planes between shifts of the register z-queue, and option bits
 // (1: packed x-sums, 2: undamped fast path).  step3d_variant() picks the configuration
 // used for radius M.
+// Tile height, rows per thread, prefetch depth, queue shift interval, and the option bits
+// (Cfg::F) of the plain forward step (opt) and of the store and reverse modes (opt_rev).
 struct Step3dVariant {
-    int ty, ry, pf, u, opt;
+    int ty, ry, pf, u, opt, opt_rev;
 };
 Step3dVariant step3d_variant(int M);
 int step3d_smem_bytes(int M);
