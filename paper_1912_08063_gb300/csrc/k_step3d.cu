@@ -11,11 +11,11 @@ namespace fwi {
 
 // Configuration per radius; FWI_STEP3D_VARIANT=<ty>,<ry>,<pf>,<u>,<opt>[,<opt_rev>]
 // overrides it for tuning runs (only the instantiated combinations are accepted).  At
-// radius 8 the store and reverse modes take the packed x-sums (their epilogues are the
-// heavier ones) and the plain forward step the scalar ones, as measured fastest.
+// radius 8 the queue shifts every 2 planes and all modes take the packed x-sums, as
+// measured fastest on GB300 (against U = 3 and scalar x-sums).
 Step3dVariant step3d_variant(int M)
 {
-    Step3dVariant v = M == 8 ? Step3dVariant{32, 2, 2, 3, 0, 1} : Step3dVariant{16, 2, 3, 2, 0, 0};
+    Step3dVariant v = M == 8 ? Step3dVariant{32, 2, 2, 2, 1, 1} : Step3dVariant{16, 2, 3, 2, 0, 0};
     if (const char *e = std::getenv("FWI_STEP3D_VARIANT")) {
         int ty, ry, pf, un, opt, optr;
         const int n = std::sscanf(e, "%d,%d,%d,%d,%d,%d", &ty, &ry, &pf, &un, &opt, &optr);

@@ -7,9 +7,9 @@ Step3dKernelInfo step3d_kernel_m8(const Step3dVariant &v, int mode)
 {
     const int opt = mode == kModeStep ? v.opt : v.opt_rev;
     if (v.ty == 32 && v.ry == 2 && v.pf == 2) {
+        if (v.u == 2 && opt == 1) return s3d::kernel_info<8, 32, 2, 2, 2, 1>(mode);
+        if (v.u == 2 && opt == 0) return s3d::kernel_info<8, 32, 2, 2, 2, 0>(mode);
         if (v.u == 3 && opt == 0) return s3d::kernel_info<8, 32, 2, 2, 3, 0>(mode);
-        if (v.u == 3 && opt == 1) return s3d::kernel_info<8, 32, 2, 2, 3, 1>(mode);
-        if (v.u == 1 && opt == 0) return s3d::kernel_info<8, 32, 2, 2, 1, 0>(mode);
     }
     return Step3dKernelInfo{nullptr, 0, 0};
 }
