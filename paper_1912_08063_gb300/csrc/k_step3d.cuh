@@ -28,15 +28,19 @@
 //     queue of 2M + U planes that shifts by U every U planes (U - 1 spare slots halve or
 //     third the register moves), the x/y-neighbours from the resident halo stage of the
 //     output plane (it arrived M planes earlier and the ring keeps it);
-//   * y and z sums use packed FP32x2 FMAs and split accumulators (independent chains);
-//     the sponge division is a fast reciprocal, branch-free;
+//   * y and z sums use packed FP32x2 FMAs and split accumulators (independent chains),
+//     the x-sums too with option kPackX; the update is prev + increment / (1 + s) in
+//     packed form with a fast reciprocal, branch-free; the plane's s_z arrives with its
+//     pointwise tiles;
 //   * results are stored with 16-byte stores straight from registers.
 // Measured on GB300 (radius 8, 512^3): this layout beat a variant that unrolls the
 // plane loop so the queue rotates at compile time (larger code, slower), a variant that
 // reads the forward z-neighbours from the resident stages instead of registers (more
 // shared-memory loads, 15-20 % slower even with the freed registers spent on the options
-// below), and one thread per 4 x 1 points (more y loads, slower); U = 2 or 3 beat U = 1
-// by 7 %.
+// below), one thread per 4 x 1 points (16 warps, more y loads, 10 % slower), and
+// per-stage release barriers instead of the per-plane CTA barrier (warps drifting a
+// plane apart, 16 % slower); U = 2 with packed x-sums beats U = 3 by 1-4 % and U = 1 by
+// more than 7 %.
 // DRAM traffic per point and step: c once (halo re-reads hit L2), the pointwise fields
 // once, the writes once: 16 bytes (kModeStep) or 28 bytes (kModeAdj: + aux, g read and
 // written).
