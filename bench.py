@@ -308,20 +308,28 @@ def batched_section(dev, nt=3000):
     tb = time.perf_counter() - t0
     i1 = m.info()
     nf = i1["fwd_step_launches"] - i0["fwd_step_launches"]
+    nst = i1["store_step_launches"] - i0["store_step_launches"]
     na = i1["adj_step_launches"] - i0["adj_step_launches"]
     fms = (i1["fwd_step_ms"] - i0["fwd_step_ms"]) / max(nf, 1)
+    sms = (i1["store_step_ms"] - i0["store_step_ms"]) / max(nst, 1)
     ams = (i1["adj_step_ms"] - i0["adj_step_ms"]) / max(na, 1)
     # W is one field shared by all shots: per point and step the forward step moves
-    # 12 + 4 / shots bytes, the reverse step 22 + 4 / shots (u^m as a 2-byte code)
+    # 12 + 4 / shots bytes, with a checkpoint store 2 more (u^n alone as a 16-bit code),
+    # the reverse step 22 + 4 / shots (u^m as a 2-byte code)
     bf = 12.0 + 4.0 / w.nshots
+    bs = bf + 2.0
     ba = BYTES_ADJ - 4.0 + 4.0 / w.nshots
+    npts = i1["points"] * w.nshots
     kern = {"fwd_step_avg_ms": round(fms, 4), "fwd_step_launches": nf,
             "fwd_bytes_per_point": round(bf, 3),
-            "fwd_step_GB/s": round(bf * i1["points"] * w.nshots / (fms * 1e-3) / 1e9, 1),
+            "fwd_step_GB/s": round(bf * npts / (fms * 1e-3) / 1e9, 1),
+            "store_step_avg_ms": round(sms, 4), "store_step_launches": nst,
+            "store_bytes_per_point": round(bs, 3),
+            "store_step_GB/s": round(bs * npts / (sms * 1e-3) / 1e9, 1) if nst else None,
             "adj_step_avg_ms": round(ams, 4), "adj_step_launches": na,
             "adj_bytes_per_point": round(ba, 3),
-            "adj_step_GB/s": round(ba * i1["points"] * w.nshots / (ams * 1e-3) / 1e9, 1),
-            "kernel_seconds": round((nf * fms + na * ams) / 1e3, 3)}
+            "adj_step_GB/s": round(ba * npts / (ams * 1e-3) / 1e9, 1),
+            "kernel_seconds": round((nf * fms + nst * sms + na * ams) / 1e3, 3)}
     singles = [fwi.Acquisition(w.src[i:i + 1], w.rec) for i in range(w.nshots)]
     t0 = time.perf_counter()
     for i, a in enumerate(singles):

@@ -884,7 +884,7 @@ struct GradJob {
     size_t ia = 0;    // next schedule action
     int kdone = 0;    // forward steps already issued of the current ADVANCE action
     int aux_slot = -1;   // checkpoint the next reverse step reads u^m from in place
-    int st_slot = -1, st_comps = 0;   // store the next forward step writes (3-D)
+    int st_slot = -1, st_comps = 0;   // store the next forward step writes
     // CUDA graphs of kGradGraphSteps plain forward steps (no checkpoint store or max-abs
     // among them), keyed by the buffer parity at their start and whether they record
     // traces, replayed with the device step counter m->step_ctr (dev_n: its value as the
@@ -1128,7 +1128,7 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
         } else if (kind == 2) {   // STORE the pair (u^step, u^{step-1}), or u^step alone
             const bool have_max = j.fused_max && ia > 0 && m->sched[2 * (ia - 1)] == 1;
             const bool next_adv = ia + 1 < nact && m->sched[2 * (ia + 1)] == 1;
-            if (have_max && next_adv && use_step3d(m)) {
+            if (have_max && next_adv) {
                 // the next forward step reads exactly this pair: it writes the checkpoint
                 // from its epilogue with the scales derived here
                 FWI_LAUNCH(m, launch_snap_scales(m->maxbits.as<unsigned>(), ns,

@@ -91,8 +91,11 @@ struct RowIn {
 };
 
 // Every global load of row z is issued before its arithmetic; with PFR the loads of row
-// z + 1 are issued before row z's arithmetic (software pipelining).
-template <int M, bool IMG, bool PFR>
+// z + 1 are issued before row z's arithmetic (software pipelining).  STORE (forward only)
+// also writes the checkpoint of the input pair (c = u^n, prev = u^{n-1}) in the encode
+// kernel's format from the epilogue: the store the schedule asks for right before this
+// step, without the encode pass's second read of both fields.
+template <int M, bool IMG, bool PFR, bool STORE = false>
 __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
 {
     constexpr int Q = 2 * M + 1, W4 = M / 4;   // x-window: W4 groups of 4 either side
@@ -132,6 +135,11 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
         }
     }
     unsigned mxa = 0u, mxd = 0u;   // bits of max|out| and max|out - c| (p.maxbits set)
+    float sca = 1.0f, scd = 1.0f;   // STORE: the checkpoint's scales
+    if (STORE && p.st_dtype != 0) {
+        sca = p.st_scale[2 * shot];
+        scd = p.st_scale[2 * shot + 1];
+    }
 
     auto load_row = [&](int z, RowIn<M, IMG> &in) {
         const int zn = z + M;
@@ -183,6 +191,21 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
                                      (!IMG && z == src_z) ? src_e : -1, srcv);
             const float rhs[4] = {o.x, o.y, o.z, o.w};
             *(float4 *)(prev + row + x0) = o;
+            if (STORE) {
+                // FP32 pair unchanged, or 16-bit a = c s_a and d = (c - prev) s_d
+                const int64_t ci = (int64_t)shot * p.st_cstride + row + x0;
+                if (p.st_dtype == 0) {
+                    *(float4 *)((float *)p.st_code + ci) = c;
+                    if (p.st_comps == 2) *(float4 *)((float *)p.st_code + ci + p.g.field) = pv;
+                } else {
+                    unsigned short *cc = (unsigned short *)p.st_code + ci;
+                    *(uint2 *)cc = pack_code4(c, p.st_dtype, sca);
+                    if (p.st_comps == 2)
+                        *(uint2 *)(cc + p.g.field) = pack_code4(
+                            make_float4(c.x - pv.x, c.y - pv.y, c.z - pv.z, c.w - pv.w),
+                            p.st_dtype, scd);
+                }
+            }
             if (!IMG && p.maxbits) {
                 const float cc[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
@@ -400,18 +423,15 @@ cudaError_t launch_tb2x(const StepParams &p0, int nshots, float *out1, float *ou
     return cudaGetLastError();
 }
 
-template <int M, bool IMG>
-cudaError_t launch2(const StepParams &p0, int nshots, cudaStream_t s)
+// Resident CTAs of one instantiation on the device (registers limit it).
+template <int M, bool IMG, bool PFR, bool STORE>
+int resident2()
 {
-    StepParams p = p0;
-    const int bx = (p.g.nx + kTile2 - 1) / kTile2;
-    const int64_t ctas = (int64_t)bx * nshots;
-    // resident CTAs of this instantiation on the device (registers limit it)
     static const int resident = [] {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step2d_reg<M, IMG, !IMG>,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step2d_reg<M, IMG, PFR, STORE>,
                                                           kThreads2, 0) != cudaSuccess ||
             per < 1) {
             cudaGetLastError();
@@ -419,6 +439,23 @@ cudaError_t launch2(const StepParams &p0, int nshots, cudaStream_t s)
         }
         return (sms > 0 ? sms : 152) * per;
     }();
+    return resident;
+}
+
+template <int M, bool IMG>
+cudaError_t launch2(const StepParams &p0, int nshots, cudaStream_t s)
+{
+    StepParams p = p0;
+    const int bx = (p.g.nx + kTile2 - 1) / kTile2;
+    const int64_t ctas = (int64_t)bx * nshots;
+    bool store = false;
+    int resident;
+    if constexpr (IMG) {
+        resident = resident2<M, true, false, false>();
+    } else {
+        store = p.st_code != nullptr;
+        resident = store ? resident2<M, false, true, true>() : resident2<M, false, true, false>();
+    }
     // z-chunks (at least 4M rows each) that best fill whole waves of resident CTAs; each
     // chunk streams 2M warm-up rows that cost about a third of an output row
     const int maxch = p.g.nz / (4 * M) > 0 ? p.g.nz / (4 * M) : 1;
@@ -442,7 +479,9 @@ cudaError_t launch2(const StepParams &p0, int nshots, cudaStream_t s)
     // forward: row z + 1's loads in flight during row z; reverse (imaging): all of row z's
     // loads first (its pipelined form needs too many registers; measured on 64 shots of
     // 440 x 1064: forward 0.121 -> 0.106 ms, reverse 0.190 -> 0.250 ms)
-    k_step2d_reg<M, IMG, !IMG><<<grid, kThreads2, 0, s>>>(p);
+    if constexpr (IMG) k_step2d_reg<M, true, false, false><<<grid, kThreads2, 0, s>>>(p);
+    else if (store) k_step2d_reg<M, false, true, true><<<grid, kThreads2, 0, s>>>(p);
+    else k_step2d_reg<M, false, true, false><<<grid, kThreads2, 0, s>>>(p);
     return cudaGetLastError();
 }
 
