@@ -165,7 +165,8 @@ struct fwi_model {
     int geo_shots = -1, geo_nrec = -1;
     bool og_src = false, og_rec = false;   // current acquisition uses off-grid points
     // cached schedule
-    int sched_nslots = -1;
+    int sched_nslots = -1, sched_nt = -1;
+    int64_t snaps_layout = -1;   // code layout the pool was last zeroed for
     std::vector<int32_t> sched;
     std::vector<int> sched_comps;   // per action: checkpoint components moved (1 or 2)
     int64_t sched_fwd = 0;
@@ -871,6 +872,7 @@ struct GradJob {
     int ns = 0, nr = 0, nt = 0;
     int64_t nfield = 0;
     size_t fb = 0, per_slot = 0;
+    int64_t cstride = 0;   // code elements per shot in a slot (2 fields, or 1: u^n alone)
     const void *dobs = nullptr;
     StepParams pf{}, pa{};
     float *tr = nullptr, *res = nullptr;
@@ -959,6 +961,41 @@ int grad_capture(GradJob &j, int par, bool rec)
 
 // Checkpoint slots for the budget, the schedule and its per-action component counts,
 // staging of the inputs, and the initial state.
+
+// The binomial schedule for nt steps and `slots` checkpoints, and the components each of
+// its checkpoint actions moves (cached on the model per slot count).  A restore followed
+// by a reverse step needs u^m alone (the reverse step reads only u^m, straight from the
+// checkpoint; the following action is always another restore), and a checkpoint whose
+// every restore is of that kind is stored as u^n alone.
+void plan_schedule(fwi_model *m, int nt, int slots)
+{
+    if (slots == m->sched_nslots && m->sched_nt == nt) return;
+    m->sched = revolve_actions(nt, (int32_t)slots, &m->sched_fwd);
+    m->sched_nslots = slots;
+    m->sched_nt = nt;
+    const size_t na = m->sched.size() / 2;
+    m->sched_comps.assign(na, 2);
+    for (size_t i = 0; i < na; ++i) {
+        const int kind = m->sched[2 * i], arg = m->sched[2 * i + 1];
+        if (kind == 3 && arg >= 0 && i + 1 < na && m->sched[2 * (i + 1)] == 4)
+            m->sched_comps[i] = 1;
+    }
+    for (size_t i = 0; i < na; ++i) {
+        if (m->sched[2 * i] != 2) continue;
+        const int slot = m->sched[2 * i + 1];
+        int need = 1;
+        for (size_t k = i + 1; k < na; ++k) {
+            const int kk = m->sched[2 * k], aa = m->sched[2 * k + 1];
+            if (kk == 2 && aa == slot) break;
+            if (kk == 3 && aa == slot && m->sched_comps[k] == 2) {
+                need = 2;
+                break;
+            }
+        }
+        m->sched_comps[i] = need;
+    }
+}
+
 int grad_setup(GradJob &j, fwi_model *m, const fwi_acq *acq, const float *wavelets,
                const float *d_obs, cudaStream_t s)
 {
@@ -973,55 +1010,55 @@ int grad_setup(GradJob &j, fwi_model *m, const fwi_acq *acq, const float *wavele
     j.nfield = (int64_t)ns * g.field;
     j.fb = (size_t)g.field * sizeof(float);
 
-    // checkpoint slots: as many as the budget holds, never more than nt
+    // checkpoint slots: as many as the budget holds, never more than nt.  A slot holds a
+    // pair (u^n and u^n - u^{n-1}); when the budget holds u^n alone for every step, the
+    // schedule stores every state once and restores each only for its reverse step (no
+    // recomputation), every checkpoint is u^n alone, and slots of half the size suffice.
     const int esz = m->opts.snap_dtype == FWI_SNAP_FP32 ? 4 : 2;
-    const size_t per_slot = (size_t)ns * 2 * g.field * esz;
-    j.per_slot = per_slot;
+    const size_t pair_slot = (size_t)ns * 2 * g.field * esz, half_slot = pair_slot / 2;
     int64_t budget = m->opts.snap_budget_bytes;
     if (budget <= 0) {
         size_t fr = 0, tot = 0;
         FWI_CU(cudaMemGetInfo(&fr, &tot));
         budget = (int64_t)(fr / 4);
     }
-    int64_t slots = budget / (int64_t)per_slot;
-    if (slots > nt) slots = nt;
-    if (slots < 0) slots = 0;
-    if ((size_t)slots * per_slot > m->snaps.bytes) {
+    const void *pool0 = m->snaps.p;
+    const size_t pool0_bytes = m->snaps.bytes;
+    bool half = false;
+    int64_t slots = 0;
+    if (nt >= 2 && budget / (int64_t)half_slot >= nt - 1) {
+        plan_schedule(m, nt, nt - 1);
+        half = true;
+        for (size_t i = 0; i < m->sched_comps.size(); ++i) {
+            const int kind = m->sched[2 * i];
+            if ((kind == 2 || kind == 3) && m->sched_comps[i] != 1) half = false;
+        }
+        if (half && m->snaps.bytes < (size_t)(nt - 1) * half_slot &&
+            m->snaps.ensure((size_t)(nt - 1) * half_slot) != FWI_OK)
+            half = false;
+        if (half) slots = nt - 1;
+    }
+    const size_t per_slot = half ? half_slot : pair_slot;
+    j.per_slot = per_slot;
+    j.cstride = half ? g.field : 2 * g.field;
+    if (!half) {
+        slots = budget / (int64_t)per_slot;
+        if (slots > nt) slots = nt;
+        if (slots < 0) slots = 0;
         // shrink on failure rather than fail: fewer slots only cost recomputation
-        while (slots > 0 && m->snaps.ensure((size_t)slots * per_slot) != FWI_OK) slots /= 2;
-        // zero codes in the padding columns, which stores written by the step kernel skip
-        if (m->snaps.p) FWI_CU(cudaMemsetAsync(m->snaps.p, 0, m->snaps.bytes, s));
+        if ((size_t)slots * per_slot > m->snaps.bytes)
+            while (slots > 0 && m->snaps.ensure((size_t)slots * per_slot) != FWI_OK) slots /= 2;
+        plan_schedule(m, nt, (int)slots);
+    }
+    // zero the codes of the padding columns, which the stores of the step kernels skip,
+    // whenever the pool is new or its layout changes (decoded padding must stay zero)
+    const int64_t layout = (int64_t)ns * j.cstride;
+    const bool fresh = m->snaps.p != pool0 || m->snaps.bytes != pool0_bytes;
+    if (m->snaps.p && (fresh || m->snaps_layout != layout)) {
+        FWI_CU(cudaMemsetAsync(m->snaps.p, 0, m->snaps.bytes, s));
+        m->snaps_layout = layout;
     }
     FWI_TRY(m->scales.ensure((size_t)(slots > 0 ? slots : 1) * 2 * ns * sizeof(float)));
-    if (slots != m->sched_nslots) {
-        m->sched = revolve_actions(nt, (int32_t)slots, &m->sched_fwd);
-        m->sched_nslots = (int)slots;
-        // Components each checkpoint action moves: a restore followed by a reverse step
-        // needs u^m alone (the reverse step reads only u^m, straight from the checkpoint;
-        // the following action is always another restore), and a checkpoint whose every
-        // restore is of that kind is stored as u^n alone.
-        const size_t na = m->sched.size() / 2;
-        m->sched_comps.assign(na, 2);
-        for (size_t i = 0; i < na; ++i) {
-            const int kind = m->sched[2 * i], arg = m->sched[2 * i + 1];
-            if (kind == 3 && arg >= 0 && i + 1 < na && m->sched[2 * (i + 1)] == 4)
-                m->sched_comps[i] = 1;
-        }
-        for (size_t i = 0; i < na; ++i) {
-            if (m->sched[2 * i] != 2) continue;
-            const int slot = m->sched[2 * i + 1];
-            int need = 1;
-            for (size_t k = i + 1; k < na; ++k) {
-                const int kk = m->sched[2 * k], aa = m->sched[2 * k + 1];
-                if (kk == 2 && aa == slot) break;
-                if (kk == 3 && aa == slot && m->sched_comps[k] == 2) {
-                    need = 2;
-                    break;
-                }
-            }
-            m->sched_comps[i] = need;
-        }
-    }
     m->nslots = (int)slots;
     m->slot_bytes = per_slot;
 
@@ -1105,7 +1142,7 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
                     j.pf.st_scale = m->scales.as<float>() + (size_t)j.st_slot * 2 * ns;
                     j.pf.st_dtype = m->opts.snap_dtype;
                     j.pf.st_comps = j.st_comps;
-                    j.pf.st_cstride = 2 * g.field;
+                    j.pf.st_cstride = j.cstride;
                     j.st_slot = -1;
                 }
                 if (j.fused_max && next_store && j.kdone == arg - 1) {
@@ -1150,7 +1187,7 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
             FWI_LAUNCH(m, launch_encode(m->u[j.cur].as<float>(), m->u[1 - j.cur].as<float>(),
                                         g.field, g.field, ns, m->opts.snap_dtype,
                                         m->maxbits.as<unsigned>(),
-                                        (void *)(j.codes + (size_t)arg * j.per_slot), 2 * g.field,
+                                        (void *)(j.codes + (size_t)arg * j.per_slot), j.cstride,
                                         m->scales.as<float>() + (size_t)arg * 2 * ns, m->d_flag,
                                         comps, s));
             j.slot_step[arg] = j.step;
@@ -1167,7 +1204,7 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
                 j.aux_slot = arg;
                 j.step = j.slot_step[arg];
             } else {
-                FWI_LAUNCH(m, launch_decode(j.codes + (size_t)arg * j.per_slot, 2 * g.field,
+                FWI_LAUNCH(m, launch_decode(j.codes + (size_t)arg * j.per_slot, j.cstride,
                                             m->scales.as<float>() + (size_t)arg * 2 * ns, g.field,
                                             g.field, ns, m->opts.snap_dtype,
                                             m->u[j.cur].as<float>(),
@@ -1201,7 +1238,7 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
             if (j.aux_slot >= 0) {                        // u^m from its checkpoint
                 j.pa.aux = j.codes + (size_t)j.aux_slot * j.per_slot;
                 j.pa.aux_fmt = m->opts.snap_dtype;
-                j.pa.aux_stride = 2 * g.field;
+                j.pa.aux_stride = j.cstride;
                 j.pa.aux_scale = m->scales.as<float>() + (size_t)j.aux_slot * 2 * ns;
             } else {                                      // u^m in the forward buffer
                 j.pa.aux = m->u[j.cur].as<float>();

@@ -328,3 +328,31 @@ def test_errors_are_reported():
     with pytest.raises(f.FwiError) as e:
         f.fwi_sync_status(m.handle)
     assert e.value.code == f.FWI_ERR_UNSTABLE
+
+
+@pytest.mark.parametrize("snap", ["bf16", "fp32"])
+@pytest.mark.parametrize("ndim,shape,order", [(2, (40, 52), 8), (3, (15, 16, 18), 16)])
+def test_gradient_store_all_half_slots(snap, ndim, shape, order):
+    """A budget that holds u^n alone for every step but not pairs: the schedule runs the
+    forward recursion once (nt forward steps, nt - 1 checkpoints, each restored only for
+    its reverse step), in slots of half the pair size; the gradient meets the same bars
+    as with recomputation, and with FP32 checkpoints equals the recomputing run's."""
+    w, dobs = _grad_case(ndim, shape, order, nt=90, f0=10.0)
+    probe, _, _ = make_pair(w, snap=snap, budget=1)
+    pitch, comp = probe.info()["pitch_x"], probe.info()["computed"]
+    field = -(-comp[0] * comp[1] * pitch // 64) * 64
+    esz = 4 if snap == "fp32" else 2
+    m, p, acq = make_pair(w, snap=snap, budget=(w.nt - 1) * field * esz)
+    wav, d = torch.from_numpy(w.wavelets()).cuda(), torch.from_numpy(dobs).cuda()
+    _, g = m.gradient(acq, wav, d)
+    info = m.info()
+    assert info["snap_slots"] == w.nt - 1 and info["last_forward_steps"] == w.nt
+    rphi, rg = p.gradient(dobs.astype(np.float64))
+    e = rel(g.cpu().numpy(), rg)
+    print(f"store-all grad {snap} {ndim}d: rel-L2 {e:.2e}")
+    assert e <= (TOL_GRAD32 if snap == "fp32" else TOL_GRAD16)
+    if snap == "fp32":
+        m2, _, _ = make_pair(w, snap=snap, budget=8 * 2 * esz * field)
+        _, g2 = m2.gradient(acq, wav, d)
+        assert m2.info()["last_forward_steps"] > w.nt
+        assert torch.equal(g, g2)
