@@ -211,6 +211,17 @@ int fwi_snapshot_decode(const void *code, const float *scale, int64_t n, int32_t
 int fwi_revolve_schedule(int32_t nsteps, int32_t nslots, int32_t *actions,
                          int64_t max_actions, int64_t *n_actions, int64_t *n_forward);
 
+/* Host only.  The checkpoint plan a gradient call makes for nsteps steps from a budget
+ * of half_slots units, one unit being the codes of one field (all shots): a checkpoint
+ * restored only for its reverse step is u^n alone (one unit), any other the pair
+ * u^n, u^n - u^{n-1} (two units), and a slot takes two units if the revolve schedule
+ * ever stores a pair in it.  The plan is the largest slot count whose layout fits:
+ * *slots, *pair_slots (slots of two units) and *n_forward (forward steps of the
+ * schedule; nsteps when u^n of every step fits, i.e. no recomputation).  FWI_ERR_ARG
+ * for nsteps < 1 or half_slots < 0. */
+int fwi_checkpoint_plan(int32_t nsteps, int64_t half_slots, int32_t *slots,
+                        int32_t *pair_slots, int64_t *n_forward);
+
 /* Host only.  Central second-derivative weights c_0..c_M of order 2M (M = order/2) as
  * FP64 (the stencil of Eq. 2-3's Laplacian). */
 int fwi_fd_coeffs(int32_t order, double *c);

@@ -166,6 +166,9 @@ struct fwi_model {
     bool og_src = false, og_rec = false;   // current acquisition uses off-grid points
     // cached schedule
     int sched_nslots = -1, sched_nt = -1;
+    int sched_npair = 0;               // slots that ever hold a pair
+    std::vector<int64_t> slot_off;     // slot k starts slot_off[k] half slots into the pool
+    std::vector<char> slot_pair;       // slot k holds pairs (two fields per shot)
     int64_t snaps_layout = -1;   // code layout the pool was last zeroed for
     std::vector<int32_t> sched;
     std::vector<int> sched_comps;   // per action: checkpoint components moved (1 or 2)
@@ -871,8 +874,7 @@ struct GradJob {
     cudaStream_t s = nullptr;
     int ns = 0, nr = 0, nt = 0;
     int64_t nfield = 0;
-    size_t fb = 0, per_slot = 0;
-    int64_t cstride = 0;   // code elements per shot in a slot (2 fields, or 1: u^n alone)
+    size_t fb = 0, half_slot = 0;   // bytes of one field's codes for all shots
     const void *dobs = nullptr;
     StepParams pf{}, pa{};
     float *tr = nullptr, *res = nullptr;
@@ -967,7 +969,11 @@ int grad_capture(GradJob &j, int par, bool rec)
 // by a reverse step needs u^m alone (the reverse step reads only u^m, straight from the
 // checkpoint; the following action is always another restore), and a checkpoint whose
 // every restore is of that kind is stored as u^n alone.
-void plan_schedule(fwi_model *m, int nt, int slots)
+// Code elements per shot in checkpoint slot k: two fields for a pair slot, else one.
+int64_t slot_cstride(const fwi_model *m, int k) { return (m->slot_pair[k] ? 2 : 1) * m->g.field; }
+
+template <class Plan>
+void plan_schedule(Plan *m, int nt, int slots)
 {
     if (slots == m->sched_nslots && m->sched_nt == nt) return;
     m->sched = revolve_actions(nt, (int32_t)slots, &m->sched_fwd);
@@ -980,20 +986,51 @@ void plan_schedule(fwi_model *m, int nt, int slots)
         if (kind == 3 && arg >= 0 && i + 1 < na && m->sched[2 * (i + 1)] == 4)
             m->sched_comps[i] = 1;
     }
-    for (size_t i = 0; i < na; ++i) {
-        if (m->sched[2 * i] != 2) continue;
-        const int slot = m->sched[2 * i + 1];
-        int need = 1;
-        for (size_t k = i + 1; k < na; ++k) {
-            const int kk = m->sched[2 * k], aa = m->sched[2 * k + 1];
-            if (kk == 2 && aa == slot) break;
-            if (kk == 3 && aa == slot && m->sched_comps[k] == 2) {
-                need = 2;
-                break;
-            }
+    // backwards: a store needs the pair if a pair restore of its slot follows it before
+    // the slot's next store
+    std::vector<char> need2(slots > 0 ? slots : 1, 0);
+    m->slot_pair.assign(slots > 0 ? slots : 0, 0);
+    for (size_t i = na; i-- > 0;) {
+        const int kind = m->sched[2 * i], arg = m->sched[2 * i + 1];
+        if (kind == 3 && arg >= 0 && m->sched_comps[i] == 2) need2[arg] = 1;
+        if (kind == 2) {
+            m->sched_comps[i] = need2[arg] ? 2 : 1;
+            if (need2[arg]) m->slot_pair[arg] = 1;
+            need2[arg] = 0;
         }
-        m->sched_comps[i] = need;
     }
+    m->slot_off.assign(slots > 0 ? slots : 0, 0);
+    int64_t off = 0;
+    m->sched_npair = 0;
+    for (int k = 0; k < slots; ++k) {
+        m->slot_off[k] = off;
+        off += m->slot_pair[k] ? 2 : 1;
+        m->sched_npair += m->slot_pair[k] ? 1 : 0;
+    }
+}
+
+// The largest slot count whose layout (slots that hold pairs count twice) fits `halves`
+// units, never more than nt, by bisection (s slots fit, s + 1 do not); leaves that plan
+// in *m.
+template <class Plan>
+int64_t fit_slots(Plan *m, int nt, int64_t halves)
+{
+    int64_t hi = halves < nt ? halves : nt;
+    if (hi <= 0) {
+        plan_schedule(m, nt, 0);
+        return 0;
+    }
+    plan_schedule(m, nt, (int)hi);
+    if (hi + m->sched_npair <= halves) return hi;
+    int64_t lo = 0;   // no slots: no pairs, always fits
+    while (hi - lo > 1) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        plan_schedule(m, nt, (int)mid);
+        if (mid + m->sched_npair <= halves) lo = mid;
+        else hi = mid;
+    }
+    plan_schedule(m, nt, (int)lo);
+    return lo;
 }
 
 int grad_setup(GradJob &j, fwi_model *m, const fwi_acq *acq, const float *wavelets,
@@ -1010,12 +1047,15 @@ int grad_setup(GradJob &j, fwi_model *m, const fwi_acq *acq, const float *wavele
     j.nfield = (int64_t)ns * g.field;
     j.fb = (size_t)g.field * sizeof(float);
 
-    // checkpoint slots: as many as the budget holds, never more than nt.  A slot holds a
-    // pair (u^n and u^n - u^{n-1}); when the budget holds u^n alone for every step, the
-    // schedule stores every state once and restores each only for its reverse step (no
-    // recomputation), every checkpoint is u^n alone, and slots of half the size suffice.
+    // checkpoint slots: as many as the budget holds, never more than nt.  A checkpoint is
+    // a pair (u^n and u^n - u^{n-1}) or u^n alone (every restore of it feeds a reverse
+    // step), and the schedule fixes which: a slot takes two fields of codes per shot only
+    // if it ever holds a pair, one otherwise.  The slot count is the largest whose layout
+    // fits the budget; when u^n of every step fits, the schedule stores every state once
+    // and never recomputes.
     const int esz = m->opts.snap_dtype == FWI_SNAP_FP32 ? 4 : 2;
-    const size_t pair_slot = (size_t)ns * 2 * g.field * esz, half_slot = pair_slot / 2;
+    const size_t half_slot = (size_t)ns * g.field * esz;
+    j.half_slot = half_slot;
     int64_t budget = m->opts.snap_budget_bytes;
     if (budget <= 0) {
         size_t fr = 0, tot = 0;
@@ -1024,35 +1064,18 @@ int grad_setup(GradJob &j, fwi_model *m, const fwi_acq *acq, const float *wavele
     }
     const void *pool0 = m->snaps.p;
     const size_t pool0_bytes = m->snaps.bytes;
-    bool half = false;
+    int64_t halves = budget / (int64_t)half_slot;
     int64_t slots = 0;
-    if (nt >= 2 && budget / (int64_t)half_slot >= nt - 1) {
-        plan_schedule(m, nt, nt - 1);
-        half = true;
-        for (size_t i = 0; i < m->sched_comps.size(); ++i) {
-            const int kind = m->sched[2 * i];
-            if ((kind == 2 || kind == 3) && m->sched_comps[i] != 1) half = false;
-        }
-        if (half && m->snaps.bytes < (size_t)(nt - 1) * half_slot &&
-            m->snaps.ensure((size_t)(nt - 1) * half_slot) != FWI_OK)
-            half = false;
-        if (half) slots = nt - 1;
-    }
-    const size_t per_slot = half ? half_slot : pair_slot;
-    j.per_slot = per_slot;
-    j.cstride = half ? g.field : 2 * g.field;
-    if (!half) {
-        slots = budget / (int64_t)per_slot;
-        if (slots > nt) slots = nt;
-        if (slots < 0) slots = 0;
+    for (;;) {
+        slots = fit_slots(m, nt, halves);
+        const size_t need = (size_t)(slots + m->sched_npair) * half_slot;
         // shrink on failure rather than fail: fewer slots only cost recomputation
-        if ((size_t)slots * per_slot > m->snaps.bytes)
-            while (slots > 0 && m->snaps.ensure((size_t)slots * per_slot) != FWI_OK) slots /= 2;
-        plan_schedule(m, nt, (int)slots);
+        if (slots == 0 || need <= m->snaps.bytes || m->snaps.ensure(need) == FWI_OK) break;
+        halves = (slots + m->sched_npair) / 2;
     }
     // zero the codes of the padding columns, which the stores of the step kernels skip,
     // whenever the pool is new or its layout changes (decoded padding must stay zero)
-    const int64_t layout = (int64_t)ns * j.cstride;
+    const int64_t layout = ((int64_t)ns * g.field * 8191 + slots) * 8191 + m->sched_npair;
     const bool fresh = m->snaps.p != pool0 || m->snaps.bytes != pool0_bytes;
     if (m->snaps.p && (fresh || m->snaps_layout != layout)) {
         FWI_CU(cudaMemsetAsync(m->snaps.p, 0, m->snaps.bytes, s));
@@ -1060,7 +1083,7 @@ int grad_setup(GradJob &j, fwi_model *m, const fwi_acq *acq, const float *wavele
     }
     FWI_TRY(m->scales.ensure((size_t)(slots > 0 ? slots : 1) * 2 * ns * sizeof(float)));
     m->nslots = (int)slots;
-    m->slot_bytes = per_slot;
+    m->slot_bytes = slots > 0 ? (size_t)(slots + m->sched_npair) * half_slot / slots : 0;
 
     const void *wav;
     FWI_TRY(stage_input(m, 0, wavelets, (size_t)ns * nt * sizeof(float), s, &wav));
@@ -1138,11 +1161,11 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
                 j.pf.maxbits = nullptr;
                 j.pf.st_code = nullptr;
                 if (j.st_slot >= 0) {   // the deferred checkpoint of this step's input pair
-                    j.pf.st_code = (void *)(j.codes + (size_t)j.st_slot * j.per_slot);
+                    j.pf.st_code = (void *)(j.codes + m->slot_off[j.st_slot] * j.half_slot);
                     j.pf.st_scale = m->scales.as<float>() + (size_t)j.st_slot * 2 * ns;
                     j.pf.st_dtype = m->opts.snap_dtype;
                     j.pf.st_comps = j.st_comps;
-                    j.pf.st_cstride = j.cstride;
+                    j.pf.st_cstride = slot_cstride(m, j.st_slot);
                     j.st_slot = -1;
                 }
                 if (j.fused_max && next_store && j.kdone == arg - 1) {
@@ -1187,7 +1210,7 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
             FWI_LAUNCH(m, launch_encode(m->u[j.cur].as<float>(), m->u[1 - j.cur].as<float>(),
                                         g.field, g.field, ns, m->opts.snap_dtype,
                                         m->maxbits.as<unsigned>(),
-                                        (void *)(j.codes + (size_t)arg * j.per_slot), j.cstride,
+                                        (void *)(j.codes + m->slot_off[arg] * j.half_slot), slot_cstride(m, arg),
                                         m->scales.as<float>() + (size_t)arg * 2 * ns, m->d_flag,
                                         comps, s));
             j.slot_step[arg] = j.step;
@@ -1204,7 +1227,7 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
                 j.aux_slot = arg;
                 j.step = j.slot_step[arg];
             } else {
-                FWI_LAUNCH(m, launch_decode(j.codes + (size_t)arg * j.per_slot, j.cstride,
+                FWI_LAUNCH(m, launch_decode(j.codes + m->slot_off[arg] * j.half_slot, slot_cstride(m, arg),
                                             m->scales.as<float>() + (size_t)arg * 2 * ns, g.field,
                                             g.field, ns, m->opts.snap_dtype,
                                             m->u[j.cur].as<float>(),
@@ -1236,9 +1259,9 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
             j.pa.prev = m->mu[1 - j.mcur].as<float>();   // mu^{m+2} -> mu^m
             const bool img = mm < nt;                    // mu^{nt+1} = 0: no imaging at nt
             if (j.aux_slot >= 0) {                        // u^m from its checkpoint
-                j.pa.aux = j.codes + (size_t)j.aux_slot * j.per_slot;
+                j.pa.aux = j.codes + m->slot_off[j.aux_slot] * j.half_slot;
                 j.pa.aux_fmt = m->opts.snap_dtype;
-                j.pa.aux_stride = j.cstride;
+                j.pa.aux_stride = slot_cstride(m, j.aux_slot);
                 j.pa.aux_scale = m->scales.as<float>() + (size_t)j.aux_slot * 2 * ns;
             } else {                                      // u^m in the forward buffer
                 j.pa.aux = m->u[j.cur].as<float>();
@@ -1428,6 +1451,25 @@ int fwi_revolve_schedule(int32_t nsteps, int32_t nslots, int32_t *actions,
     if (!actions) return FWI_OK;
     if (na > max_actions) return fail(FWI_ERR_ARG, "max_actions too small");
     std::memcpy(actions, a.data(), a.size() * sizeof(int32_t));
+    return FWI_OK;
+}
+
+int fwi_checkpoint_plan(int32_t nsteps, int64_t half_slots, int32_t *slots,
+                        int32_t *pair_slots, int64_t *n_forward)
+{
+    if (nsteps < 1 || half_slots < 0) return fail(FWI_ERR_ARG, "nsteps >= 1 and half_slots >= 0");
+    struct {
+        std::vector<int32_t> sched;
+        std::vector<int> sched_comps;
+        int64_t sched_fwd = 0;
+        int sched_nslots = -1, sched_nt = -1, sched_npair = 0;
+        std::vector<int64_t> slot_off;
+        std::vector<char> slot_pair;
+    } plan;
+    const int64_t n = fit_slots(&plan, nsteps, half_slots);
+    if (slots) *slots = (int32_t)n;
+    if (pair_slots) *pair_slots = plan.sched_npair;
+    if (n_forward) *n_forward = plan.sched_fwd;
     return FWI_OK;
 }
 

@@ -102,6 +102,7 @@ def lib():
                 "fwi_snapshot_encode": ([P, P, c_i64, c_i32, P, P, P], c_i32),
                 "fwi_snapshot_decode": ([P, P, c_i64, c_i32, P, P, P], c_i32),
                 "fwi_revolve_schedule": ([c_i32, c_i32, P, c_i64, P, P], c_i32),
+                "fwi_checkpoint_plan": ([c_i32, c_i64, P, P, P], c_i32),
                 "fwi_fd_coeffs": ([c_i32, P], c_i32),
                 "fwi_cfl_number": ([c_i32, c_i32, P, c_f32, c_f32], c_f64),
                 "fwi_model_info": ([P, P], c_i32),
@@ -212,6 +213,15 @@ def fwi_revolve_schedule(nsteps: int, nslots: int):
     _check(lib().fwi_revolve_schedule(int(nsteps), int(nslots), out.ctypes.data, na.value,
                                       ctypes.byref(na), ctypes.byref(nf)))
     return out, nf.value
+
+
+def fwi_checkpoint_plan(nsteps: int, half_slots: int):
+    """(slots, pair slots, forward steps) of the checkpoint plan a gradient call makes for
+    nsteps steps from a budget of half_slots field-sized units."""
+    ns, npair, nf = c_i32(), c_i32(), c_i64()
+    _check(lib().fwi_checkpoint_plan(int(nsteps), int(half_slots), ctypes.byref(ns),
+                                     ctypes.byref(npair), ctypes.byref(nf)))
+    return ns.value, npair.value, nf.value
 
 
 def fwi_fd_coeffs(order: int) -> np.ndarray:

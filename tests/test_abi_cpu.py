@@ -116,3 +116,47 @@ def test_revolve_schedule_large(nsteps, nslots):
     while comb(c + 1 + r, c + 1) < l:
         r += 1
     assert nf == r * l - comb(c + 2 + r - 1, c + 2)
+
+
+def _pair_slots(acts):
+    """Slots that ever receive a pair, from the schedule alone: a restore followed by an
+    adjoint step needs u^m only; a store needs the pair when a restore of another kind
+    reads its slot before the slot's next store."""
+    acts = [tuple(a) for a in acts]
+    pairs = set()
+    for i, (kind, arg) in enumerate(acts):
+        if kind != 2:
+            continue
+        for k in range(i + 1, len(acts)):
+            kk, aa = acts[k]
+            if kk == 2 and aa == arg:
+                break
+            if kk == 3 and aa == arg and not (k + 1 < len(acts) and acts[k + 1][0] == 4):
+                pairs.add(arg)
+                break
+    return pairs
+
+
+@pytest.mark.parametrize("nsteps,halves", [(60, 200), (60, 59), (60, 40), (60, 8), (60, 1),
+                                           (300, 45), (4000, 613), (3000, 2999)])
+def test_checkpoint_plan_is_the_largest_layout_that_fits(nsteps, halves):
+    slots, npair, nf = fwi.fwi_checkpoint_plan(nsteps, halves)
+    acts, nf_ref = fwi.fwi_revolve_schedule(nsteps, slots)
+    assert nf == nf_ref
+    pairs = _pair_slots(acts.tolist())
+    assert npair == len(pairs)
+    assert slots + npair <= halves and slots <= nsteps
+    if slots < nsteps:   # one more slot would not fit
+        acts1, _ = fwi.fwi_revolve_schedule(nsteps, slots + 1)
+        assert slots + 1 + len(_pair_slots(acts1.tolist())) > halves
+    if halves >= nsteps - 1:   # u^n of every step fits: no recomputation, no pairs
+        assert nf == nsteps and npair == 0
+
+
+def test_checkpoint_plan_forward_steps_fall_with_budget():
+    prev = None
+    for halves in (0, 10, 50, 200, 613, 1200, 3999):
+        nf = fwi.fwi_checkpoint_plan(4000, halves)[2]
+        assert prev is None or nf <= prev
+        prev = nf
+    assert prev == 4000

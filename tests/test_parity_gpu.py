@@ -244,12 +244,14 @@ def _config_case(w, nslots, snap):
 
 def test_gradient_layered_64_instance_bf16():
     """64^3 instance of the 256^3 layered model (h 10 m, dt 0.8 ms, 8th order, 15 Hz,
-    receivers every 2nd cell on row 5), 300 steps, 20 BF16 checkpoints."""
+    receivers every 2nd cell on row 5), 300 steps, a budget of 20 BF16 pair checkpoints
+    (more slots than 20 once those that only ever hold u^n take one field)."""
     w = synth.layered_3d(64, nt=300)
     e, info, em = _config_case(w, 20, "bf16")
     print(f"layered 64^3 bf16: grad rel-L2 {e:.2e}, misfit rel {em:.2e}, "
           f"slots {info['snap_slots']}, forward steps {info['last_forward_steps']}")
-    assert info["snap_slots"] == 20 and info["last_forward_steps"] > w.nt
+    slots, _, nf = fwi().fwi_checkpoint_plan(w.nt, 40)
+    assert info["snap_slots"] == slots >= 20 and info["last_forward_steps"] == nf > w.nt
     assert e <= TOL_GRAD16
 
 
