@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--nt", type=int, default=0, help="override the step count (short runs)")
     ap.add_argument("--n", type=int, default=0,
                     help="grid size of a scaled twin of the workload (profiling runs)")
-    ap.add_argument("--snap-budget-gb", type=float, default=192.0)
+    ap.add_argument("--snap-budget-gb", type=float, default=224.0)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

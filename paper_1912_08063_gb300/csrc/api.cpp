@@ -1071,7 +1071,7 @@ int grad_setup(GradJob &j, fwi_model *m, const fwi_acq *acq, const float *wavele
         const size_t need = (size_t)(slots + m->sched_npair) * half_slot;
         // shrink on failure rather than fail: fewer slots only cost recomputation
         if (slots == 0 || need <= m->snaps.bytes || m->snaps.ensure(need) == FWI_OK) break;
-        halves = (slots + m->sched_npair) / 2;
+        halves = (slots + m->sched_npair) * 7 / 8;
     }
     // zero the codes of the padding columns, which the stores of the step kernels skip,
     // whenever the pool is new or its layout changes (decoded padding must stay zero)
