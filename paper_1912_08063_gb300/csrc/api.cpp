@@ -553,6 +553,8 @@ int step3d_launch(fwi_model *m, const StepParams &p, int ns, int mode, cudaStrea
     }
     q.c0 = m->co.c0;
     q.c02 = make_float2(m->co.c0, m->co.c0);
+    q.iso = m->h[0] == m->h[1] && m->h[1] == m->h[2];
+    q.inv_h2 = (float)(1.0 / ((double)m->h[0] * m->h[0]));
     q.sig_x = sig_x(m);
     q.sig_y = sig_y(m);
     q.sig_z = sig_z(m);

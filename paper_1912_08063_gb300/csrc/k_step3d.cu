@@ -30,11 +30,11 @@ Step3dVariant step3d_variant(int M)
     return v;
 }
 
-static Step3dKernelInfo kernel_info(int M, int mode)
+static Step3dKernelInfo kernel_info(int M, int mode, bool iso = false)
 {
     const Step3dVariant v = step3d_variant(M);
-    if (M == 8) return step3d_kernel_m8(v, mode);
-    if (M == 4) return step3d_kernel_m4(v, mode);
+    if (M == 8) return step3d_kernel_m8(v, mode, iso);
+    if (M == 4) return step3d_kernel_m4(v, mode, iso);
     return Step3dKernelInfo{nullptr, 0, 0};
 }
 
@@ -66,7 +66,7 @@ cudaError_t launch_step3d_tma(const Step3dParams &p, int mode, int ctas,
                               const CUtensorMap &mb, const CUtensorMap &md,
                               const CUtensorMap &me, cudaStream_t s)
 {
-    const Step3dKernelInfo k = kernel_info(p.M, mode);
+    const Step3dKernelInfo k = kernel_info(p.M, mode, p.iso != 0);
     if (!k.fn) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute((const void *)k.fn,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem);

@@ -146,11 +146,55 @@ __device__ __forceinline__ void src_image(float2 &g0, float2 &g1, float4 c, floa
 //              offsets pair points (0,1) and (2,3) and add into the y accumulators, odd
 //              offsets pair (1,2))
 //   kInterior  rows with no damping (s = 0 at all four points) skip the sponge division
-constexpr int kPackX = 1, kInterior = 2;
+//   kIso       isotropic grid (hx = hy = hz): the stencil weights are compile-time
+//              constants and the Laplacian is scaled by 1 / h^2 once per point, so the
+//              weights take no registers and no loads
+constexpr int kPackX = 1, kInterior = 2, kIso = 16;
+
+// Taylor weights of radius M evaluated at compile time from their closed form
+// c_k = 2 (-1)^{k+1} (M!)^2 / (k^2 (M-k)! (M+k)!), c_0 = -2 sum_k c_k (the host's
+// set-up evaluates the same expression), and the 3-D centre weight 3 c_0.
+template <int M>
+struct TaylorW {
+    float c[M + 1];
+    float c0x3;
+};
+
+template <int M>
+__host__ __device__ constexpr TaylorW<M> taylor_weights()
+{
+    TaylorW<M> w{};
+    double total = 0.0;
+    for (int k = 1; k <= M; ++k) {
+        double ratio = 1.0;
+        for (int i = 1; i <= k; ++i) ratio *= (double)(M - k + i) / (double)(M + i);
+        const double ck = ((k & 1) ? 2.0 : -2.0) * ratio / ((double)k * k);
+        w.c[k] = (float)ck;
+        total += ck;
+    }
+    w.c[0] = (float)(-2.0 * total);
+    w.c0x3 = (float)(-6.0 * total);
+    return w;
+}
+
+template <int M>
+__device__ __forceinline__ float taylor(int k)
+{
+    constexpr TaylorW<M> w = taylor_weights<M>();
+    return w.c[k];
+}
+
+template <int M>
+__device__ __forceinline__ float taylor_centre3()
+{
+    constexpr TaylorW<M> w = taylor_weights<M>();
+    return w.c0x3;
+}
 
 template <int M_, int TY_, int RY_, int P_, int U_, int F_, int NPW_>
 struct Cfg {
     static constexpr int M = M_, TY = TY_, RY = RY_, P = P_, U = U_, F = F_;
+    static constexpr bool ISO = (F & kIso) != 0;
     static constexpr int NPW = NPW_;   // pointwise tiles per stage
     static constexpr int TX = 64, RX = 4;
     static constexpr int NTX = TX / RX, NTY = TY / RY, NT = NTX * NTY;
@@ -283,7 +327,8 @@ struct Ctx {
                 if (d == 0) {
                     ctr[r] = v;
                 } else if (d >= -M && d <= M) {
-                    const float2 cc = p->cy2[d < 0 ? -d : d];
+                    const float2 cc = C::ISO ? make_float2(taylor<M>(d < 0 ? -d : d), taylor<M>(d < 0 ? -d : d))
+                                             : p->cy2[d < 0 ? -d : d];
                     if (t & 1) {
                         ya[r][0] = __ffma2_rn(cc, lo2(v), ya[r][0]);
                         ya[r][1] = __ffma2_rn(cc, hi2(v), ya[r][1]);
@@ -316,7 +361,7 @@ struct Ctx {
                 float x0 = 0.0f, x3 = 0.0f;
 #pragma unroll
                 for (int k = 1; k <= M; ++k) {
-                    const float ck = p->cx[k];
+                    const float ck = C::ISO ? taylor<M>(k) : p->cx[k];
                     const float2 ck2 = make_float2(ck, ck);
                     if ((k & 1) == 0) {
                         ya[r][0] = __ffma2_rn(ck2, __fadd2_rn(make_float2(w[M + k], w[M + k + 1]),
@@ -343,8 +388,9 @@ struct Ctx {
 #pragma unroll
                     for (int k = 1; k <= M; ++k) {
                         const float s = w[M + e + k] + w[M + e - k];
-                        if (k & 1) a0 = fmaf(p->cx[k], s, a0);
-                        else a1 = fmaf(p->cx[k], s, a1);
+                        const float ck = C::ISO ? taylor<M>(k) : p->cx[k];
+                        if (k & 1) a0 = fmaf(ck, s, a0);
+                        else a1 = fmaf(ck, s, a1);
                     }
                     lx[e] = a0 + a1;
                 }
@@ -354,7 +400,7 @@ struct Ctx {
 #pragma unroll
             for (int k = 1; k <= M; ++k) {
                 const float4 up = q[R - M + k][r], dn = q[R - M - k][r];
-                const float2 cc = p->cz2[k];
+                const float2 cc = C::ISO ? make_float2(taylor<M>(k), taylor<M>(k)) : p->cz2[k];
                 if (k & 1) {
                     za0 = __ffma2_rn(cc, __fadd2_rn(lo2(up), lo2(dn)), za0);
                     za1 = __ffma2_rn(cc, __fadd2_rn(hi2(up), hi2(dn)), za1);
@@ -364,11 +410,16 @@ struct Ctx {
                 }
             }
             const float4 cz4 = q[R - M][r];
-            const float2 c0 = p->c02;
+            const float2 c0 = C::ISO ? make_float2(taylor_centre3<M>(), taylor_centre3<M>()) : p->c02;
             const float2 s0 = __fadd2_rn(__fadd2_rn(za0, zb0), __fadd2_rn(ya[r][0], yb[r][0]));
             const float2 s1 = __fadd2_rn(__fadd2_rn(za1, zb1), __fadd2_rn(ya[r][1], yb[r][1]));
-            const float2 l0 = __ffma2_rn(c0, lo2(cz4), __fadd2_rn(s0, make_float2(lx[0], lx[1])));
-            const float2 l1 = __ffma2_rn(c0, hi2(cz4), __fadd2_rn(s1, make_float2(lx[2], lx[3])));
+            float2 l0 = __ffma2_rn(c0, lo2(cz4), __fadd2_rn(s0, make_float2(lx[0], lx[1])));
+            float2 l1 = __ffma2_rn(c0, hi2(cz4), __fadd2_rn(s1, make_float2(lx[2], lx[3])));
+            if (C::ISO) {
+                const float2 ih = make_float2(p->inv_h2, p->inv_h2);
+                l0 = __fmul2_rn(l0, ih);
+                l1 = __fmul2_rn(l1, ih);
+            }
 
             const int y = y0 + r;
             const int toff = (ty * RY + r) * TX + tx * 4;

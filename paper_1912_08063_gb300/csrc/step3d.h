@@ -26,6 +26,8 @@ struct Step3dParams {
     int rem_ctas;                 // CTAs sharing the leftover columns along z
     float cx[kMaxM + 1], cy[kMaxM + 1], cz[kMaxM + 1], c0;
     float2 cy2[kMaxM + 1], cz2[kMaxM + 1], c02;   // the same weights as packed pairs
+    int iso;                      // hx = hy = hz: the isotropic instantiation may run
+    float inv_h2;                 // 1 / h^2 of an isotropic grid
     const float *sig_x, *sig_y, *sig_z;
     float *out;                   // the new state, over prev (in place)
     float *g;                     // kModeAdj: gradient accumulator
@@ -78,8 +80,10 @@ struct Step3dKernelInfo {
     Step3dKernel fn;
     int threads, smem;
 };
-Step3dKernelInfo step3d_kernel_m4(const Step3dVariant &v, int mode);
-Step3dKernelInfo step3d_kernel_m8(const Step3dVariant &v, int mode);
+// iso: the grid is isotropic, so an instantiation with compile-time stencil weights
+// (scaled by 1 / h^2 once per point) may be returned.
+Step3dKernelInfo step3d_kernel_m4(const Step3dVariant &v, int mode, bool iso = false);
+Step3dKernelInfo step3d_kernel_m8(const Step3dVariant &v, int mode, bool iso = false);
 
 // Encodes a 4-D tensor map over shots of a field laid out as in Geom (elements of
 // `elem_bytes` = 4 or 2, shots `shot_stride` elements apart), with box (bx, by, 1, 1) and
