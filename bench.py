@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=32)
+    ap.add_argument("--serving-rates", default="0.8",
+                    help="comma-separated fractions of the batched capacity for Poisson arrivals")
     ap.add_argument("--batched-nt", type=int, default=3000,
                     help="time steps of the batched 2-D section (shorter for profiling)")
     return ap.parse_args()
@@ -229,10 +231,11 @@ def cpu_baseline_one_core(args, sample_n=160, sample_nt=10):
         return None
 
 
-def serving_section(dev, n_req, seed=4):
+def serving_section(dev, n_req, seed=4, rates=(0.8,)):
     """Serving workload (Poisson stream of forward/gradient requests, 75 % 2-D / 25 % 3-D,
     sides 128..1024 / 64..192, nt 500..3000): closed-loop capacity with continuous batching
-    and one request at a time, then Poisson arrivals at 0.8 x the batched capacity."""
+    and one request at a time, then Poisson arrivals at 0.8 x the batched capacity (both
+    ways), and at each further fraction in `rates` (batched only)."""
     import math
 
     import torch
@@ -270,7 +273,17 @@ def serving_section(dev, n_req, seed=4):
     arr = np.cumsum(rng.exponential(1.0 / lam, n_req))
     _, lat_b, _ = run(16, arr)
     _, lat_1, _ = run(1, arr)
-    return {"requests": n_req, "completed": [ok_b, ok_1],
+    sweep = []
+    for f in rates:
+        if abs(f - 0.8) < 1e-9:
+            lat, ok = lat_b, ok_b
+        else:
+            arr_f = np.cumsum(np.random.default_rng(seed).exponential(1.0 / (f * cap_b), n_req))
+            _, lat, ok = run(16, arr_f)
+        sweep.append({"rate_fraction": f, "rate_per_s": round(f * cap_b, 3), "completed": ok,
+                      "p50_s": round(float(np.percentile(lat, 50)), 3),
+                      "p99_s": round(float(np.percentile(lat, 99)), 3)})
+    return {"requests": n_req, "completed": [ok_b, ok_1], "load_sweep": sweep,
             "shots_per_s": round(cap_b, 3), "shots_per_s_one_at_a_time": round(cap_1, 3),
             "poisson_rate_per_s": round(lam, 3),
             "p50_s": round(float(np.percentile(lat_b, 50)), 3),
@@ -521,7 +534,8 @@ def main():
     model.close()
     serving = batched = None
     if rank == 0 and not args.no_serving:
-        serving = serving_section(dev, args.serving_requests)
+        serving = serving_section(dev, args.serving_requests,
+                                  rates=tuple(float(x) for x in args.serving_rates.split(",")))
     if rank == 0 and not args.no_batched:
         batched = batched_section(dev, args.batched_nt, args.snap_budget_gb)
 
