@@ -60,7 +60,8 @@ typedef struct {
     int32_t fold_every;         /* adjoint steps between FP32 -> FP64 gradient folds
                                    (default 64)                                         */
     int64_t snap_budget_bytes;  /* device bytes for checkpoints over all shots; 0 = a
-                                   quarter of the free memory at the first gradient call */
+                                   quarter of the free memory at the first gradient call;
+                                   sliced as fwi_checkpoint_plan describes              */
     float   sponge_r0;          /* target reflection coefficient (default 1e-3)         */
     float   sponge_vref;        /* velocity in the sponge strength; <= 0: largest
                                    velocity of the model at creation                     */
@@ -147,8 +148,11 @@ int fwi_forward(fwi_model *m, const fwi_acq *acq, const float *wavelets, float *
  * physical velocity grid, by the exact discrete adjoint of the forward scheme and the
  * zero-lag imaging condition (gradient named in Sec. 1; derivation in the library's
  * design notes).  Checkpointing: binomial (revolve) schedule over nt with as many
- * checkpoints per shot as snap_budget_bytes allows, stored as opts.snap_dtype with a
- * per-checkpoint power-of-two scale; forward states between checkpoints are recomputed.
+ * checkpoints per shot as snap_budget_bytes allows (fwi_checkpoint_plan: a checkpoint is
+ * u^n alone when it only ever feeds reverse steps, else the pair u^n, u^n - u^{n-1}, and
+ * slots are sized by what they hold; when u^n of every step fits, nothing is
+ * recomputed), stored as opts.snap_dtype with a per-checkpoint power-of-two scale;
+ * forward states between checkpoints are recomputed.
  * d_obs: FP32 [nshots][nt][nrec] (host or device).  misfit: FP64 [1] (host or device,
  * nullable).  grad: FP32 physical grid (host or device, nullable).  grad64: FP64
  * physical grid (host or device, nullable).  Gradients are summed over shots. */
@@ -279,7 +283,8 @@ typedef struct {
     int64_t hbm_budget_bytes;   /* device memory for admitted requests (0: 80 % free)   */
     int32_t max_active;         /* admitted requests at once (default 16)               */
     int32_t steps_per_turn;     /* time steps issued per request per turn (default 8)   */
-    int32_t snap_slots;         /* checkpoints per gradient request (default 64)        */
+    int32_t snap_slots;         /* checkpoint budget per gradient request, in pairs
+                                   (default 64; slots holding u^n alone take half)      */
     int32_t nb;                 /* sponge width (default 20)                            */
 } fwi_serve_opts;
 
