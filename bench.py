@@ -294,11 +294,12 @@ def serving_section(dev, n_req, seed=4, rates=(0.8,)):
                         "half forward / half gradient (BF16 checkpoints), 8th order"}
 
 
-def batched_section(dev, nt=3000, budget_gb=192.0):
+def batched_section(dev, nt=3000, budget_gb=224.0):
     """64 shots of the 400 x 1024 faulted 2-D model: one batched gradient call (shots on
     the grid's z launch dimension, FP64 gradient sum over shots) against 64 one-shot
     calls of the same kernels.  With the default checkpoint budget every step's u^n fits
-    (2999 BF16 checkpoints of 60 MB), so the forward recursion runs once."""
+    (BF16 checkpoints of 60 MB, 180 GB for 3000 steps), so the forward recursion runs
+    once."""
     import torch
 
     from paper_1912_08063_gb300 import fwi, synth
