@@ -160,3 +160,12 @@ def test_checkpoint_plan_forward_steps_fall_with_budget():
         assert prev is None or nf <= prev
         prev = nf
     assert prev == 4000
+
+
+@pytest.mark.parametrize("nsteps,pairs", [(500, 64), (3000, 64), (4000, 306), (4000, 20), (90, 8)])
+def test_checkpoint_plan_never_worse_than_pair_slots(nsteps, pairs):
+    """A budget of `pairs` pair-sized slots (2 * pairs units): sizing slots by what they
+    hold gives at least as many slots and no more forward steps than pair slots alone."""
+    slots, npair, nf = fwi.fwi_checkpoint_plan(nsteps, 2 * pairs)
+    _, nf_pairs = fwi.fwi_revolve_schedule(nsteps, min(pairs, nsteps))
+    assert slots >= min(pairs, nsteps) and nf <= nf_pairs
