@@ -70,8 +70,9 @@ typedef struct {
                                    the call then waits for its stream at the end        */
     int32_t temporal_blocking;  /* 1: 2-D forward calls whose shots fill the GPU advance
                                    two time steps per pass (same results bit for bit;
-                                   measured at parity with single steps on GB300, 3 %
-                                   slower, see the design notes); default 0             */
+                                   measured on GB300 within 3 % of single steps: the
+                                   2-D step is latency-bound, so halving its DRAM bytes
+                                   buys nothing); default 0                             */
 } fwi_opts;
 
 /* Acquisition geometry of one call: shot s has one source and nrec receivers, each a
@@ -146,8 +147,9 @@ int fwi_forward(fwi_model *m, const fwi_acq *acq, const float *wavelets, float *
 
 /* Misfit (Eq. 1, summed over shots, no 1/2) and its gradient with respect to the
  * physical velocity grid, by the exact discrete adjoint of the forward scheme and the
- * zero-lag imaging condition (gradient named in Sec. 1; derivation in the library's
- * design notes).  Checkpointing: binomial (revolve) schedule over nt with as many
+ * zero-lag imaging condition (gradient named in Sec. 1; the reverse recursion is the
+ * transpose of the discrete forward one, so the gradient is exact for the discrete
+ * misfit).  Checkpointing: binomial (revolve) schedule over nt with as many
  * checkpoints per shot as snap_budget_bytes allows (fwi_checkpoint_plan: a checkpoint is
  * u^n alone when it only ever feeds reverse steps, else the pair u^n, u^n - u^{n-1}, and
  * slots are sized by what they hold; when u^n of every step fits, nothing is
