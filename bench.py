@@ -187,6 +187,7 @@ def cpu_baseline(w, sample_n=320, sample_nt=30):
     import oracle
     n = w.shape[0]
     sample_n = min(sample_n, n)
+    sample_nt = min(sample_nt, w.nt)
     c0 = (n - sample_n) // 2
     sl = slice(c0, c0 + sample_n)
     v = np.ascontiguousarray(w.v[sl, sl, sl], dtype=np.float64)

@@ -54,3 +54,25 @@ def test_reference_arm_other_ranks_exit_quietly(capsys, monkeypatch):
     monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--gpus", "2"])
     bench.run_reference(bench.parse())
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_json_line(capsys, monkeypatch):
+    """Rank 0 of the reference arm times the oracle on a bounded sample and prints one
+    JSON line with the contract's keys (here on a 48^3 twin for speed)."""
+    import json
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--n", "48", "--nt", "6",
+                                     "--steps", "1", "--warmup", "0"])
+    bench.run_reference(bench.parse())
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"]
+    assert line["metric"] == "Gpts/s fwd+adjoint" and line["unit"] == "Gpts/s"
+    assert line["config"]["workload"].startswith("salt_3d")
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
