@@ -383,3 +383,33 @@ def test_anisotropic_spacing_3d(order):
     e_g = rel(g.cpu().numpy(), p.gradient(dobs.astype(np.float64))[1])
     print(f"anisotropic 3-D o{order}: traces {e_tr:.2e}, gradient {e_g:.2e}")
     assert e_tr <= TOL_FWD and e_g <= TOL_GRAD32
+
+
+def test_model_reuse_across_checkpoint_layouts():
+    """One model, one budget, calls whose checkpoint layouts differ: 1 shot fits u^n of
+    every step (store-all, one field per slot), 2 shots do not (recomputation, pair slots
+    among them).  The pool is re-zeroed when its layout changes, so every call equals the
+    same call on a fresh model bit for bit."""
+    w, dobs = _grad_case(2, (40, 52), 8, nt=90, f0=10.0, nshots=2)
+    probe, _, _ = make_pair(w, snap="bf16", budget=1)
+    pitch, comp = probe.info()["pitch_x"], probe.info()["computed"]
+    field = -(-comp[0] * comp[1] * pitch // 64) * 64
+    budget = (w.nt - 1) * field * 2
+    f = fwi()
+    wav = torch.from_numpy(w.wavelets()).cuda()
+    d = torch.from_numpy(dobs).cuda()
+    acq2 = f.Acquisition(w.src, w.rec)
+    acq1 = f.Acquisition(w.src[:1], w.rec)
+
+    def fresh(acq, ns):
+        m, _, _ = make_pair(w, snap="bf16", budget=budget)
+        return m.gradient(acq, wav[:ns], d[:ns])[1]
+
+    m, _, _ = make_pair(w, snap="bf16", budget=budget)
+    g1a = m.gradient(acq1, wav[:1], d[:1])[1]
+    assert m.info()["last_forward_steps"] == w.nt          # store-all
+    g2 = m.gradient(acq2, wav, d)[1]
+    assert m.info()["last_forward_steps"] > w.nt           # recomputation
+    g1b = m.gradient(acq1, wav[:1], d[:1])[1]
+    assert torch.equal(g1a, g1b)
+    assert torch.equal(g1a, fresh(acq1, 1)) and torch.equal(g2, fresh(acq2, 2))
