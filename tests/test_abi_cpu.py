@@ -169,3 +169,23 @@ def test_checkpoint_plan_never_worse_than_pair_slots(nsteps, pairs):
     slots, npair, nf = fwi.fwi_checkpoint_plan(nsteps, 2 * pairs)
     _, nf_pairs = fwi.fwi_revolve_schedule(nsteps, min(pairs, nsteps))
     assert slots >= min(pairs, nsteps) and nf <= nf_pairs
+
+
+def test_host_functions_reject_bad_arguments():
+    """Host-only entry points return FWI_ERR_ARG with a message for arguments outside their
+    domain, and never touch the device."""
+    with pytest.raises(fwi.FwiError) as e:
+        fwi.fwi_revolve_schedule(0, 5)
+    assert e.value.code == fwi.FWI_ERR_ARG and "nsteps" in fwi.fwi_last_error()
+    with pytest.raises(fwi.FwiError) as e:
+        fwi.fwi_checkpoint_plan(0, 10)
+    assert e.value.code == fwi.FWI_ERR_ARG
+    with pytest.raises(fwi.FwiError) as e:
+        fwi.fwi_checkpoint_plan(10, -1)
+    assert e.value.code == fwi.FWI_ERR_ARG
+    for order in (0, 7, 40):
+        with pytest.raises(fwi.FwiError) as e:
+            fwi.fwi_fd_coeffs(order)
+        assert e.value.code == fwi.FWI_ERR_ARG
+    assert fwi.fwi_cfl_number(4, 8, (10.0, 10.0, 10.0), 3000.0, 1e-3) < 0      # bad ndim
+    assert fwi.fwi_cfl_number(3, 9, (10.0, 10.0, 10.0), 3000.0, 1e-3) < 0      # odd order
