@@ -100,3 +100,23 @@ def test_fwi_on_a_reduced_faulted_model_follows_the_oracle():
     assert np.allclose(hist, hist_o, rtol=1e-2, atol=0)
     du, du_o = r["v"] - v0, v_o - v0
     assert np.linalg.norm(du - du_o) <= 2e-2 * np.linalg.norm(du_o)
+
+
+def test_descend_respects_the_box_and_the_mask():
+    """Cells the mask zeroes never move; cells pushed against a bound stay on it (the
+    projected direction leaves them out), and the loop still lowers phi."""
+    rng = np.random.default_rng(3)
+    n = 40
+    vstar = rng.uniform(1000.0, 5000.0, n)          # some minimisers lie outside the box
+    f = lambda v: (float(np.sum((v - vstar) ** 2)), 2.0 * (v - vstar))
+    mask = np.ones(n)
+    mask[:5] = 0.0
+    v0 = np.full(n, 3000.0)
+    v, hist = invert.descend(v0, f, iters=100, max_dv=300.0, mask=mask)
+    assert np.array_equal(v[:5], v0[:5])
+    assert v.min() >= 1500.0 and v.max() <= 4500.0
+    low, high = vstar[5:] < 1500.0, vstar[5:] > 4500.0
+    assert np.allclose(v[5:][low], 1500.0) and np.allclose(v[5:][high], 4500.0)
+    inside = ~(low | high)
+    assert np.allclose(v[5:][inside], vstar[5:][inside], atol=1.0)
+    assert hist[-1] < hist[0] and all(b <= a for a, b in zip(hist, hist[1:]))
