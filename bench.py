@@ -17,8 +17,12 @@ bounded sample of the same workload (rank 0 only).
 
 Besides the contract's keys the line carries: ``roofline.kernels`` (each 3-D step
 instantiation's launches, average CUDA-event time, algorithmic bytes per point, achieved
-GB/s and recorded DRAM traffic per launch; ``roofline`` itself is the one with the most
-device time), ``serving`` (a Poisson stream of mixed 2-D/3-D forward/gradient requests
+GB/s, fraction of the measured peak and recorded DRAM traffic per launch; ``roofline``
+itself is the one with the most device time, with ``min_frac`` (the slowest kernel) and
+``time_weighted_frac`` (all step kernels' algorithmic bytes over their device time)
+beside it), ``layered_3d_256`` (the 256^3 layered model at 8th order with BF16
+checkpoints: gradient rate, each step kernel's GB/s, and the forward step's cost per
+point and step at order 8 against the headline workload's order 16), ``serving`` (a Poisson stream of mixed 2-D/3-D forward/gradient requests
 through the continuous-batching loop against one request at a time: shots/s, p50/p99
 latency) and ``batched_2d`` (64 shots of the 400 x 1024 faulted model in one gradient
 call against 64 one-shot calls, with the step kernels' times, and the forward-only rate
@@ -66,6 +70,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-layered", action="store_true")
+    ap.add_argument("--layered-nt", type=int, default=2000,
+                    help="time steps of the 256^3 layered section (shorter for profiling)")
     ap.add_argument("--serving-requests", type=int, default=32)
     ap.add_argument("--serving-rates", default="0.8",
                     help="comma-separated fractions of the batched capacity for Poisson arrivals")
@@ -380,6 +387,85 @@ def batched_section(dev, nt=3000, budget_gb=224.0):
             "seconds": round(tb, 3), "seconds_per_shot_calls": round(t1, 3), "kernels": kern}
 
 
+def kernel_stats(info0, info1, npts, peak, traffic=True):
+    """Per 3-D step instantiation between two fwi_model_info snapshots: launches, average
+    CUDA-event time, algorithmic bytes per point, achieved GB/s and its fraction of the
+    peak; plus the minimum fraction and the time-weighted one (all kernels' algorithmic
+    bytes over their summed device time)."""
+    kern = {}
+    tot_bytes = tot_s = 0.0
+    for key, nkey, mkey, bpp in (("fwd_step_3d", "fwd_step_launches", "fwd_step_ms", BYTES_FWD),
+                                 ("store_step_3d", "store_step_launches", "store_step_ms", BYTES_STORE),
+                                 ("adj_step_3d", "adj_step_launches", "adj_step_ms", BYTES_ADJ)):
+        n = info1[nkey] - info0[nkey]
+        tot = info1[mkey] - info0[mkey]
+        avg = tot / n if n else 0.0
+        gbs = bpp * npts / (avg * 1e-3) / 1e9 if n else None
+        kern[key] = {"launches": n, "total_ms": tot, "avg_ms": avg, "bytes_per_point": bpp,
+                     "GB/s": gbs, "frac": round(gbs / peak, 4) if n else None,
+                     "traffic": recorded_traffic(key) if traffic else None}
+        if n:
+            tot_bytes += bpp * npts * n
+            tot_s += tot * 1e-3
+    fr = [k["frac"] for k in kern.values() if k["frac"] is not None]
+    summary = {"min_frac": min(fr) if fr else None,
+               "time_weighted_frac": round(tot_bytes / tot_s / 1e9 / peak, 4) if tot_s else None}
+    return kern, summary
+
+
+def layered_section(dev, nt=2000, budget_gb=224.0, peak=None, k1_order16=None):
+    """The 256^3 layered model with Gaussian random perturbations (8th order, dt 0.8 ms,
+    BF16 checkpoints, 128 x 128 receivers): one misfit gradient, timed after a warm-up,
+    with each step kernel's achieved bandwidth; then the forward step alone, whose cost
+    per point and step sets, against the 16th-order step of the headline workload, the
+    GPU side of the order trade-off (Sec. 4, Fig. 6)."""
+    import torch
+
+    from paper_1912_08063_gb300 import fwi
+
+    w = workload("layered_3d_256", nt)
+    acq = fwi.Acquisition(w.src, w.rec)
+    wav = torch.from_numpy(w.wavelets()).to(dev)
+    obs = fwi.FwiModel(torch.from_numpy(w.v_obs).to(dev), w.h, w.dt, w.nt, order=w.order,
+                       nb=w.nb, sponge_vref=4500.0)
+    dobs = obs.forward(acq, wav)
+    obs.close()
+    m = fwi.FwiModel(torch.from_numpy(w.v).to(dev), w.h, w.dt, w.nt, order=w.order, nb=w.nb,
+                     snap_dtype=w.snap_dtype, snap_budget_bytes=int(budget_gb * 2 ** 30),
+                     sponge_vref=4500.0, timing=True)
+    m.gradient(acq, wav, dobs)   # warm-up
+    torch.cuda.synchronize()
+    i0 = m.info()
+    t0 = time.perf_counter()
+    m.gradient(acq, wav, dobs)
+    torch.cuda.synchronize()
+    tg = time.perf_counter() - t0
+    i1 = m.info()
+    pts = i1["points"]
+    kern, summ = kernel_stats(i0, i1, pts * w.nshots, peak, traffic=False)
+    # forward only: the plain step's cost per point and step at order 8
+    i2 = m.info()
+    m.forward(acq, wav)
+    torch.cuda.synchronize()
+    i3 = m.info()
+    m.close()
+    nf = i3["fwd_step_launches"] - i2["fwd_step_launches"]
+    f_ms = (i3["fwd_step_ms"] - i2["fwd_step_ms"]) / max(nf, 1)
+    ps8 = f_ms * 1e9 / (pts * w.nshots)
+    trade = {"fwd_ps_per_point_step_order8": round(ps8, 4)}
+    if k1_order16:
+        ms16, pts16 = k1_order16
+        ps16 = ms16 * 1e9 / pts16
+        trade.update({"fwd_ps_per_point_step_order16": round(ps16, 4),
+                      "order16_over_order8": round(ps16 / ps8, 4)})
+    return {"workload": w.name, "grid": list(w.shape), "computed_points": pts,
+            "order": w.order, "nt": w.nt, "checkpoints": w.snap_dtype,
+            "checkpoint_slots": i1["snap_slots"],
+            "forward_steps_per_gradient": i1["last_forward_steps"],
+            "seconds": round(tg, 4), "gpts_per_s": round(gpts_per_s(pts * w.nshots, w.nt, tg), 2),
+            "kernels": kern, **summ, "order_tradeoff": trade}
+
+
 def replica_rate(ms_local, units_local, world, dist=None, device="cpu"):
     """Whole-job timing of N independent replicas: the step time is the maximum over
     ranks, the rate the units all ranks processed per second of that time.  Returns
@@ -481,18 +567,10 @@ def main():
     ms, rate = replica_rate(ms_local, units, world, dist, dev)
     value = rate / 1e9   # Gpts/s over all ranks
     peak, peak_kind = measured_hbm()
-    kern = {}
-    for key, nkey, mkey, bpp in (("fwd_step_3d", "fwd_step_launches", "fwd_step_ms", BYTES_FWD),
-                                 ("store_step_3d", "store_step_launches", "store_step_ms", BYTES_STORE),
-                                 ("adj_step_3d", "adj_step_launches", "adj_step_ms", BYTES_ADJ)):
-        n = info1[nkey] - info0[nkey]
-        tot = info1[mkey] - info0[mkey]
-        avg = tot / n if n else 0.0
-        kern[key] = {"launches": n, "total_ms": tot, "avg_ms": avg, "bytes_per_point": bpp,
-                     "GB/s": bpp * pts * w.nshots / (avg * 1e-3) / 1e9 if n else None,
-                     "traffic": recorded_traffic(key)}
+    kern, summ = kernel_stats(info0, info1, pts * w.nshots, peak)
     launches = (info1["kernel_launches"] - info0["kernel_launches"])
-    # the dominant kernel: the largest share of the step's device time
+    # the dominant kernel: the largest share of the step's device time; the slowest
+    # kernel's fraction and the time-weighted one stand beside it
     kname = max(kern, key=lambda k: kern[k]["total_ms"])
     kd = kern[kname]
     achieved = kd["GB/s"] or 0.0
@@ -500,7 +578,7 @@ def main():
             "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
             "traffic": kd["traffic"],
             "algorithmic_bytes_per_launch": kd["bytes_per_point"] * pts * w.nshots,
-            "kernels": kern}
+            **summ, "kernels": kern}
 
     # end to end through the C ABI with pinned host buffers, copies inside the timing
     e2e = None
@@ -534,7 +612,11 @@ def main():
 
     # the other two workloads of the metric, measured after the timed region
     model.close()
-    serving = batched = None
+    serving = batched = layered = None
+    if rank == 0 and not args.no_layered and args.workload == "salt_3d_512":
+        k1 = kern["fwd_step_3d"]
+        layered = layered_section(dev, args.layered_nt, args.snap_budget_gb, peak,
+                                  (k1["avg_ms"], pts * w.nshots) if k1["launches"] else None)
     if rank == 0 and not args.no_serving:
         serving = serving_section(dev, args.serving_requests,
                                   rates=tuple(float(x) for x in args.serving_rates.split(",")))
@@ -556,7 +638,7 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "clocks": ck, "e2e": e2e, "gpu_launches": launches,
                 "roofline": roof, "cpu_baseline": cpu, "misfit": float(phi.item()),
-                "serving": serving, "batched_2d": batched}
+                "layered_3d_256": layered, "serving": serving, "batched_2d": batched}
         print(json.dumps(line), flush=True)
     model.close()
     if world > 1:

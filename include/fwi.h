@@ -297,6 +297,18 @@ typedef struct {
 int fwi_serve(const fwi_request *reqs, int32_t n, const fwi_serve_opts *opts,
               fwi_result *results);
 
+/* Failure-path self-test of the bounded device waits (no counterpart in the paper; the
+ * waits guard the TMA-staged 3-D step kernels).  Launches, on `stream`, one CTA that arms
+ * an mbarrier the way the step kernels' producer does (an arrival with an expected
+ * transaction count), issues no copy, and waits with the step kernels' bounded wait
+ * limited to `polls` polls (1 <= polls <= 2^22).  The wait runs out and raises the model's
+ * latched timeout status exactly as a step kernel whose data never arrived would: the
+ * next fwi_sync_status returns FWI_ERR_TIMEOUT, and every later call on this model
+ * returns it too (the status stays latched; create a new model to continue).  No copy is
+ * in flight, so nothing faults and nothing waits without bound.  Returns FWI_ERR_ARG for
+ * polls out of range, FWI_ERR_CUDA if the launch fails. */
+int fwi_selftest_wait(fwi_model *m, int32_t polls, cudaStream_t stream);
+
 /* Waits for the model's last stream and returns its latched device status. */
 int fwi_sync_status(fwi_model *m);
 

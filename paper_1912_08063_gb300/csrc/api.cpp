@@ -192,7 +192,7 @@ struct fwi_model {
         CUtensorMap map;
     };
     std::vector<MapEntry> maps;
-    int resident = 0;   // resident CTAs of the 3-D step kernel
+    int resident[3] = {0, 0, 0};   // resident CTAs of the 3-D step kernel, per mode
     int64_t t_fwd_n = 0, t_adj_n = 0, t_st_n = 0;
     double t_fwd_ms = 0.0, t_adj_ms = 0.0, t_st_ms = 0.0;
 
@@ -532,6 +532,14 @@ int field_map(fwi_model *m, const void *base, int ns, int bx, int by, CUtensorMa
     return FWI_OK;
 }
 
+// Resident CTAs of each 3-D step mode, queried once per model (outside any capture).
+void ensure_resident(fwi_model *m)
+{
+    const bool iso = m->h[0] == m->h[1] && m->h[1] == m->h[2];
+    for (int mode = 0; mode < 3; ++mode)
+        if (m->resident[mode] <= 0) m->resident[mode] = step3d_resident_ctas(m->g.M, mode, iso);
+}
+
 // One launch of the TMA-staged 3-D kernel (k_step3d.cu) in `mode`.
 int step3d_launch(fwi_model *m, const StepParams &p, int ns, int mode, cudaStream_t s)
 {
@@ -588,10 +596,10 @@ int step3d_launch(fwi_model *m, const StepParams &p, int ns, int mode, cudaStrea
         q.aux_fmt = p.aux_fmt;
         q.aux_scale = p.aux_scale;
     }
-    if (m->resident <= 0) m->resident = step3d_resident_ctas(g.M);
+    ensure_resident(m);
     const int tiles = ((g.nx + 63) / 64) * ((g.ny + TY - 1) / TY);
     q.nshots = ns;
-    const int ctas = plan_persistent(q, tiles * ns, m->resident);
+    const int ctas = plan_persistent(q, tiles * ns, m->resident[mode]);
     FWI_CU(launch_step3d_tma(q, mode, ctas, mc, ma, mb, md, me, s));
     return FWI_OK;
 }
@@ -776,7 +784,7 @@ int fwd_capture(FwdJob &j, int units)
         j.gexec = nullptr;
     }
     FWI_TRY(m->step_ctr.ensure(sizeof(int)));
-    if (use_step3d(m) && m->resident <= 0) m->resident = step3d_resident_ctas(m->g.M);
+    if (use_step3d(m)) ensure_resident(m);
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(j.s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
@@ -918,7 +926,7 @@ int grad_capture(GradJob &j, int par, bool rec)
 {
     fwi_model *m = j.m;
     FWI_TRY(m->step_ctr.ensure(sizeof(int)));
-    if (use_step3d(m) && m->resident <= 0) m->resident = step3d_resident_ctas(m->g.M);
+    if (use_step3d(m)) ensure_resident(m);
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(j.s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
@@ -1743,6 +1751,16 @@ int fwi_model_info(const fwi_model *m, fwi_info *o)
     o->adj_step_ms = m->t_adj_ms;
     o->store_step_launches = m->t_st_n;
     o->store_step_ms = m->t_st_ms;
+    return FWI_OK;
+}
+
+int fwi_selftest_wait(fwi_model *m, int32_t polls, cudaStream_t s)
+{
+    if (!m) return fail(FWI_ERR_ARG, "null argument");
+    if (polls < 1 || polls > (1 << 22))
+        return fail(FWI_ERR_ARG, "fwi_selftest_wait: polls must lie in [1, 2^22]");
+    m->last_stream = s;
+    FWI_LAUNCH(m, launch_wait_selftest(m->d_flag, polls, s));
     return FWI_OK;
 }
 

@@ -169,6 +169,10 @@ cudaError_t launch_fold(float *g32, double *g64, int64_t n, cudaStream_t s);
 cudaError_t launch_finish(const Geom &g, int nb, const int64_t np[3], int nshots,
                           const double *g64, const float *v, float *grad32, double *grad64,
                           cudaStream_t s);
+// One CTA that arms an mbarrier with an expected byte count, issues no copy and waits with
+// the step kernels' bounded wait limited to `polls`; raises bit 1 of *err when it runs
+// out (k_selftest.cu)
+cudaError_t launch_wait_selftest(unsigned *err, int polls, cudaStream_t s);
 cudaError_t launch_nonfinite_check(const float *a, int64_t n, unsigned *flag,
                                    cudaStream_t s);
 

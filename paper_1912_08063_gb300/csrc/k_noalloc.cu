@@ -11,11 +11,15 @@
 // holds it (32 KB) until the process exits.  Host code cannot pass the variable's name
 // to a kernel (on the host it is only a stand-in, not a device address), so the first
 // call on each device looks up the array's device address with cudaGetSymbolAddress,
-// with that device current, and caches it; that first call should therefore come before
-// any stream capture.  Every call shares the one array and overwrites the partials it
-// uses (no clearing is needed: each partial is written before it is read), so calls
-// that overlap on the GPU — on two streams of the same device — race and must be
-// ordered by the caller.
+// with that device current, and caches it per (device, context); that first call should
+// therefore come before any stream capture.  A cudaDeviceReset creates a new context on
+// its next use, in which the module and its array are loaded again at another address:
+// the first call in the new context looks the address up again.  Every call shares the
+// one array and overwrites the partials it uses (no clearing is needed: each partial is
+// written before it is read), so calls that overlap on the GPU — on two streams of the
+// same device — race and must be ordered by the caller.
+#include <cudaTypedefs.h>
+
 #include <mutex>
 #include <string>
 
@@ -37,6 +41,27 @@ static __device__ __align__(256) double g_misfit_partials[kMaxPartials];
 
 std::mutex g_mutex;
 double *g_partials_addr[kMaxDevices] = {};
+CUcontext g_partials_ctx[kMaxDevices] = {};
+
+// The current driver context (through the runtime's driver entry point, so the library
+// needs no libcuda link); null when it cannot be queried.
+CUcontext current_context()
+{
+    static PFN_cuCtxGetCurrent_v4000 get = nullptr;
+    if (!get) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !f) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        get = (PFN_cuCtxGetCurrent_v4000)f;
+    }
+    CUcontext c = nullptr;
+    return get(&c) == CUDA_SUCCESS ? c : nullptr;
+}
 
 __device__ double block_sum(double v)
 {
@@ -80,7 +105,8 @@ __global__ void k_total(const double *__restrict__ part, int nb, double *__restr
     if (threadIdx.x == 0) out[0] = t;
 }
 
-// Device address of the partials array on the current device (looked up once per device).
+// Device address of the partials array on the current device (looked up once per device
+// and context).
 int partials_address(double **out)
 {
     int dev = 0;
@@ -89,14 +115,18 @@ int partials_address(double **out)
         return fwi::report_error(FWI_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices)
         return fwi::report_error(FWI_ERR_ARG, "device ordinal beyond the supported 64");
+    // cudaGetSymbolAddress below makes the device's primary context current if none is,
+    // so the context is read after it when the cache is empty
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_partials_addr[dev]) {
+    const CUcontext ctx = current_context();
+    if (!g_partials_addr[dev] || !ctx || ctx != g_partials_ctx[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_misfit_partials);
         if (e != cudaSuccess || !p)
             return fwi::report_error(FWI_ERR_CUDA, std::string("cudaGetSymbolAddress: ") +
                                                        cudaGetErrorString(e));
         g_partials_addr[dev] = (double *)p;
+        g_partials_ctx[dev] = ctx ? ctx : current_context();
     }
     *out = g_partials_addr[dev];
     return FWI_OK;
@@ -118,11 +148,20 @@ extern "C" int fwi_misfit_noalloc(const float *d_mod, const float *d_obs, int64_
     const int rc = partials_address(&part);
     if (rc != FWI_OK) return rc;
     const int nb = (int)((n + kChunk - 1) / kChunk);
-    if (nb > 0) k_partials<<<nb, kThreads, 0, stream>>>(d_mod, d_obs, n, part);
+    // each launch is checked on its own, so the total never runs after a failed partials
+    // launch (an error already pending from earlier, unrelated work is reported here too:
+    // the runtime keeps one last-error slot per thread)
+    if (nb > 0) {
+        k_partials<<<nb, kThreads, 0, stream>>>(d_mod, d_obs, n, part);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return fwi::report_error(FWI_ERR_CUDA, std::string("fwi_misfit_noalloc (partials): ") +
+                                                       cudaGetErrorString(e));
+    }
     k_total<<<1, kThreads, 0, stream>>>(part, nb, misfit_dev);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
-        return fwi::report_error(FWI_ERR_CUDA, std::string("fwi_misfit_noalloc: ") +
+        return fwi::report_error(FWI_ERR_CUDA, std::string("fwi_misfit_noalloc (total): ") +
                                                    cudaGetErrorString(e));
     return FWI_OK;
 }

@@ -41,12 +41,25 @@ static Step3dKernelInfo kernel_info(int M, int mode, bool iso = false)
 int step3d_smem_bytes(int M) { return kernel_info(M, kModeStep).smem; }
 int step3d_threads(int M) { return kernel_info(M, kModeStep).threads; }
 
-int step3d_resident_ctas(int M)
+// Resident CTAs per SM need the kernel's largest shared-memory carveout: with the
+// driver's default preference a 101 KB reverse-step CTA at radius 4 may get a carveout
+// that holds only one of them, and the persistent grid, sized for two, would then run in
+// two waves.
+static cudaError_t prepare_kernel(const Step3dKernelInfo &k)
 {
-    const Step3dKernelInfo k = kernel_info(M, kModeStep);
+    cudaError_t e = cudaFuncSetAttribute((const void *)k.fn,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void *)k.fn,
+                                cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+}
+
+int step3d_resident_ctas(int M, int mode, bool iso)
+{
+    const Step3dKernelInfo k = kernel_info(M, mode, iso);
     if (!k.fn) return 152;
-    if (cudaFuncSetAttribute((const void *)k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             k.smem) != cudaSuccess) {
+    if (prepare_kernel(k) != cudaSuccess) {
         cudaGetLastError();
         return 152;
     }
@@ -68,8 +81,7 @@ cudaError_t launch_step3d_tma(const Step3dParams &p, int mode, int ctas,
 {
     const Step3dKernelInfo k = kernel_info(p.M, mode, p.iso != 0);
     if (!k.fn) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute((const void *)k.fn,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem);
+    const cudaError_t e = prepare_kernel(k);
     if (e != cudaSuccess) return e;
     if (ctas < 1) return cudaErrorInvalidValue;
     k.fn<<<ctas, k.threads, k.smem, s>>>(p, mc, ma, mb, md, me);

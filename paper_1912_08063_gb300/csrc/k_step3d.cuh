@@ -88,10 +88,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: gives up after ~2^22 polls (each poll may suspend the thread briefly).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// Bounded wait: gives up after `limit` polls, ~2^22 by default (each poll may suspend the
+// thread briefly).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int limit = 1 << 22)
 {
-    for (int i = 0; i < (1 << 22); ++i)
+    for (int i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }

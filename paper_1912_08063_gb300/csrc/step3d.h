@@ -61,8 +61,9 @@ struct Step3dVariant {
 Step3dVariant step3d_variant(int M);
 int step3d_smem_bytes(int M);
 int step3d_threads(int M);
-// Resident CTAs of the 3-D step kernel on the current device (SMs x CTAs per SM).
-int step3d_resident_ctas(int M);
+// Resident CTAs of the 3-D step kernel of `mode` on the current device (SMs x CTAs per
+// SM), for the instantiation a launch on an isotropic (iso) or anisotropic grid uses.
+int step3d_resident_ctas(int M, int mode, bool iso);
 
 // map_c: 4-D [shot][z][y][x] map of the streamed field with the halo box;
 // map_a, map_b, map_d, map_e: maps of the pointwise fields prev, W, aux, g with the

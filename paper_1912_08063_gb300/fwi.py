@@ -108,6 +108,7 @@ def lib():
                 "fwi_model_info": ([P, P], c_i32),
                 "fwi_serve": ([P, c_i32, P, P], c_i32),
                 "fwi_sync_status": ([P], c_i32),
+                "fwi_selftest_wait": ([P, c_i32, P], c_i32),
                 "fwi_destroy": ([P], None),
                 "fwi_last_error": ([], ctypes.c_char_p),
             }
@@ -300,6 +301,10 @@ def fwi_serve(requests, budget_bytes=0, max_active=16, steps_per_turn=8, snap_sl
 
 def fwi_sync_status(model):
     _check(lib().fwi_sync_status(model))
+
+
+def fwi_selftest_wait(model, polls, stream=None):
+    _check(lib().fwi_selftest_wait(model, int(polls), _stream(stream)))
 
 
 def fwi_destroy(model):

@@ -120,3 +120,38 @@ def test_graph_replayed_gradient_equals_direct_call():
         m.close()
         assert x["misfit"] == phi.item()
         assert np.array_equal(np.asarray(o).reshape(g.shape), g.cpu().numpy())
+
+
+def test_served_results_match_the_oracle():
+    """One forward and one gradient request served in a mix with others, against the FP64
+    oracle on the same inputs: traces to 1e-4 and the BF16-checkpoint gradient to 1e-2
+    (relative L2), as for direct calls.  The observed traces of the gradient request come
+    from the oracle's forward run of the perturbed model."""
+    import oracle
+    from paper_1912_08063_gb300 import fwi
+    reqs = _requests(6, seed=11)
+    fwd = next(i for i, r in enumerate(reqs) if r["kind"] == "forward")
+    grd = next(i for i, r in enumerate(reqs) if r["kind"] == "gradient")
+
+    def problem(r, v):
+        return oracle.Problem(v, r["h"], r["dt"], r["nt"], order=8, nb=20,
+                              src=np.asarray(r["src"])[None], rec=r["rec"],
+                              wavelet=r["wavelet"][None])
+
+    rg = reqs[grd]
+    rg["d_obs"] = problem(rg, rg["v_obs"]).forward()[0].astype(np.float32)
+    for i, r in enumerate(reqs):
+        r["arrival"] = 0.001 * i
+    res, out = fwi.fwi_serve(reqs, max_active=6, steps_per_turn=4, snap_slots=6)
+    assert all(x["status"] == 0 for x in res), res
+    rf = reqs[fwd]
+    ref = problem(rf, rf["v"]).forward()[0]
+    e = _rel(np.asarray(out[fwd]).reshape(ref.shape), ref)
+    print(f"served forward ({rf['v'].ndim}-D {rf['v'].shape}, nt {rf['nt']}): rel-L2 {e:.2e}")
+    assert e <= 1e-4
+    phi, g = problem(rg, rg["v"]).gradient(rg["d_obs"][None].astype(np.float64))
+    eg = _rel(np.asarray(out[grd]).reshape(g.shape), g)
+    ephi = abs(res[grd]["misfit"] - phi) / phi
+    print(f"served gradient ({rg['v'].ndim}-D {rg['v'].shape}, nt {rg['nt']}, "
+          f"{rg['snap_dtype']}): rel-L2 {eg:.2e}, misfit {ephi:.2e}")
+    assert eg <= 1e-2 and ephi <= 1e-4

@@ -11,8 +11,15 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+# CUmemPool_attribute values (cuda.h)
+_RESERVED_MEM_CURRENT = 5
+_USED_MEM_CURRENT = 7
+_USED_MEM_HIGH = 8
 
 
 def _entry():
@@ -30,8 +37,9 @@ def test_noalloc_misfit_matches_misfit_on_two_calls_in_a_row():
     stream = torch.cuda.current_stream().cuda_stream
     # two calls in a row on different sizes: the second must not see the first's partials
     for n in (5_000_003, 70_001):
-        a = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).cuda()
-        b = torch.from_numpy((rng.standard_normal(n) * 0.3).astype(np.float32)).cuda()
+        a_h = rng.standard_normal(n).astype(np.float32)
+        b_h = (rng.standard_normal(n) * 0.3).astype(np.float32)
+        a, b = torch.from_numpy(a_h).cuda(), torch.from_numpy(b_h).cuda()
         ref = torch.zeros(1, dtype=torch.float64, device="cuda")
         fwi.fwi_misfit(a, b, n, ref)
         out = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
@@ -41,6 +49,10 @@ def test_noalloc_misfit_matches_misfit_on_two_calls_in_a_row():
         r, o = ref.item(), out.item()
         # same terms, different FP64 summation order: |error| <= n eps sum|terms|
         assert abs(o - r) <= n * 2.0 ** -52 * r, (o, r)
+        # and against the FP64 oracle on the FP32 residual the kernel forms (Eq. 1)
+        res = (a_h - b_h).astype(np.float64)
+        phi = oracle.misfit(res, np.zeros_like(res))
+        assert abs(o - phi) <= n * 2.0 ** -52 * phi, (o, phi)
 
 
 def test_noalloc_misfit_rejects_sizes_beyond_its_array():
@@ -52,3 +64,57 @@ def test_noalloc_misfit_rejects_sizes_beyond_its_array():
            torch.cuda.current_stream().cuda_stream)
     assert rc == fwi.FWI_ERR_ARG
     assert "exceeds the maximum" in fwi.fwi_last_error()
+
+
+class _Pool:
+    """The device's default memory pool (the one stream-ordered allocation draws from),
+    read through the driver API."""
+
+    def __init__(self, ordinal):
+        cu = ctypes.CDLL("libcuda.so.1")
+        dev = ctypes.c_int(0)
+        assert cu.cuDeviceGet(ctypes.byref(dev), ctypes.c_int(ordinal)) == 0
+        self.pool = ctypes.c_void_p(0)
+        assert cu.cuDeviceGetDefaultMemPool(ctypes.byref(self.pool), dev) == 0
+        self.cu = cu
+
+    def get(self, attr):
+        v = ctypes.c_uint64(0)
+        assert self.cu.cuMemPoolGetAttribute(self.pool, ctypes.c_int(attr), ctypes.byref(v)) == 0
+        return v.value
+
+    def reset_high(self):
+        zero = ctypes.c_uint64(0)   # resets the high watermark to the current value
+        assert self.cu.cuMemPoolSetAttribute(self.pool, ctypes.c_int(_USED_MEM_HIGH),
+                                             ctypes.byref(zero)) == 0
+
+
+def test_noalloc_misfit_allocates_nothing():
+    fwi, f = _entry()
+    n = 3_000_017
+    rng = np.random.default_rng(78)
+    a = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).cuda()
+    b = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).cuda()
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    assert f(a.data_ptr(), b.data_ptr(), n, out.data_ptr(), stream) == 0   # set-up call
+    torch.cuda.synchronize()
+    pool = _Pool(torch.cuda.current_device())
+
+    def watch(call):
+        torch.cuda.synchronize()
+        pool.reset_high()
+        used0, res0 = pool.get(_USED_MEM_CURRENT), pool.get(_RESERVED_MEM_CURRENT)
+        free0 = torch.cuda.mem_get_info()[0]
+        call()
+        torch.cuda.synchronize()
+        return (pool.get(_USED_MEM_HIGH) - used0, pool.get(_RESERVED_MEM_CURRENT) - res0,
+                free0 - torch.cuda.mem_get_info()[0])
+
+    # control: the allocating entry point does raise the pool's high watermark
+    ctl = watch(lambda: fwi.fwi_misfit(a, b, n, out))
+    assert ctl[0] > 0, ctl
+    for _ in range(2):
+        d_high, d_res, d_free = watch(
+            lambda: f(a.data_ptr(), b.data_ptr(), n, out.data_ptr(), stream))
+        assert (d_high, d_res, d_free) == (0, 0, 0)
