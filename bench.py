@@ -462,6 +462,7 @@ def layered_section(dev, nt=2000, budget_gb=224.0, peak=None, k1_order16=None):
             "order": w.order, "nt": w.nt, "checkpoints": w.snap_dtype,
             "checkpoint_slots": i1["snap_slots"],
             "forward_steps_per_gradient": i1["last_forward_steps"],
+            "step_ctas_fwd_adj_store": i1["step_ctas"],
             "seconds": round(tg, 4), "gpts_per_s": round(gpts_per_s(pts * w.nshots, w.nt, tg), 2),
             "kernels": kern, **summ, "order_tradeoff": trade}
 
@@ -634,6 +635,7 @@ def main():
                            "checkpoint_slots": info1["snap_slots"],
                            "forward_steps_per_gradient": info1["last_forward_steps"],
                            "adjoint_steps_per_gradient": info1["last_adjoint_steps"],
+                           "step_ctas_fwd_adj_store": info1["step_ctas"],
                            "l2": "inputs larger than L2 (each field >= 100 MB)",
                            "parallelism": f"replicas x{world}"},
                 "clocks": ck, "e2e": e2e, "gpu_launches": launches,

@@ -120,6 +120,12 @@ typedef struct {
     double  adj_step_ms;
     int64_t store_step_launches; /* timed forward steps that also wrote a checkpoint    */
     double  store_step_ms;
+    int32_t step_ctas[3];       /* 3-D models: CTAs of one persistent step launch in the
+                                   forward, reverse and forward+store modes (SMs x CTAs
+                                   resident per SM); 0 before the first 3-D step, and
+                                   -e when the occupancy query failed with CUDA error e
+                                   (the launch then uses one CTA per SM)                */
+    int32_t reserved2;
 } fwi_info;
 
 /* Creates a model: the velocity grid v (physical, [nz][ny][nx] FP32, host or device,

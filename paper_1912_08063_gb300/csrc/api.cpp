@@ -193,6 +193,7 @@ struct fwi_model {
     };
     std::vector<MapEntry> maps;
     int resident[3] = {0, 0, 0};   // resident CTAs of the 3-D step kernel, per mode
+    int resident_query[3] = {0, 0, 0};   // what the occupancy query returned (-e: error e)
     int64_t t_fwd_n = 0, t_adj_n = 0, t_st_n = 0;
     double t_fwd_ms = 0.0, t_adj_ms = 0.0, t_st_ms = 0.0;
 
@@ -536,8 +537,21 @@ int field_map(fwi_model *m, const void *base, int ns, int bx, int by, CUtensorMa
 void ensure_resident(fwi_model *m)
 {
     const bool iso = m->h[0] == m->h[1] && m->h[1] == m->h[2];
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        sms = 152;
+    }
     for (int mode = 0; mode < 3; ++mode)
-        if (m->resident[mode] <= 0) m->resident[mode] = step3d_resident_ctas(m->g.M, mode, iso);
+        if (m->resident[mode] <= 0) {
+            const int r = step3d_resident_ctas(m->g.M, mode, iso);
+            m->resident_query[mode] = r;
+            m->resident[mode] = r > 0 ? r : sms;   // one CTA per SM if the query failed
+            // tuning runs: FWI_STEP3D_PER_SM=<k> plans k CTAs per SM instead
+            if (const char *e = std::getenv("FWI_STEP3D_PER_SM"))
+                if (std::atoi(e) > 0) m->resident[mode] = sms * std::atoi(e);
+        }
 }
 
 // One launch of the TMA-staged 3-D kernel (k_step3d.cu) in `mode`.
@@ -599,7 +613,9 @@ int step3d_launch(fwi_model *m, const StepParams &p, int ns, int mode, cudaStrea
     ensure_resident(m);
     const int tiles = ((g.nx + 63) / 64) * ((g.ny + TY - 1) / TY);
     q.nshots = ns;
-    const int ctas = plan_persistent(q, tiles * ns, m->resident[mode]);
+    // z-parts in step when the streamed field is larger than the L2 (~126 MB)
+    const bool in_step = (double)g.field * 4.0 * ns > 96.0 * (1 << 20);
+    const int ctas = plan_persistent(q, tiles * ns, m->resident[mode], in_step);
     FWI_CU(launch_step3d_tma(q, mode, ctas, mc, ma, mb, md, me, s));
     return FWI_OK;
 }
@@ -1751,6 +1767,13 @@ int fwi_model_info(const fwi_model *m, fwi_info *o)
     o->adj_step_ms = m->t_adj_ms;
     o->store_step_launches = m->t_st_n;
     o->store_step_ms = m->t_st_ms;
+    // modes in the order forward, reverse, forward + store
+    const int mode_of[3] = {kModeStep, kModeAdj, kModeStepStore};
+    for (int k = 0; k < 3; ++k) {
+        const int q = m->resident_query[mode_of[k]];
+        o->step_ctas[k] = q < 0 ? q : m->resident[mode_of[k]];
+    }
+    o->reserved2 = 0;
     return FWI_OK;
 }
 

@@ -5,22 +5,28 @@
 #include <cstdlib>
 #include <cstring>
 
+#include <algorithm>
+
 #include "step3d.h"
 
 namespace fwi {
 
 // Configuration per radius; FWI_STEP3D_VARIANT=<ty>,<ry>,<pf>,<u>,<opt>[,<opt_rev>]
-// overrides it for tuning runs (only the instantiated combinations are accepted).  At
+// overrides it for tuning runs (only the instantiated combinations are accepted), and
+// FWI_STEP3D_TMEM=0/1 turns the tensor-memory kernel off/on at radius 8 (on by default:
+// measured faster in every mode on GB300).  At
 // radius 8 the queue shifts every 2 planes and all modes take the packed x-sums, as
 // measured fastest on GB300 (against U = 3 and scalar x-sums).
 Step3dVariant step3d_variant(int M)
 {
-    Step3dVariant v = M == 8 ? Step3dVariant{32, 2, 2, 2, 1, 1} : Step3dVariant{16, 2, 3, 2, 0, 0};
+    Step3dVariant v = M == 8 ? Step3dVariant{32, 2, 2, 2, 1, 1, 1} : Step3dVariant{16, 2, 3, 2, 0, 0, 0};
+    if (M == 8)
+        if (const char *e = std::getenv("FWI_STEP3D_TMEM")) v.tm = std::atoi(e) != 0;
     if (const char *e = std::getenv("FWI_STEP3D_VARIANT")) {
         int ty, ry, pf, un, opt, optr;
         const int n = std::sscanf(e, "%d,%d,%d,%d,%d,%d", &ty, &ry, &pf, &un, &opt, &optr);
         if (n == 5 || n == 6) {
-            Step3dVariant w{ty, ry, pf, un, opt, n == 6 ? optr : opt};
+            Step3dVariant w{ty, ry, pf, un, opt, n == 6 ? optr : opt, 0};
             bool ok = true;
             for (int mode = 0; mode < 3; ++mode)
                 ok = ok && (M == 8 ? step3d_kernel_m8(w, mode) : step3d_kernel_m4(w, mode)).fn;
@@ -58,20 +64,38 @@ static cudaError_t prepare_kernel(const Step3dKernelInfo &k)
 int step3d_resident_ctas(int M, int mode, bool iso)
 {
     const Step3dKernelInfo k = kernel_info(M, mode, iso);
-    if (!k.fn) return 152;
-    if (prepare_kernel(k) != cudaSuccess) {
-        cudaGetLastError();
-        return 152;
-    }
+    if (!k.fn) return -(int)cudaErrorInvalidDeviceFunction;
+    cudaError_t e = prepare_kernel(k);
     int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k.fn, k.threads,
-                                                      k.smem) != cudaSuccess || per < 1) {
-        cudaGetLastError();
-        per = 1;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && k.tmem_cols > 0) {
+        // kernels that allocate tensor memory: the occupancy query counts one CTA per SM
+        // for them (measured), while their registers, shared memory and columns admit
+        // more; count from those resources
+        cudaFuncAttributes a{};
+        int regs = 0, shm = 0, rsv = 0, thr = 0;
+        e = cudaFuncGetAttributes(&a, (const void *)k.fn);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&shm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+        if (e == cudaSuccess) {
+            const int warps = (k.threads + 31) / 32;
+            const int regs_warp = (a.numRegs + 7) / 8 * 8 * 32;   // per-warp granule of 256
+            per = 512 / k.tmem_cols;
+            if (regs_warp > 0) per = std::min(per, regs / (regs_warp * warps));
+            per = std::min(per, shm / (k.smem + (int)a.sharedSizeBytes + rsv));
+            per = std::min(per, thr / k.threads);
+        }
+    } else if (e == cudaSuccess) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k.fn, k.threads, k.smem);
     }
-    return (sms > 0 ? sms : 152) * per;
+    if (e != cudaSuccess || per < 1 || sms < 1) {
+        cudaGetLastError();
+        return -(int)(e != cudaSuccess ? e : cudaErrorInvalidConfiguration);
+    }
+    return sms * per;
 }
 
 cudaError_t launch_step3d_tma(const Step3dParams &p, int mode, int ctas,

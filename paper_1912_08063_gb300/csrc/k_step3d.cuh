@@ -589,6 +589,50 @@ __device__ __forceinline__ void run_segment(Ctx<C, MODE> &c, int col, int z0, in
     c.pbase += c.nout;
 }
 
+// Walks this CTA's share of the persistent schedule (plan_persistent): in each of the
+// p.rounds rounds CTA k < p.round_ctas takes unit u = r p.round_ctas + k (z-part
+// h = u / columns, planes [h nz / zparts, (h + 1) nz / zparts), of tile column
+// u mod columns); the leftover units, all in the last z-part,
+// are cut along z into p.rem_ctas equal pieces, one per CTA (a piece may end one column
+// and start the next).  seg(col, z0, z1) streams one segment; the walk stops when the
+// CTA's abort flag is raised.
+template <class Seg>
+__device__ __forceinline__ void walk_schedule(const Step3dParams &p, int columns, const int *abort_flag,
+                                              Seg &&seg)
+{
+    const int k = blockIdx.x;
+    bool go = true;
+    for (int i = 0; go && i < p.rounds; ++i) {
+        if (k < p.round_ctas) {
+            const int u = i * p.round_ctas + k;
+            const int h = u / columns;
+            seg(u - h * columns, (int)((int64_t)h * p.nz / p.zparts),
+                (int)((int64_t)(h + 1) * p.nz / p.zparts));
+        }
+        __syncthreads();
+        go = !*(volatile const int *)abort_flag;
+    }
+    const int first = p.rounds * p.round_ctas;
+    const int rem = columns * p.zparts - first;
+    if (go && rem > 0 && k < p.rem_ctas) {
+        const int zb = (int)((int64_t)(p.zparts - 1) * p.nz / p.zparts);   // last part: zb .. nz - 1
+        const int len_u = p.nz - zb;
+        const int64_t total = (int64_t)rem * len_u;
+        const int64_t len = (total + p.rem_ctas - 1) / p.rem_ctas;
+        int64_t s0 = (int64_t)k * len;
+        const int64_t s1 = s0 + len < total ? s0 + len : total;
+        while (go && s0 < s1) {
+            const int u = first + (int)(s0 / len_u);
+            const int z0 = zb + (int)(s0 % len_u);
+            const int z1 = (int)(z0 + (s1 - s0) < p.nz ? z0 + (s1 - s0) : p.nz);
+            seg(u % columns, z0, z1);
+            s0 += z1 - z0;
+            __syncthreads();
+            go = !*(volatile const int *)abort_flag;
+        }
+    }
+}
+
 // Persistent launch: gridDim.x CTAs.  The first p.rounds rounds give every CTA of
 // p.round_ctas one whole tile column (all CTAs stream z in step, so neighbouring tiles'
 // halos are read while still in L2); the leftover columns are cut along z into
@@ -601,7 +645,9 @@ k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUt
 {
     using C = Cfg<M, TY, RY, P, U, F, MODE == kModeAdj ? 4 : 2>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // aligned by pointer arithmetic on the shared array (a round trip through an integer
+    // would hide the address space, and every shared-memory read would become generic)
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
 
     Ctx<C, MODE> c;
     c.p = &p;
@@ -634,30 +680,8 @@ k_step3d_tma(const __grid_constant__ Step3dParams p, const __grid_constant__ CUt
 
     const int tiles_x = (p.nx + C::TX - 1) / C::TX;
     const int tiles = tiles_x * ((p.ny + C::TY - 1) / C::TY);
-    const int k = blockIdx.x;
-    bool go = true;
-    for (int i = 0; go && i < p.rounds; ++i) {
-        if (k < p.round_ctas) run_segment(c, i * p.round_ctas + k, 0, p.nz, tiles_x, tiles);
-        __syncthreads();
-        go = !*(volatile int *)c.abort_flag;
-    }
-    const int first = p.rounds * p.round_ctas;
-    const int rem = tiles * p.nshots - first;
-    if (go && rem > 0 && k < p.rem_ctas) {
-        const int64_t total = (int64_t)rem * p.nz;
-        const int64_t len = (total + p.rem_ctas - 1) / p.rem_ctas;
-        int64_t s0 = (int64_t)k * len;
-        const int64_t s1 = s0 + len < total ? s0 + len : total;
-        while (go && s0 < s1) {
-            const int col = first + (int)(s0 / p.nz);
-            const int z0 = (int)(s0 % p.nz);
-            const int z1 = (int)(z0 + (s1 - s0) < p.nz ? z0 + (s1 - s0) : p.nz);
-            run_segment(c, col, z0, z1, tiles_x, tiles);
-            s0 += z1 - z0;
-            __syncthreads();
-            go = !*(volatile int *)c.abort_flag;
-        }
-    }
+    walk_schedule(p, tiles * p.nshots, c.abort_flag,
+                  [&](int col, int z0, int z1) { run_segment(c, col, z0, z1, tiles_x, tiles); });
     __syncthreads();
     if (*(volatile int *)c.abort_flag && c.tid == 0) {
         // a bounded wait gave up: report, then give every copy still in flight (at most the

@@ -22,8 +22,11 @@ struct Step3dParams {
     int nx, ny, nz, px;           // computed extents and row pitch (floats)
     int64_t plane, field;         // floats per z-plane and per shot
     int nshots;
-    int rounds, round_ctas;       // whole-column rounds and the CTAs each round uses
-    int rem_ctas;                 // CTAs sharing the leftover columns along z
+    int rounds, round_ctas;       // whole-unit rounds and the CTAs each round uses
+    int rem_ctas;                 // CTAs sharing the leftover units along z
+    int zparts;                   // a unit is z-part h, planes [h nz / zparts,
+                                  // (h + 1) nz / zparts), of a tile column; units are
+                                  // numbered part-major
     float cx[kMaxM + 1], cy[kMaxM + 1], cz[kMaxM + 1], c0;
     float2 cy2[kMaxM + 1], cz2[kMaxM + 1], c02;   // the same weights as packed pairs
     int iso;                      // hx = hy = hz: the isotropic instantiation may run
@@ -54,15 +57,19 @@ struct Step3dParams {
 // (1: packed x-sums, 2: undamped fast path).  step3d_variant() picks the configuration
 // used for radius M.
 // Tile height, rows per thread, prefetch depth, queue shift interval, and the option bits
-// (Cfg::F) of the plain forward step (opt) and of the store and reverse modes (opt_rev).
+// (Cfg::F) of the plain forward step (opt) and of the store and reverse modes (opt_rev);
+// tm = 1 selects the radius-8 kernel whose z-stream lives in tensor memory
+// (k_step3d_tm.cuh: 64 x 32 tiles, two CTAs per SM; the other fields then do not apply).
 struct Step3dVariant {
     int ty, ry, pf, u, opt, opt_rev;
+    int tm;
 };
 Step3dVariant step3d_variant(int M);
 int step3d_smem_bytes(int M);
 int step3d_threads(int M);
 // Resident CTAs of the 3-D step kernel of `mode` on the current device (SMs x CTAs per
-// SM), for the instantiation a launch on an isotropic (iso) or anisotropic grid uses.
+// SM), for the instantiation a launch on an isotropic (iso) or anisotropic grid uses;
+// -e when a CUDA call of the query failed with error e.
 int step3d_resident_ctas(int M, int mode, bool iso);
 
 // map_c: 4-D [shot][z][y][x] map of the streamed field with the halo box;
@@ -80,11 +87,14 @@ typedef void (*Step3dKernel)(const Step3dParams, const CUtensorMap, const CUtens
 struct Step3dKernelInfo {
     Step3dKernel fn;
     int threads, smem;
+    int tmem_cols = 0;   // tensor-memory columns each CTA allocates
 };
 // iso: the grid is isotropic, so an instantiation with compile-time stencil weights
 // (scaled by 1 / h^2 once per point) may be returned.
 Step3dKernelInfo step3d_kernel_m4(const Step3dVariant &v, int mode, bool iso = false);
 Step3dKernelInfo step3d_kernel_m8(const Step3dVariant &v, int mode, bool iso = false);
+// The tensor-memory radius-8 kernel (k_step3d_tm8.cu).
+Step3dKernelInfo step3d_kernel_tm8(int mode, bool iso);
 
 // Encodes a 4-D tensor map over shots of a field laid out as in Geom (elements of
 // `elem_bytes` = 4 or 2, shots `shot_stride` elements apart), with box (bx, by, 1, 1) and
@@ -93,9 +103,13 @@ int encode_field_map(CUtensorMap *map, const void *base, const Geom &g, int nsho
                      int by, int elem_bytes, int64_t shot_stride);
 
 // Persistent schedule of one launch over `columns` tile columns of nz planes on
-// `resident` CTAs: whole-column rounds, then the leftover columns cut along z into
-// pieces of at least 4M planes (each piece streams 2M warm-up planes).  Fills p.rounds,
-// p.round_ctas, p.rem_ctas and returns the grid size.
-int plan_persistent(Step3dParams &p, int columns, int resident);
+// `resident` CTAs: rounds of whole units, then the leftover units cut along z into
+// pieces of at least 4M planes (each piece streams 2M warm-up planes).  A unit is a whole
+// column, or, with `in_step` and fewer columns than CTAs, one of S = ceil(resident /
+// columns) z-parts of a column that begin at the same z in every column: the CTAs of a
+// round then stream z in step part by part, so a tile's halo planes are still in L2 when
+// its neighbours read them (a field larger than L2 needs this).  Fills p.rounds,
+// p.round_ctas, p.rem_ctas, p.zparts and returns the grid size.
+int plan_persistent(Step3dParams &p, int columns, int resident, bool in_step = false);
 
 }  // namespace fwi

@@ -39,12 +39,26 @@ int encode_field_map(CUtensorMap *map, const void *base, const Geom &g, int nsho
     return r == CUDA_SUCCESS ? 0 : -1;
 }
 
-int plan_persistent(Step3dParams &p, int columns, int resident)
+int plan_persistent(Step3dParams &p, int columns, int resident, bool in_step)
 {
     if (resident < 1) resident = 1;
+    int S = 1;
+    if (in_step && columns > 0 && columns < resident) {
+        S = (resident + columns - 1) / columns;
+        // parts no shorter than 4M planes
+        while (S > 1 && p.nz / S < 4 * p.M) --S;
+        // the walk needs every leftover unit in the last part, which S = ceil(resident /
+        // columns) guarantees; a thinner split keeps whole columns
+        if ((long long)S * columns < resident) S = 1;
+    }
+    p.zparts = S;
+    const int last = p.nz - (int)((long long)(S - 1) * p.nz / S);   // planes of the last part
+    const long long units = (long long)columns * S;
     p.round_ctas = resident;
-    p.rounds = columns / resident;
-    const long long rem_planes = (long long)(columns - p.rounds * resident) * p.nz;
+    p.rounds = (int)(units / resident);
+    // the leftover units all lie in the last part: (S - 1) columns' worth of units fit in
+    // fewer than `resident` slots when S = ceil(resident / columns)
+    const long long rem_planes = (units - (long long)p.rounds * resident) * (S > 1 ? last : p.nz);
     long long pieces = rem_planes / (4LL * p.M);
     if (pieces < 1) pieces = 1;
     if (pieces > resident) pieces = resident;

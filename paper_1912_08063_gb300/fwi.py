@@ -51,7 +51,8 @@ class fwi_info(ctypes.Structure):
                 ("last_snap_restores", c_i64), ("sponge_eta_max", c_f32 * 3), ("cfl", c_f32),
                 ("kernel_launches", c_i64), ("fwd_step_launches", c_i64),
                 ("adj_step_launches", c_i64), ("fwd_step_ms", c_f64), ("adj_step_ms", c_f64),
-                ("store_step_launches", c_i64), ("store_step_ms", c_f64)]
+                ("store_step_launches", c_i64), ("store_step_ms", c_f64),
+                ("step_ctas", c_i32 * 3), ("reserved2", c_i32)]
 
 
 class fwi_request(ctypes.Structure):
