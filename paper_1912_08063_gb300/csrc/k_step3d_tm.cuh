@@ -187,25 +187,33 @@ struct Ctx {
     float *szs;
     uint32_t traw, tpart;       // TMEM addresses of this thread's rings (slot 0)
     int tid, tx, ty, za, nout, niter, shot, bx, by, x0, y0, hx, hy;
-    int hbase, pbase, h_issued, p_issued;
+    // ring positions: the next halo / pointwise stage to consume (with its phase bit) and
+    // to fill (thread 0), and the loads issued so far (for the drain after an abort)
+    int hst, hph, pst, pph, hfill, pfill, h_issued, p_issued;
     float sx1[4], syr[C::RY];
-    bool xin;
-    int64_t sb;
-    int src_j, src_r, src_e;
+    bool rowok[C::RY];          // this thread's rows r store (inside the grid)
+    int64_t plane_f;            // floats per z-plane
+    float *outp;                // out at (plane 0, row y0, column x0) of this shot
+    float *gp;                  // kModeAdj: g at the same place
+    unsigned short *codep;      // kModeStepStore with 16-bit codes: code at the same place
+    float *codef;               // kModeStepStore with FP32: the same
+    int src_j, src_r, src_e;   // source node in this thread's block (src_j < 0: none)
     float srcv;
+    bool domax;                 // raise the checkpoint maxima (p->maxbits set)
     float mxa, mxd;
 
     __device__ __forceinline__ void issue_halo(int it)
     {
-        const int st = (hbase + it) % C::SH;
-        uint64_t *b = bar_h + st;
+        uint64_t *b = bar_h + hfill;
         mbar_expect_tx(b, C::HALO_BYTES);
-        tma_load4(halo + st * C::HALO_STRIDE, mc, hx, hy, za - C::M + it, shot, b);
+        tma_load4(halo + hfill * C::HALO_STRIDE, mc, hx, hy, za - C::M + it, shot, b);
+        hfill = hfill + 1 == C::SH ? 0 : hfill + 1;
+        ++h_issued;
     }
 
     __device__ __forceinline__ void issue_pw(int o)
     {
-        const int st = (pbase + o) % C::SP;
+        const int st = pfill;
         uint64_t *b = bar_p + st;
         unsigned char *d = pw + st * C::PW_STRIDE;
         mbar_expect_tx(b, (C::NPW == 4 && p->aux_fmt != 0 ? 3 * C::TILE_BYTES + C::TILE_BYTES / 2
@@ -220,6 +228,8 @@ struct Ctx {
             tma_load4(d + 2 * C::TILE_BYTES, md, bx * C::TX, by * C::TY, za + o, shot, b);
             tma_load4(d + 3 * C::TILE_BYTES, me, bx * C::TX, by * C::TY, za + o, shot, b);
         }
+        pfill = pfill + 1 == C::SP ? 0 : pfill + 1;
+        ++p_issued;
     }
 
     // A bounded wait whose outcome every lane of the warp shares (the TMEM instructions
@@ -302,106 +312,120 @@ struct Ctx {
 
     __device__ __forceinline__ float cz(int k) const { return C::ISO ? taylor<C::M>(k) : p->cz[k]; }
 
-    // One plane iteration: plane i = za - M + it arrives.  Returns false when the loop
+    // One plane iteration: plane i = za - M + it arrives.  DP: form the partial P(i)
+    // (i in [za, za + nout)); DF: finish output plane j = i - M (j in [za, za + nout)).
+    // A value of 2 takes the decision at run time from the iteration (one body for every
+    // phase: the reverse step, whose larger epilogue gains less from specialised bodies
+    // than it loses to their code size, measured on GB300).  Returns false when the loop
     // must stop.
+    template <int DP_, int DF_>
     __device__ __forceinline__ bool plane(int it)
     {
-        constexpr int M = C::M, SH = C::SH, SP = C::SP, TX = C::TX, RY = C::RY;
-        if (it >= niter) return false;
+        constexpr int M = C::M, RY = C::RY;
+        const bool DP = DP_ == 2 ? (it >= M && it < nout + M) : DP_ != 0;
+        const bool DF = DF_ == 2 ? it >= 2 * M : DF_ != 0;
+        // every thread passes this barrier in every iteration, so an abort raised by any
+        // thread in iteration it is seen by all of them here, in iteration it + 1
         __syncthreads();
         if (*(volatile int *)abort_flag) return false;
         if (tid == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            if (it + C::P < niter) {
-                issue_halo(it + C::P);
-                h_issued = hbase + it + C::P + 1;
-            }
+            if (it + C::P < niter) issue_halo(it + C::P);
             const int op = it - 2 * M + C::PP;
-            if (op >= 0 && op < nout) {
-                issue_pw(op);
-                p_issued = pbase + op + 1;
-            }
+            if (op >= 0 && op < nout) issue_pw(op);
         }
         const int i = za - M + it;
         const uint32_t slot = (uint32_t)(i & (M - 1)) * 8u;   // same slot for i and i - M
-        const int kh = hbase + it;
-        const int st = kh % SH;
-        if (!wait_warp(bar_h + st, (kh / SH) & 1)) {
+        const bool hok = wait_warp(bar_h + hst, (uint32_t)hph);
+        const float *hk = (const float *)(halo + hst * C::HALO_STRIDE);
+        hph ^= hst + 1 == C::SH;
+        hst = hst + 1 == C::SH ? 0 : hst + 1;
+        if (!hok) {
             atomicExch(abort_flag, 1);
             return true;
         }
-        const float *hk = (const float *)(halo + st * C::HALO_STRIDE);
-        const bool do_p = it >= M && it < nout + M;   // P(i) for i in [za, za + nout)
-        const bool do_f = it >= 2 * M;                 // output j = i - M in [za, za + nout)
         float4 ctr[RY];
         float2 pacc[RY][2];
-        if (do_p) {
+        if (DP) {
             lap_xy(hk, pacc, ctr);
         } else {
 #pragma unroll
             for (int r = 0; r < RY; ++r) ctr[r] = *(const float4 *)(hk + (ty * RY + r + M) * C::SX + tx * 4 + M);
         }
-        if (!do_p && !do_f) {   // warm-up: the plane only enters the raw ring
+        if (!DP && !DF) {   // warm-up: the plane only enters the raw ring
             tmem_st8(traw + slot, ctr[0], ctr[1]);
             return true;
-        }
-        // the previous iteration's TMEM stores must have landed before these loads
-        tmem_wait_st();
-        // planes i-1 .. i-4 and the partial P(j) (the slot P(i) will take), then planes
-        // i-5 .. i-8 (i - 8 = j)
-        Slot8 q1, q2, q3, q4, pj;
-        tmem_ld5x8(traw + ((slot - 8u) & 63u), traw + ((slot - 16u) & 63u), traw + ((slot - 24u) & 63u),
-                   traw + ((slot - 32u) & 63u), tpart + slot, q1, q2, q3, q4, pj);
-        float2 lacc[RY][2];
-        // plane i - m enters P(i) with c_m and L(j) (j = i - M) with c_{M-m}
-        auto add = [&](const Slot8 &q, int m) {
-            if (do_p) {
-                fma4(pacc[0][0], pacc[0][1], cz(m), q.a);
-                fma4(pacc[1][0], pacc[1][1], cz(m), q.b);
+        } else {
+            // the previous iteration's TMEM stores must have landed before these loads
+            tmem_wait_st();
+            // planes i-1 .. i-4 and the partial P(j) (the slot P(i) will take), then planes
+            // i-5 .. i-8 (i - 8 = j)
+            Slot8 q1, q2, q3, q4, pj;
+            tmem_ld5x8(traw + ((slot - 8u) & 63u), traw + ((slot - 16u) & 63u),
+                       traw + ((slot - 24u) & 63u), traw + ((slot - 32u) & 63u), tpart + slot, q1,
+                       q2, q3, q4, pj);
+            float2 lacc[RY][2];
+            // plane i - m enters P(i) with c_m and L(j) (j = i - M) with c_{M-m}
+            auto add = [&](const Slot8 &q, int m) {
+                if (DP) {
+                    fma4(pacc[0][0], pacc[0][1], cz(m), q.a);
+                    fma4(pacc[1][0], pacc[1][1], cz(m), q.b);
+                }
+                if (DF) {
+                    if (m < M) {
+                        fma4(lacc[0][0], lacc[0][1], cz(M - m), q.a);
+                        fma4(lacc[1][0], lacc[1][1], cz(M - m), q.b);
+                    }
+                }
+            };
+            if (DF) {
+                // L(j) starts from P(j) and the newest plane's term c_M u(i)
+                lacc[0][0] = lo2(pj.a);
+                lacc[0][1] = hi2(pj.a);
+                lacc[1][0] = lo2(pj.b);
+                lacc[1][1] = hi2(pj.b);
+                fma4(lacc[0][0], lacc[0][1], cz(M), ctr[0]);
+                fma4(lacc[1][0], lacc[1][1], cz(M), ctr[1]);
             }
-            if (do_f && m < M) {
-                fma4(lacc[0][0], lacc[0][1], cz(M - m), q.a);
-                fma4(lacc[1][0], lacc[1][1], cz(M - m), q.b);
-            }
-        };
-        if (do_f) {
-            // L(j) starts from P(j) and the newest plane's term c_M u(i)
-            lacc[0][0] = lo2(pj.a);
-            lacc[0][1] = hi2(pj.a);
-            lacc[1][0] = lo2(pj.b);
-            lacc[1][1] = hi2(pj.b);
-            fma4(lacc[0][0], lacc[0][1], cz(M), ctr[0]);
-            fma4(lacc[1][0], lacc[1][1], cz(M), ctr[1]);
+            add(q1, 1);
+            add(q2, 2);
+            add(q3, 3);
+            add(q4, 4);
+            tmem_ld4x8(traw + ((slot - 40u) & 63u), traw + ((slot - 48u) & 63u),
+                       traw + ((slot - 56u) & 63u), traw + slot, q1, q2, q3, q4);
+            add(q1, 5);
+            add(q2, 6);
+            add(q3, 7);
+            add(q4, 8);
+            const Slot8 uj = q4;
+            // the raw slot of plane i - M = j and the partial slot of P(j) are read: refill
+            tmem_st8(traw + slot, ctr[0], ctr[1]);
+            if (DP)
+                tmem_st8(tpart + slot, make_float4(pacc[0][0].x, pacc[0][0].y, pacc[0][1].x, pacc[0][1].y),
+                         make_float4(pacc[1][0].x, pacc[1][0].y, pacc[1][1].x, pacc[1][1].y));
+            if (DF) return finish(it, lacc, uj);
+            return true;
         }
-        add(q1, 1);
-        add(q2, 2);
-        add(q3, 3);
-        add(q4, 4);
-        tmem_ld4x8(traw + ((slot - 40u) & 63u), traw + ((slot - 48u) & 63u), traw + ((slot - 56u) & 63u),
-                   traw + slot, q1, q2, q3, q4);
-        add(q1, 5);
-        add(q2, 6);
-        add(q3, 7);
-        add(q4, 8);
-        const Slot8 uj = q4;
-        // the raw slot of plane i - M = j and the partial slot of P(j) are read: refill
-        tmem_st8(traw + slot, ctr[0], ctr[1]);
-        if (do_p)
-            tmem_st8(tpart + slot, make_float4(pacc[0][0].x, pacc[0][0].y, pacc[0][1].x, pacc[0][1].y),
-                     make_float4(pacc[1][0].x, pacc[1][0].y, pacc[1][1].x, pacc[1][1].y));
-        if (!do_f) return true;
+    }
 
-        // ---- output plane j: the update and the epilogue ----
+    // The update and the epilogue of output plane j = za + it - 2M from L(j) (unscaled
+    // in the isotropic instantiation) and u(j).
+    __device__ __forceinline__ bool finish(int it, float2 (&lacc)[C::RY][2], const Slot8 &uj)
+    {
+        constexpr int M = C::M, TX = C::TX, RY = C::RY;
         const int o = it - 2 * M, j = za + o;
-        const int ko = pbase + o;
-        const int sp = ko % SP;
-        if (!wait_warp(bar_p + sp, (ko / SP) & 1)) {
+        const bool pok = wait_warp(bar_p + pst, (uint32_t)pph);
+        const int sp = pst;
+        pph ^= pst + 1 == C::SP;
+        pst = pst + 1 == C::SP ? 0 : pst + 1;
+        if (!pok) {
             atomicExch(abort_flag, 1);
             return true;
         }
         const float *ta = (const float *)(pw + sp * C::PW_STRIDE);
         const float *tb = ta + TX * C::TY;
         const float sz = szs[4 * sp + (j & 3)];
+        const int64_t zoff = (int64_t)j * plane_f;
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
             const float4 cz4 = r == 0 ? uj.a : uj.b;
@@ -411,18 +435,18 @@ struct Ctx {
                 l0 = __fmul2_rn(l0, ih);
                 l1 = __fmul2_rn(l1, ih);
             }
-            const int y = y0 + r;
             const int toff = (ty * RY + r) * TX + tx * 4;
+            const int64_t off = zoff + (int64_t)r * p->px;
             const float4 A = *(const float4 *)(ta + toff);   // prev
             const float4 B = *(const float4 *)(tb + toff);   // W
-            const int64_t base = (int64_t)j * p->plane + (int64_t)y * p->px + x0;
-            const bool store = xin && y < p->ny;
-            const bool at_src = j == src_j && r == src_r;
+            // (2c + W lap - (1 - s) prev [+ dt^2 w at the source]) / (1 + s), evaluated as
+            // prev + (2 (c - prev) + W lap [+ dt^2 w]) / (1 + s)
             const float2 m1 = make_float2(-1.0f, -1.0f), two = make_float2(2.0f, 2.0f);
             const float2 dc0 = __ffma2_rn(lo2(A), m1, lo2(cz4));
             const float2 dc1 = __ffma2_rn(hi2(A), m1, hi2(cz4));
             float2 t0 = __ffma2_rn(lo2(B), l0, __fmul2_rn(two, dc0));
             float2 t1 = __ffma2_rn(hi2(B), l1, __fmul2_rn(two, dc1));
+            const bool at_src = j == src_j && r == src_r;
             if (MODE != kModeAdj && at_src) {
                 if (src_e == 0) t0.x += srcv;
                 else if (src_e == 1) t0.y += srcv;
@@ -434,30 +458,32 @@ struct Ctx {
             const float2 d1 = __fadd2_rn(make_float2(sx1[2], sx1[3]), make_float2(syz, syz));
             const float2 o0 = __ffma2_rn(t0, make_float2(rcp_fast(d0.x), rcp_fast(d0.y)), lo2(A));
             const float2 o1 = __ffma2_rn(t1, make_float2(rcp_fast(d1.x), rcp_fast(d1.y)), hi2(A));
-            const float rhs[4] = {o0.x, o0.y, o1.x, o1.y};
-            if (MODE != kModeAdj && p->maxbits) {
-                const float czv[4] = {cz4.x, cz4.y, cz4.z, cz4.w};
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    mxa = absmax_nan(mxa, rhs[e]);
-                    mxd = absmax_nan(mxd, rhs[e] - czv[e]);
-                }
+            if (MODE != kModeAdj && domax) {
+                mxa = absmax_nan(mxa, o0.x);
+                mxa = absmax_nan(mxa, o0.y);
+                mxa = absmax_nan(mxa, o1.x);
+                mxa = absmax_nan(mxa, o1.y);
+                mxd = absmax_nan(mxd, o0.x - cz4.x);
+                mxd = absmax_nan(mxd, o0.y - cz4.y);
+                mxd = absmax_nan(mxd, o1.x - cz4.z);
+                mxd = absmax_nan(mxd, o1.y - cz4.w);
             }
-            if (store) *(float4 *)(p->out + sb + base) = make_float4(rhs[0], rhs[1], rhs[2], rhs[3]);
-            if (MODE == kModeStepStore && store) {
-                const int64_t ci = (int64_t)shot * p->st_cstride + base;
+            if (rowok[r]) *(float4 *)(outp + off) = make_float4(o0.x, o0.y, o1.x, o1.y);
+            if (MODE == kModeStepStore && rowok[r]) {
+                // checkpoint of the input pair (c = u^n, prev = u^{n-1}) in the encode
+                // kernel's format: FP32 pair, or 16-bit a = c s_a and d = (c - prev) s_d
                 if (p->st_dtype == 0) {
-                    *(float4 *)((float *)p->st_code + ci) = cz4;
-                    if (p->st_comps == 2) *(float4 *)((float *)p->st_code + ci + p->field) = A;
+                    *(float4 *)(codef + off) = cz4;
+                    if (p->st_comps == 2) *(float4 *)(codef + off + p->field) = A;
                 } else {
-                    unsigned short *cc = (unsigned short *)p->st_code + ci;
-                    *(uint2 *)cc = pack_code4(cz4, p->st_dtype, sts[0]);
+                    *(uint2 *)(codep + off) = pack_code4(cz4, p->st_dtype, sts[0]);
                     if (p->st_comps == 2)
-                        *(uint2 *)(cc + p->field) =
+                        *(uint2 *)(codep + off + p->field) =
                             pack_code4(make_float4(dc0.x, dc0.y, dc1.x, dc1.y), p->st_dtype, sts[1]);
                 }
             }
             if (MODE == kModeAdj) {
+                // g += u^m * (L mu^{m+1});  at the source point g -= dt^2 w[m] mu^{m+1} / W
                 const float *td = ta + 2 * TX * C::TY, *te = ta + 3 * TX * C::TY;
                 const float4 Ua =
                     p->aux_fmt == 0
@@ -468,7 +494,7 @@ struct Ctx {
                 float2 g0 = __ffma2_rn(lo2(Ua), l0, lo2(G));
                 float2 g1 = __ffma2_rn(hi2(Ua), l1, hi2(G));
                 if (at_src) src_image(g0, g1, cz4, B, src_e, srcv);
-                if (store) *(float4 *)(p->g + sb + base) = make_float4(g0.x, g0.y, g1.x, g1.y);
+                if (rowok[r]) *(float4 *)(gp + off) = make_float4(g0.x, g0.y, g1.x, g1.y);
             }
         }
         return true;
@@ -496,8 +522,20 @@ __device__ __forceinline__ void run_segment(Ctx<C, MODE> &c, int col, int z0, in
     for (int e = 0; e < 4; ++e) c.sx1[e] = 1.0f + ((c.x0 + e < p.nx) ? p.sig_x[c.x0 + e] : 0.0f);
 #pragma unroll
     for (int r = 0; r < RY; ++r) c.syr[r] = (c.y0 + r < p.ny) ? p.sig_y[c.y0 + r] : 0.0f;
-    c.xin = c.x0 < p.nx;
-    c.sb = (int64_t)c.shot * p.field;
+    {
+        const bool xin = c.x0 < p.nx;
+#pragma unroll
+        for (int r = 0; r < RY; ++r) c.rowok[r] = xin && c.y0 + r < p.ny;
+        const int64_t rowbase = (int64_t)c.y0 * p.px + c.x0;
+        c.plane_f = p.plane;
+        c.outp = p.out + (int64_t)c.shot * p.field + rowbase;
+        if (MODE == kModeAdj) c.gp = p.g + (int64_t)c.shot * p.field + rowbase;
+        if (MODE == kModeStepStore) {
+            c.codep = (unsigned short *)p.st_code + (int64_t)c.shot * p.st_cstride + rowbase;
+            c.codef = (float *)p.st_code + (int64_t)c.shot * p.st_cstride + rowbase;
+        }
+        c.domax = MODE != kModeAdj && p.maxbits != nullptr;
+    }
     c.src_j = -1;
     c.src_r = c.src_e = 0;
     c.srcv = 0.0f;
@@ -522,10 +560,23 @@ __device__ __forceinline__ void run_segment(Ctx<C, MODE> &c, int col, int z0, in
     if (c.tid == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         for (int it = 0; it < C::P && it < c.niter; ++it) c.issue_halo(it);
-        c.h_issued = c.hbase + (C::P < c.niter ? C::P : c.niter);
     }
-    for (int it = 0; it < c.niter; ++it)
-        if (!c.plane(it)) break;
+    // phases: warm-up (planes only enter the raw ring), partials only, partials and
+    // outputs (the steady state), outputs only; with nout < M a gap of warm-up planes
+    // separates the partials from the outputs
+    if (MODE == kModeAdj) {
+        for (int it = 0; it < c.niter; ++it)
+            if (!c.template plane<2, 2>(it)) break;
+    } else {
+        const int e1 = 2 * M < c.nout + M ? 2 * M : c.nout + M;
+        int it = 0;
+        bool go = true;
+        for (; go && it < M; ++it) go = c.template plane<0, 0>(it);
+        for (; go && it < e1; ++it) go = c.template plane<1, 0>(it);
+        for (; go && it < 2 * M; ++it) go = c.template plane<0, 0>(it);
+        for (; go && it < c.nout + M; ++it) go = c.template plane<1, 1>(it);
+        for (; go && it < c.niter; ++it) go = c.template plane<0, 1>(it);
+    }
     if (MODE != kModeAdj && p.maxbits) {
         const unsigned a = __reduce_max_sync(0xffffffffu, __float_as_uint(c.mxa) & 0x7fffffffu);
         const unsigned d = __reduce_max_sync(0xffffffffu, __float_as_uint(c.mxd) & 0x7fffffffu);
@@ -535,8 +586,6 @@ __device__ __forceinline__ void run_segment(Ctx<C, MODE> &c, int col, int z0, in
         }
         c.mxa = c.mxd = 0.0f;
     }
-    c.hbase += c.niter;
-    c.pbase += c.nout;
 }
 
 // Persistent launch with the schedule of k_step3d.cuh (whole-column rounds, then the
@@ -574,7 +623,7 @@ k_step3d_tm(const __grid_constant__ Step3dParams p, const __grid_constant__ CUte
     c.tid = threadIdx.x;
     c.tx = c.tid % C::NTX;
     c.ty = c.tid / C::NTX;
-    c.hbase = c.pbase = 0;
+    c.hst = c.hph = c.pst = c.pph = c.hfill = c.pfill = 0;
     c.h_issued = c.p_issued = 0;
     c.mxa = c.mxd = 0.0f;
 
