@@ -263,18 +263,22 @@ def serving_section(dev, n_req, seed=4, rates=(0.8,)):
             m.close()
     torch.cuda.synchronize()
 
-    def run(max_active, arrivals):
+    def run(max_active, arrivals, shared=True):
         for r, a in zip(reqs, arrivals):
             r["arrival"] = float(a)
         t0 = time.perf_counter()
-        res, _ = fwi.fwi_serve(reqs, max_active=max_active, steps_per_turn=16, snap_slots=64)
+        res, _ = fwi.fwi_serve(reqs, max_active=max_active, steps_per_turn=16, snap_slots=64,
+                               shared_launch=shared)
         wall = time.perf_counter() - t0
         lat = np.array([x["t_done"] - a for x, a in zip(res, arrivals)])
         ok = sum(1 for x in res if x["status"] == 0)
+        run.shared = sum(x["shared_launch"] for x in res)
         return ok / wall, lat, ok
 
     zero = np.zeros(n_req)
+    cap_ns, _, _ = run(16, zero, shared=False)
     cap_b, _, ok_b = run(16, zero)
+    n_shared = run.shared
     cap_1, _, ok_1 = run(1, zero)
     lam = 0.8 * cap_b
     rng = np.random.default_rng(seed)
@@ -293,6 +297,8 @@ def serving_section(dev, n_req, seed=4, rates=(0.8,)):
                       "p99_s": round(float(np.percentile(lat, 99)), 3)})
     return {"requests": n_req, "completed": [ok_b, ok_1], "load_sweep": sweep,
             "shots_per_s": round(cap_b, 3), "shots_per_s_one_at_a_time": round(cap_1, 3),
+            "shots_per_s_without_shared_launch": round(cap_ns, 3),
+            "requests_in_shared_launch": n_shared,
             "poisson_rate_per_s": round(lam, 3),
             "p50_s": round(float(np.percentile(lat_b, 50)), 3),
             "p99_s": round(float(np.percentile(lat_b, 99)), 3),

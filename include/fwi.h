@@ -252,8 +252,12 @@ int fwi_model_info(const fwi_model *m, fwi_info *out);
  * budget's remainder; an admitted request owns a model (wavefields and checkpoints stay
  * on the device) and a stream, and one host thread issues the admitted requests' time
  * steps round-robin (steps_per_turn at a time, at most two turns in flight per request),
- * so their work overlaps on the device.  Finished requests are retired and release
- * their memory.  max_active = 1 serves one request at a time on the same kernels. */
+ * so their work overlaps on the device.  2-D forward requests with node source and
+ * receivers share one launch instead: each tick, one captured graph of persistent
+ * multi-request step and sampling kernels advances all of them by steps_per_turn
+ * (rounded up to even) steps from a device table of request descriptors updated in
+ * place.  Finished requests are retired and release their memory.  max_active = 1
+ * serves one request at a time on the same kernels. */
 #define FWI_REQ_FORWARD  0
 #define FWI_REQ_GRADIENT 1
 
@@ -280,7 +284,7 @@ typedef struct {
 
 typedef struct {
     int32_t status;             /* FWI_OK or the request's error code                   */
-    int32_t reserved;
+    int32_t shared_launch;      /* 1: its steps ran in the shared launch                */
     double  misfit;             /* gradient requests (Eq. 1)                            */
     double  t_admit, t_start, t_done;   /* seconds after the start of fwi_serve         */
     int64_t device_bytes;       /* device memory the request's model held at admission  */
@@ -294,6 +298,12 @@ typedef struct {
     int32_t snap_slots;         /* checkpoint budget per gradient request, in pairs
                                    (default 64; slots holding u^n alone take half)      */
     int32_t nb;                 /* sponge width (default 20)                            */
+    int32_t no_shared_launch;   /* 1: every request issues its own steps on its own
+                                   stream; 0 (default): 2-D forward requests with node
+                                   source and receivers are advanced together by the
+                                   shared launch (one graph of multi-request step and
+                                   sampling kernels per tick over a device table of
+                                   request descriptors)                                */
 } fwi_serve_opts;
 
 /* Runs the request stream to completion: waits for each arrival time, admits, steps and

@@ -1381,6 +1381,7 @@ struct Job {
     FwdJob f;
     GradJob gj;
     int nrec = 0;
+    int row_z = -2, row_x0 = 0;   // receivers as one row (row_z >= 0), -1: not, -2: unknown
 };
 
 Job *job_forward(fwi_model *m, const fwi_acq *acq, const float *wavelets, cudaStream_t s,
@@ -1423,6 +1424,67 @@ Job *job_gradient(fwi_model *m, const fwi_acq *acq, const float *wavelets, const
 int job_advance(Job *j, int64_t units, bool *done)
 {
     return j->kind == 0 ? fwd_advance(j->f, units, done) : grad_advance(j->gj, units, done);
+}
+
+// The serving loop's shared 2-D forward launch.  A forward job of one 2-D shot with a
+// node source and node receivers (no temporal blocking, no kernel timing) may have its
+// time steps issued by k_step2d_multi instead of job_advance: job_batch_entry fills a
+// table entry with its state, job_batch_moved records that `steps` steps ran.
+bool job_batchable(const Job *j)
+{
+    if (j->kind != 0) return false;
+    const fwi_model *m = j->f.m;
+    return m->ndim == 2 && j->f.ns == 1 && !m->og_src && !m->og_rec && j->f.tb_chunks == 0 &&
+           !m->opts.timing && j->f.tr != nullptr;
+}
+
+int job_batch_entry(Job *j, Batch2dEntry *e, int zchunk)
+{
+    if (!job_batchable(j)) return fail(FWI_ERR_ARG, "job not eligible for the shared launch");
+    const FwdJob &f = j->f;
+    const fwi_model *m = f.m;
+    if (j->row_z == -2) {
+        // receivers that are consecutive nodes of one row are sampled by the step itself
+        j->row_z = -1;
+        const int nr = f.nr;
+        if (nr > 0 && (int64_t)m->geo_rec.size() >= 3 * (int64_t)nr) {
+            const int64_t o0 = node_offset(m, m->geo_rec.data());
+            const int z = (int)(o0 / m->g.plane), x0 = (int)(o0 - (int64_t)z * m->g.plane);
+            bool row = x0 + nr <= m->g.nx;
+            for (int r = 1; row && r < nr; ++r) row = node_offset(m, m->geo_rec.data() + 3 * r) == o0 + r;
+            if (row) {
+                j->row_z = z;
+                j->row_x0 = x0;
+            }
+        }
+    }
+    e->p = f.p;
+    e->p.zchunk = zchunk;
+    e->p.nzchunks = (m->g.nz + zchunk - 1) / zchunk;
+    e->p.n_dev = nullptr;
+    e->u0 = f.uc;
+    e->u1 = f.up;
+    e->n0 = f.n;
+    e->xtiles = (m->g.nx + 255) / 256;
+    e->rec_off = m->rec_off.as<int64_t>();
+    e->traces = f.tr;
+    e->nrec = f.nr;
+    e->rec_z = j->row_z;
+    e->rec_x0 = j->row_x0;
+    e->nsamp = j->row_z >= 0 ? 0 : f.nr;
+    return FWI_OK;
+}
+
+int job_batch_moved(Job *j, int steps, bool *done)
+{
+    FwdJob &f = j->f;
+    const int left = f.m->nt - f.n;
+    const int moved = steps < left ? steps : left;
+    if (moved & 1) std::swap(f.uc, f.up);
+    f.n += moved;
+    f.m->launches += 2 * (int64_t)moved;
+    *done = f.n >= f.m->nt;
+    return FWI_OK;
 }
 
 // Issues the result copies into host buffers (traces [ns][nt][nrec] of a forward job, or

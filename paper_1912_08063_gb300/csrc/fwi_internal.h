@@ -107,6 +107,35 @@ cudaError_t launch_gather_src_pts(const Geom &g, const float *f, const PointTaps
 
 // 2-D step (k_step2d.cu); the 3-D step has its own launcher (step3d.h)
 cudaError_t launch_step2d(const StepParams &p, int nshots, bool imaging, cudaStream_t s);
+
+// The serving loop's shared 2-D forward launch: a device table of requests, each a
+// one-shot 2-D forward run with a node source and node receivers.  A tick of k steps is
+// k launches of each kernel (step t = 0 .. k - 1).
+struct Batch2dEntry {
+    StepParams p;             // the request's step parameters (g, c, W, sig, src_off,
+                              // wavelet, nt, dt2, zchunk, nzchunks; cur/prev/n unused)
+    float *u0, *u1;           // u^{n0} and u^{n0 - 1} at the tick's start
+    int n0;                   // step index at the tick's start
+    int xtiles;               // work items: xtiles x p.nzchunks
+    int work0, rec0;          // first work item and first receiver of the entry
+    const int64_t *rec_off;   // [nrec] receiver offsets in the field
+    float *traces;            // [nt][nrec]
+    int nrec;
+    int nsamp;                // receivers the sampling kernel reads: nrec, or 0 when the
+                              // step samples them (rec_z >= 0)
+    int rec_z, rec_x0;        // receivers on row rec_z, columns rec_x0 .. rec_x0 + nrec - 1
+                              // (rec_z = -1: any other layout)
+    int pad[2];
+};
+constexpr int kBatch2dMax = 64;
+struct Batch2d {
+    int count, total_work, total_rec, pad;   // total_rec: receivers of the sampling kernel
+    Batch2dEntry e[kBatch2dMax];
+};
+// Persistent grid of k_step2d_multi for radius M (resident CTAs on the current device).
+int multi2d_grid(int M);
+cudaError_t launch_step2d_multi(const Batch2d *tab, int M, int t, int grid, cudaStream_t s);
+cudaError_t launch_sample_multi(const Batch2d *tab, int t, int grid, cudaStream_t s);
 // Two forward steps in one pass (2-D): from (p.cur = u^n, p.prev = u^{n-1}) write u^{n+1}
 // to out1 and u^{n+2} to out2 (neither may alias cur or prev); sources at steps n and
 // n + 1.  step2d_tb2_chunks is 0 when the batch is too small to fill the GPU (then use

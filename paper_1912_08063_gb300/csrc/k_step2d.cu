@@ -95,19 +95,26 @@ struct RowIn {
 // also writes the checkpoint of the input pair (c = u^n, prev = u^{n-1}) in the encode
 // kernel's format from the epilogue: the store the schedule asks for right before this
 // step, without the encode pass's second read of both fields.
-template <int M, bool IMG, bool PFR, bool STORE = false>
-__global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
+// One CTA's work: x tile bx, z-chunk zc of shot `shot`, from state (cur_base = u^n,
+// prev_base = u^{n-1}, overwritten by u^{n+1}) at step n.  p supplies everything else
+// (it may live in kernel parameters or in a device table).  With row_tr, the receivers
+// are the rn consecutive nodes of row rz from column rx0 on, and the epilogue writes
+// their samples u^{n+1} to row_tr[0 .. rn) (forward step only).
+template <int M, bool IMG, bool PFR, bool STORE>
+__device__ __forceinline__ void step2d_body(const StepParams &p, const float *cur_base,
+                                            float *prev_base, int n, int bx, int shot, int zc,
+                                            float *row_tr = nullptr, int rz = -1, int rx0 = 0,
+                                            int rn = 0)
 {
     constexpr int Q = 2 * M + 1, W4 = M / 4;   // x-window: W4 groups of 4 either side
-    const int shot = blockIdx.z / p.nzchunks, zc = blockIdx.z - shot * p.nzchunks;
     const int nz = p.g.nz, nx = p.g.nx, px = p.g.px;
     const int z0 = zc * p.zchunk, z1 = min(nz, z0 + p.zchunk);
-    const int x0 = blockIdx.x * kTile2 + threadIdx.x * 4;
+    const int x0 = bx * kTile2 + threadIdx.x * 4;
     const bool xin = x0 < nx;
     const int64_t plane = p.g.plane;
     const int64_t sb = (int64_t)shot * p.g.field;
-    const float *__restrict__ cur = p.cur + sb;
-    float *__restrict__ prev = p.prev + sb;
+    const float *__restrict__ cur = cur_base + sb;
+    float *__restrict__ prev = prev_base + sb;
     const int afmt = p.aux_fmt;
     const char *__restrict__ auxb =
         IMG ? (const char *)p.aux + (size_t)shot * p.aux_stride * (afmt ? 2 : 4) : nullptr;
@@ -131,7 +138,7 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
         if (sxx >= x0 && sxx < x0 + 4) {
             src_z = sz;
             src_e = sxx - x0;
-            srcv = p.dt2 * p.wavelet[(int64_t)shot * p.nt + (p.n_dev ? *p.n_dev : 0) + p.n];
+            srcv = p.dt2 * p.wavelet[(int64_t)shot * p.nt + n];
         }
     }
     unsigned mxa = 0u, mxd = 0u;   // bits of max|out| and max|out - c| (p.maxbits set)
@@ -191,6 +198,13 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
                                      (!IMG && z == src_z) ? src_e : -1, srcv);
             const float rhs[4] = {o.x, o.y, o.z, o.w};
             *(float4 *)(prev + row + x0) = o;
+            if (!IMG && row_tr && z == rz) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int r = x0 + e - rx0;
+                    if (r >= 0 && r < rn) row_tr[r] = rhs[e];
+                }
+            }
             if (STORE) {
                 // FP32 pair unchanged, or 16-bit a = c s_a and d = (c - prev) s_d
                 const int64_t ci = (int64_t)shot * p.st_cstride + row + x0;
@@ -243,6 +257,56 @@ __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
             if (a) atomicMax(p.maxbits + 2 * shot, a);
             if (d) atomicMax(p.maxbits + 2 * shot + 1, d);
         }
+    }
+}
+
+template <int M, bool IMG, bool PFR, bool STORE = false>
+__global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
+{
+    const int shot = blockIdx.z / p.nzchunks, zc = blockIdx.z - shot * p.nzchunks;
+    step2d_body<M, IMG, PFR, STORE>(p, p.cur, p.prev, (p.n_dev ? *p.n_dev : 0) + p.n, blockIdx.x,
+                                    shot, zc);
+}
+
+// ---- the serving loop's shared launch: one forward step of every request in a table ----
+
+// Step t of a tick for every request of the table: work item w of the persistent loop is
+// (x tile, z-chunk) (w - work0) of the entry whose range holds it; the entry's state is
+// (u0, u1) at the tick's start, so step t reads u^n from u0 (t even) or u1 (t odd) and
+// overwrites the other; entries whose nt ends within the tick skip the steps past it.
+template <int M>
+__global__ void __launch_bounds__(kThreads2) k_step2d_multi(const Batch2d *__restrict__ tab, int t)
+{
+    const int count = tab->count, total = tab->total_work;
+    int e = 0;
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+        while (e + 1 < count && tab->e[e + 1].work0 <= w) ++e;   // w increases: scan on
+        const Batch2dEntry &E = tab->e[e];
+        const int n = E.n0 + t;
+        if (n >= E.p.nt) continue;
+        const int lw = w - E.work0;
+        const int bx = lw % E.xtiles, zc = lw / E.xtiles;
+        const bool odd = t & 1;
+        step2d_body<M, false, true, false>(E.p, odd ? E.u1 : E.u0, odd ? E.u0 : E.u1, n, bx, 0, zc,
+                                           E.rec_z >= 0 ? E.traces + (int64_t)n * E.nrec : nullptr,
+                                           E.rec_z, E.rec_x0, E.nrec);
+    }
+}
+
+// The receiver samples of step t, traces[n][r] = u^{n+1}(rec_r), of every entry whose
+// step does not sample them itself (nsamp receivers each).
+__global__ void k_sample_multi(const Batch2d *__restrict__ tab, int t)
+{
+    const int count = tab->count, total = tab->total_rec;
+    int e = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        while (e + 1 < count && tab->e[e + 1].rec0 <= i) ++e;
+        const Batch2dEntry &E = tab->e[e];
+        const int n = E.n0 + t;
+        if (n >= E.p.nt) continue;
+        const int r = i - E.rec0;
+        const float *next = (t & 1) ? E.u0 : E.u1;   // the buffer step t wrote
+        E.traces[(int64_t)n * E.nrec + r] = next[E.rec_off[r]];
     }
 }
 
@@ -507,6 +571,34 @@ cudaError_t launch_step2d_tb2(const StepParams &p, int nshots, float *out1, floa
     if (p.g.M == 4) return launch_tb2x<4, false>(p, nshots, out1, out2, s);
     if (p.g.M == 8) return launch_tb2x<8, false>(p, nshots, out1, out2, s);
     return cudaErrorInvalidValue;
+}
+
+int multi2d_grid(int M)
+{
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per, M == 8 ? (const void *)k_step2d_multi<8> : (const void *)k_step2d_multi<4>,
+            kThreads2, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 152 * 8;
+    }
+    return (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
+}
+
+cudaError_t launch_step2d_multi(const Batch2d *tab, int M, int t, int grid, cudaStream_t s)
+{
+    if (M == 4) k_step2d_multi<4><<<grid, kThreads2, 0, s>>>(tab, t);
+    else if (M == 8) k_step2d_multi<8><<<grid, kThreads2, 0, s>>>(tab, t);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_multi(const Batch2d *tab, int t, int grid, cudaStream_t s)
+{
+    k_sample_multi<<<grid, 256, 0, s>>>(tab, t);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_step2d(const StepParams &p, int nshots, bool imaging, cudaStream_t s)

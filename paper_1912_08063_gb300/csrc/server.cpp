@@ -11,8 +11,20 @@
 // when they land it is retired, its memory returns to the budget and the next waiting
 // request can be admitted.  max_active = 1 gives the one-request-at-a-time baseline on
 // the same kernels.
+//
+// Shared launch: 2-D forward requests (one shot, node source and receivers) of the same
+// stencil radius do not issue their own steps.  They join a pool whose device table holds
+// one descriptor per request (its step parameters, state buffers, step index, receivers
+// and traces); each tick, the loop refreshes the table in place (one upload from pinned
+// memory on the pool's stream) and replays one captured graph of k persistent launches
+// of the multi-request step kernel and k of the multi-request sampling kernel, which
+// advance every pooled request by k steps.  The graph reads the table at run time, so
+// admissions and retirements change only the table, never the graph.  A request that
+// reaches its last step leaves the pool: its own stream waits for that tick before the
+// result copies.
 #include <algorithm>
 #include <chrono>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -21,8 +33,13 @@
 
 #include "fwi.h"
 
+#include "fwi_internal.h"
+
 namespace fwi {
 struct Job;
+bool job_batchable(const Job *j);
+int job_batch_entry(Job *j, Batch2dEntry *e, int zchunk);
+int job_batch_moved(Job *j, int steps, bool *done);
 Job *job_forward(fwi_model *m, const fwi_acq *acq, const float *wavelets, cudaStream_t s, int *rc);
 Job *job_gradient(fwi_model *m, const fwi_acq *acq, const float *wavelets, const float *d_obs,
                   cudaStream_t s, int *rc);
@@ -49,7 +66,100 @@ struct Slot {
     float *out_pinned = nullptr;  // traces or gradient
     double *misfit_pinned = nullptr;
     size_t out_bytes = 0;
+    int pool = -1;                // index of the shared-launch pool it is in, or -1
+    bool pool_synced = false;     // the pool's stream has waited for its set-up
 };
+
+// A pool of requests advanced together by the shared launch (one per stencil radius).
+struct Pool {
+    int M = 0;
+    fwi::Batch2d *dev = nullptr;       // device table
+    fwi::Batch2d *host[2] = {};        // pinned staging, used alternately
+    cudaEvent_t uploaded[2] = {};      // the upload from host[i] has finished
+    bool pending[2] = {false, false};
+    int buf = 0;
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;       // one tick: k x (multi step, multi sample)
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphNode_t> nodes;   // its kernel nodes in launch order
+    std::vector<cudaKernelNodeParams> params;
+    int grid_step = 0, grid_sample = 0;   // persistent grids (resident CTAs)
+    bool sampling = true;                 // the sampling nodes are enabled
+    int k = 0;
+    cudaEvent_t tick = nullptr;        // recorded after a tick that finished a request
+    std::vector<int> members;          // slot indices
+    bool failed = false;               // set-up failed: requests run on their own streams
+};
+
+constexpr int kPoolZChunk = 128;   // most rows per work item of the multi-request step
+constexpr int kPools = 4;          // shared-launch pools per stencil radius
+
+void pool_release(Pool &p)
+{
+    if (p.stream) cudaStreamSynchronize(p.stream);
+    if (p.exec) cudaGraphExecDestroy(p.exec);
+    if (p.graph) cudaGraphDestroy(p.graph);
+    for (int i = 0; i < 2; ++i) {
+        if (p.host[i]) cudaFreeHost(p.host[i]);
+        if (p.uploaded[i]) cudaEventDestroy(p.uploaded[i]);
+    }
+    if (p.tick) cudaEventDestroy(p.tick);
+    if (p.dev) cudaFree(p.dev);
+    if (p.stream) cudaStreamDestroy(p.stream);
+    p = Pool();
+}
+
+// Allocates the pool's table and stream and captures its tick graph (k steps).
+int pool_setup(Pool &p, int M, int k)
+{
+    p.M = M;
+    p.k = k;
+    cudaError_t e = cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&p.dev, sizeof(fwi::Batch2d));
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaMallocHost((void **)&p.host[i], sizeof(fwi::Batch2d));
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.uploaded[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.tick, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.dev, 0, sizeof(fwi::Batch2d), p.stream);
+    if (e != cudaSuccess) return fwi::report_error(FWI_ERR_CUDA, std::string("serve pool: ") + cudaGetErrorString(e));
+    p.grid_step = fwi::multi2d_grid(M);
+    p.grid_sample = 152 * 4;
+    e = cudaStreamBeginCapture(p.stream, cudaStreamCaptureModeThreadLocal);
+    for (int t = 0; t < k && e == cudaSuccess; ++t) {
+        e = fwi::launch_step2d_multi(p.dev, M, t, p.grid_step, p.stream);
+        if (e == cudaSuccess) e = fwi::launch_sample_multi(p.dev, t, p.grid_sample, p.stream);
+    }
+    const cudaError_t ec = cudaStreamEndCapture(p.stream, &p.graph);
+    if (e == cudaSuccess) e = ec;
+    // the kernel nodes, in launch order (a chain), so each tick can size their grids
+    size_t nn = 0;
+    if (e == cudaSuccess) e = cudaGraphGetNodes(p.graph, nullptr, &nn);
+    if (e == cudaSuccess && nn != (size_t)(2 * k)) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess) {
+        std::vector<cudaGraphNode_t> all(nn);
+        e = cudaGraphGetRootNodes(p.graph, all.data(), &nn);
+        cudaGraphNode_t cur = nn == 1 ? all[0] : nullptr;
+        while (e == cudaSuccess && cur) {
+            p.nodes.push_back(cur);
+            cudaKernelNodeParams kp{};
+            e = cudaGraphKernelNodeGetParams(cur, &kp);
+            p.params.push_back(kp);
+            size_t ne = 0;
+            if (e == cudaSuccess) e = cudaGraphNodeGetDependentNodes(cur, nullptr, nullptr, &ne);
+            cudaGraphNode_t nx = nullptr;
+            if (e == cudaSuccess && ne == 1) e = cudaGraphNodeGetDependentNodes(cur, &nx, nullptr, &ne);
+            cur = ne == 1 ? nx : nullptr;
+        }
+        if (e == cudaSuccess && p.nodes.size() != (size_t)(2 * k)) e = cudaErrorInvalidValue;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p.exec, p.graph, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fwi::report_error(FWI_ERR_CUDA, std::string("serve pool graph: ") + cudaGetErrorString(e));
+    }
+    return FWI_OK;
+}
 
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
@@ -150,6 +260,15 @@ extern "C" int fwi_serve(const fwi_request *reqs, int32_t n, const fwi_serve_opt
                      [&](int a, int b) { return reqs[a].arrival < reqs[b].arrival; });
 
     std::vector<Slot> slots(o.max_active);
+    // shared-launch pools, radius 4 and radius 8, set up on first use; a tick is an even
+    // number of steps (steps_per_turn rounded up)
+    // kPools pools per radius, filled round-robin: their ticks overlap on the device
+    // (measured on GB300: one pool serialises its requests' steps behind one another,
+    // four match the throughput of one stream per request)
+    std::vector<Pool> pools(2 * kPools);
+    int rr = 0;
+    const int tick_k = (o.steps_per_turn + 1) / 2 * 2;
+    const bool share = o.no_shared_launch == 0;
     int64_t used = 0;
     size_t next = 0;
     int finished = 0;
@@ -187,6 +306,22 @@ extern "C" int fwi_serve(const fwi_request *reqs, int32_t n, const fwi_serve_opt
                 ++finished;
                 continue;
             }
+            if (share && fwi::job_batchable(free_slot->job)) {
+                const int pi = (r.order == 16 ? kPools : 0) + (rr++ % kPools);
+                Pool &pl = pools[pi];
+                if (!pl.stream && !pl.failed && pool_setup(pl, r.order / 2, tick_k) != FWI_OK) {
+                    pool_release(pl);
+                    pl.failed = true;
+                }
+                if (!pl.failed && (int)pl.members.size() < fwi::kBatch2dMax &&
+                    cudaEventRecord(free_slot->turn, free_slot->stream) == cudaSuccess) {
+                    free_slot->pool = pi;   // its set-up is ordered before the pool's next tick
+                    results[idx].shared_launch = 1;
+                    pl.members.push_back((int)(free_slot - slots.data()));
+                } else {
+                    cudaGetLastError();
+                }
+            }
             free_slot->bytes = est;
             results[idx].reserved_bytes = est;
             used += est;
@@ -222,7 +357,7 @@ extern "C" int fwi_serve(const fwi_request *reqs, int32_t n, const fwi_serve_opt
                 ++finished;
                 continue;
             }
-            if (s.issued_all) continue;
+            if (s.issued_all || s.pool >= 0) continue;
             // keep at most two turns in flight: skip while the previous turn still runs
             if (cudaEventQuery(s.turn) == cudaErrorNotReady) continue;
             if (res.t_start == 0.0) res.t_start = now();
@@ -247,6 +382,115 @@ extern "C" int fwi_serve(const fwi_request *reqs, int32_t n, const fwi_serve_opt
             }
             issued = true;
         }
+        // shared-launch ticks
+        for (Pool &pl : pools) {
+            if (pl.members.empty()) continue;
+            if (pl.pending[pl.buf]) {   // two ticks in flight: wait for the older upload
+                if (cudaEventQuery(pl.uploaded[pl.buf]) == cudaErrorNotReady) continue;
+                pl.pending[pl.buf] = false;
+            }
+            fwi::Batch2d *h = pl.host[pl.buf];
+            int work = 0, recs = 0, rc = FWI_OK;
+            // z-chunk rows per work item: about one item per resident CTA, so a step's
+            // critical path (one CTA streaming its chunk) stays short, but no shorter
+            // than the 2M warm-up rows each chunk streams
+            int64_t row_tiles = 0;
+            for (int si : pl.members) {
+                const fwi_request &r = reqs[slots[si].req];
+                row_tiles += (int64_t)((r.shape[2] + 2 * o.nb + 255) / 256) * (r.shape[0] + 2 * o.nb);
+            }
+            const int zchunk = (int)std::max<int64_t>(
+                2 * pl.M, std::min<int64_t>(kPoolZChunk, (row_tiles + pl.grid_step - 1) / pl.grid_step));
+            h->count = 0;
+            for (int si : pl.members) {
+                Slot &s = slots[si];
+                fwi::Batch2dEntry &e = h->e[h->count++];
+                rc = fwi::job_batch_entry(s.job, &e, zchunk);
+                if (rc != FWI_OK) break;
+                e.work0 = work;
+                e.rec0 = recs;
+                work += e.xtiles * e.p.nzchunks;
+                recs += e.nsamp;
+                if (!s.pool_synced) {
+                    if (cudaStreamWaitEvent(pl.stream, s.turn, 0) != cudaSuccess) rc = FWI_ERR_CUDA;
+                    s.pool_synced = true;
+                }
+                if (results[s.req].t_start == 0.0) results[s.req].t_start = now();
+            }
+            h->total_work = work;
+            h->total_rec = recs;
+            const size_t bytes = offsetof(fwi::Batch2d, e) + (size_t)h->count * sizeof(fwi::Batch2dEntry);
+            // grids sized to this tick's work (the persistent loops cover any excess)
+            const unsigned gs = (unsigned)std::max(1, std::min(work, pl.grid_step));
+            const unsigned gr = (unsigned)std::max(1, std::min((recs + 255) / 256, pl.grid_sample));
+            // the sampling nodes run only when some request's step does not sample itself
+            const bool sample = recs > 0;
+            for (size_t q = 0; rc == FWI_OK && q < pl.nodes.size(); ++q) {
+                if ((q & 1) && sample != pl.sampling &&
+                    cudaGraphNodeSetEnabled(pl.exec, pl.nodes[q], sample ? 1 : 0) != cudaSuccess)
+                    rc = FWI_ERR_CUDA;
+                if ((q & 1) && !sample) continue;
+                cudaKernelNodeParams kp = pl.params[q];
+                kp.gridDim = dim3((q & 1) ? gr : gs, 1, 1);
+                if (cudaGraphExecKernelNodeSetParams(pl.exec, pl.nodes[q], &kp) != cudaSuccess) rc = FWI_ERR_CUDA;
+            }
+            pl.sampling = sample;
+            if (rc == FWI_OK && (cudaMemcpyAsync(pl.dev, h, bytes, cudaMemcpyHostToDevice, pl.stream) != cudaSuccess ||
+                                 cudaEventRecord(pl.uploaded[pl.buf], pl.stream) != cudaSuccess ||
+                                 cudaGraphLaunch(pl.exec, pl.stream) != cudaSuccess))
+                rc = FWI_ERR_CUDA;
+            if (rc != FWI_OK) {   // the pool's requests fail; the loop goes on
+                cudaGetLastError();
+                cudaStreamSynchronize(pl.stream);
+                for (int si : pl.members) {
+                    Slot &s = slots[si];
+                    results[s.req].status = rc;
+                    results[s.req].t_done = now();
+                    used -= s.bytes;
+                    release(s);
+                    ++finished;
+                }
+                pl.members.clear();
+                continue;
+            }
+            pl.pending[pl.buf] = true;
+            pl.buf ^= 1;
+            issued = true;
+            // advance the jobs; requests that reached their last step leave the pool
+            bool recorded = false;
+            std::vector<int> keep;
+            for (int si : pl.members) {
+                Slot &s = slots[si];
+                bool done = false;
+                fwi::job_batch_moved(s.job, pl.k, &done);
+                if (!done) {
+                    keep.push_back(si);
+                    continue;
+                }
+                int frc = FWI_OK;
+                if (!recorded) {
+                    if (cudaEventRecord(pl.tick, pl.stream) != cudaSuccess) frc = FWI_ERR_CUDA;
+                    recorded = true;
+                }
+                if (frc == FWI_OK && cudaStreamWaitEvent(s.stream, pl.tick, 0) != cudaSuccess) frc = FWI_ERR_CUDA;
+                if (frc == FWI_OK) frc = fwi::job_finish(s.job, s.misfit_pinned, s.out_pinned);
+                if (frc == FWI_OK && cudaEventRecord(s.done, s.stream) != cudaSuccess) frc = FWI_ERR_CUDA;
+                s.pool = -1;
+                s.issued_all = true;
+                if (frc == FWI_OK) {
+                    s.finishing = true;
+                } else {
+                    cudaGetLastError();
+                    cudaStreamSynchronize(s.stream);
+                    results[s.req].status = frc;
+                    results[s.req].t_done = now();
+                    used -= s.bytes;
+                    release(s);
+                    ++finished;
+                }
+            }
+            pl.members.swap(keep);
+        }
         if (!any_active && next < order.size()) {
             // idle until the next arrival
             const double wait = reqs[order[next]].arrival - now();
@@ -255,5 +499,6 @@ extern "C" int fwi_serve(const fwi_request *reqs, int32_t n, const fwi_serve_opt
             std::this_thread::yield();
         }
     }
+    for (Pool &pl : pools) pool_release(pl);
     return FWI_OK;
 }

@@ -64,14 +64,14 @@ class fwi_request(ctypes.Structure):
 
 
 class fwi_result(ctypes.Structure):
-    _fields_ = [("status", c_i32), ("reserved", c_i32), ("misfit", c_f64), ("t_admit", c_f64),
+    _fields_ = [("status", c_i32), ("shared_launch", c_i32), ("misfit", c_f64), ("t_admit", c_f64),
                 ("t_start", c_f64), ("t_done", c_f64), ("device_bytes", c_i64),
                 ("reserved_bytes", c_i64)]
 
 
 class fwi_serve_opts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", c_i64), ("max_active", c_i32), ("steps_per_turn", c_i32),
-                ("snap_slots", c_i32), ("nb", c_i32)]
+                ("snap_slots", c_i32), ("nb", c_i32), ("no_shared_launch", c_i32)]
 
 
 class FwiError(RuntimeError):
@@ -247,7 +247,8 @@ def fwi_model_info(model) -> dict:
     return out
 
 
-def fwi_serve(requests, budget_bytes=0, max_active=16, steps_per_turn=8, snap_slots=64, nb=20):
+def fwi_serve(requests, budget_bytes=0, max_active=16, steps_per_turn=8, snap_slots=64, nb=20,
+              shared_launch=True):
     """Runs a request stream through the serving loop.  `requests` is a list of dicts with
     keys kind ('forward'/'gradient'), v (float32 physical grid), h, dt, nt, order,
     snap_dtype, src (3 ints), rec (int32 [nrec][3]), wavelet (float32 [nt]), d_obs
@@ -294,9 +295,9 @@ def fwi_serve(requests, budget_bytes=0, max_active=16, steps_per_turn=8, snap_sl
         q.arrival = float(r.get("arrival", 0.0))
     res = (fwi_result * n)()
     opts = fwi_serve_opts(int(budget_bytes), int(max_active), int(steps_per_turn),
-                          int(snap_slots), int(nb))
+                          int(snap_slots), int(nb), 0 if shared_launch else 1)
     _check(lib().fwi_serve(arr, n, ctypes.byref(opts), res))
-    results = [{k: getattr(x, k) for k, _ in fwi_result._fields_ if k != "reserved"} for x in res]
+    results = [{k: getattr(x, k) for k, _ in fwi_result._fields_} for x in res]
     return results, outs
 
 

@@ -74,17 +74,23 @@ def test_admission_respects_the_budget():
     assert len({round(x["t_admit"], 6) for x in res}) > 1
 
 
-def test_graph_replayed_forward_equals_direct_call():
-    """Forward requests in the serving loop run their turns as captured CUDA graphs that
-    read the step index from a device counter (turns of 6 steps here; nt not a multiple
-    of 6, so the last steps run one by one); the traces equal a direct forward call bit
-    for bit."""
+@pytest.mark.parametrize("shared", [True, False])
+def test_graph_replayed_forward_equals_direct_call(shared):
+    """Forward requests in the serving loop run either in the shared launch (2-D: one
+    graph per tick of multi-request step and sampling kernels over a table of request
+    descriptors) or, without it, as per-request turns replayed from captured CUDA graphs
+    that read the step index from a device counter (turns of 6 steps here; nt not a
+    multiple of 6, so the last steps run one by one); either way the traces equal a direct
+    forward call bit for bit."""
     from paper_1912_08063_gb300 import fwi
     reqs = [r for r in _requests(10, seed=5) if r["kind"] == "forward"][:4]
     assert reqs
     for r in reqs:
         r["arrival"] = 0.0
-    res, out = fwi.fwi_serve(reqs, max_active=4, steps_per_turn=6, snap_slots=4)
+    res, out = fwi.fwi_serve(reqs, max_active=4, steps_per_turn=6, snap_slots=4,
+                             shared_launch=shared)
+    n2d = sum(1 for r in reqs if r["v"].ndim == 2)
+    assert sum(x["shared_launch"] for x in res) == (n2d if shared else 0)
     for r, x, o in zip(reqs, res, out):
         assert x["status"] == 0
         m = fwi.FwiModel(torch.from_numpy(r["v"]).cuda(), r["h"], r["dt"], r["nt"])
@@ -129,8 +135,9 @@ def test_served_results_match_the_oracle():
     from the oracle's forward run of the perturbed model."""
     import oracle
     from paper_1912_08063_gb300 import fwi
-    reqs = _requests(6, seed=11)
-    fwd = next(i for i, r in enumerate(reqs) if r["kind"] == "forward")
+    reqs = _requests(8, seed=11)
+    # a 2-D forward request (it runs in the shared launch) and a gradient request
+    fwd = next(i for i, r in enumerate(reqs) if r["kind"] == "forward" and r["v"].ndim == 2)
     grd = next(i for i, r in enumerate(reqs) if r["kind"] == "gradient")
 
     def problem(r, v):
@@ -142,8 +149,9 @@ def test_served_results_match_the_oracle():
     rg["d_obs"] = problem(rg, rg["v_obs"]).forward()[0].astype(np.float32)
     for i, r in enumerate(reqs):
         r["arrival"] = 0.001 * i
-    res, out = fwi.fwi_serve(reqs, max_active=6, steps_per_turn=4, snap_slots=6)
+    res, out = fwi.fwi_serve(reqs, max_active=8, steps_per_turn=4, snap_slots=6)
     assert all(x["status"] == 0 for x in res), res
+    assert res[fwd]["shared_launch"] == 1 and res[grd]["shared_launch"] == 0
     rf = reqs[fwd]
     ref = problem(rf, rf["v"]).forward()[0]
     e = _rel(np.asarray(out[fwd]).reshape(ref.shape), ref)
@@ -155,3 +163,26 @@ def test_served_results_match_the_oracle():
     print(f"served gradient ({rg['v'].ndim}-D {rg['v'].shape}, nt {rg['nt']}, "
           f"{rg['snap_dtype']}): rel-L2 {eg:.2e}, misfit {ephi:.2e}")
     assert eg <= 1e-2 and ephi <= 1e-4
+
+
+def test_shared_launch_equals_own_streams():
+    """A mixed stream served with the shared launch and without it: every result is the
+    same bit for bit (the shared launch runs the same step arithmetic), the 2-D forward
+    requests ran in the shared launch, and several of them were in it at once."""
+    from paper_1912_08063_gb300 import fwi
+    reqs = _requests(12, seed=7)
+    for i, r in enumerate(reqs):
+        r["arrival"] = 0.001 * i
+    a, oa = fwi.fwi_serve(reqs, max_active=12, steps_per_turn=4, snap_slots=6)
+    b, ob = fwi.fwi_serve(reqs, max_active=12, steps_per_turn=4, snap_slots=6,
+                          shared_launch=False)
+    assert all(x["status"] == 0 for x in a + b)
+    pooled = [i for i, r in enumerate(reqs) if r["kind"] == "forward" and r["v"].ndim == 2]
+    assert len(pooled) >= 2
+    assert [i for i, x in enumerate(a) if x["shared_launch"]] == pooled
+    assert not any(x["shared_launch"] for x in b)
+    for i in range(len(reqs)):
+        assert np.array_equal(oa[i], ob[i]), i
+        assert a[i]["misfit"] == b[i]["misfit"]
+    iv = sorted((a[i]["t_start"], a[i]["t_done"]) for i in pooled)
+    assert any(y[0] < x[1] for x, y in zip(iv, iv[1:]))
