@@ -22,7 +22,9 @@ itself is the one with the most device time, with ``min_frac`` (the slowest kern
 ``time_weighted_frac`` (all step kernels' algorithmic bytes over their device time)
 beside it), ``layered_3d_256`` (the 256^3 layered model at 8th order with BF16
 checkpoints: gradient rate, each step kernel's GB/s, and the forward step's cost per
-point and step at order 8 against the headline workload's order 16), ``serving`` (a Poisson stream of mixed 2-D/3-D forward/gradient requests
+point and step at order 8 against the headline workload's order 16), ``onchip_2d``
+(one-shot 2-D forward runs of the serving mix's kind at 128^2..384^2, single steps against
+temporal blocking on chip), ``serving`` (a Poisson stream of mixed 2-D/3-D forward/gradient requests
 through the continuous-batching loop against one request at a time: shots/s, p50/p99
 latency) and ``batched_2d`` (64 shots of the 400 x 1024 faulted model in one gradient
 call against 64 one-shot calls, with the step kernels' times, and the forward-only rate
@@ -272,7 +274,8 @@ def serving_section(dev, n_req, seed=4, rates=(0.8,)):
         wall = time.perf_counter() - t0
         lat = np.array([x["t_done"] - a for x, a in zip(res, arrivals)])
         ok = sum(1 for x in res if x["status"] == 0)
-        run.shared = sum(x["shared_launch"] for x in res)
+        run.shared = (sum(1 for x in res if x["shared_launch"] == 1),
+                      sum(1 for x in res if x["shared_launch"] == 2))
         return ok / wall, lat, ok
 
     zero = np.zeros(n_req)
@@ -298,7 +301,8 @@ def serving_section(dev, n_req, seed=4, rates=(0.8,)):
     return {"requests": n_req, "completed": [ok_b, ok_1], "load_sweep": sweep,
             "shots_per_s": round(cap_b, 3), "shots_per_s_one_at_a_time": round(cap_1, 3),
             "shots_per_s_without_shared_launch": round(cap_ns, 3),
-            "requests_in_shared_launch": n_shared,
+            "requests_in_shared_launch": {"multi_request_steps": n_shared[0],
+                                          "cluster_on_chip": n_shared[1]},
             "poisson_rate_per_s": round(lam, 3),
             "p50_s": round(float(np.percentile(lat_b, 50)), 3),
             "p99_s": round(float(np.percentile(lat_b, 99)), 3),
@@ -473,6 +477,46 @@ def layered_section(dev, nt=2000, budget_gb=224.0, peak=None, k1_order16=None):
             "kernels": kern, **summ, "order_tradeoff": trade}
 
 
+def onchip_section(dev, sizes=(128, 256, 384), nt=1500):
+    """One-shot 2-D forward runs of the serving mix's kind (smooth model 1500..4500 m/s,
+    h 10 m, dt at 0.8 of the stability limit, source and receivers on surface row 2),
+    timed with single steps and with temporal blocking on chip (fwi_opts.temporal_blocking
+    = 2: up to 64 steps per launch, both states in the shared memory of one cluster of
+    CTAs).  Best of three runs each."""
+    import math
+
+    import torch
+
+    from paper_1912_08063_gb300 import fwi, synth
+
+    rng = np.random.default_rng(3)
+    out = {}
+    for n in sizes:
+        v = synth.smooth_random(rng, (n, n), 10.0, ell=300.0)
+        v = (1500.0 + 3000.0 * (v - v.min()) / (v.max() - v.min())).astype(np.float32)
+        h = 10.0
+        dt = math.floor(0.8 / fwi.fwi_cfl_number(2, 8, (h, h, h), 4500.0, 1.0) * 1e4) / 1e4
+        acq = fwi.Acquisition(np.array([[2, 0, n // 2]], dtype=np.int32),
+                              np.array([[2, 0, x] for x in range(n)], dtype=np.int32))
+        wav = torch.from_numpy(synth.ricker(15.0, dt, nt)[None].astype(np.float32)).to(dev)
+        res = {}
+        for tb in (0, 2):
+            m = fwi.FwiModel(torch.from_numpy(v).to(dev), h, dt, nt, temporal_blocking=tb)
+            m.forward(acq, wav)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(3):
+                t0 = time.perf_counter()
+                m.forward(acq, wav)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            res["single_step_ms" if tb == 0 else "on_chip_ms"] = round(min(ts) * 1e3, 3)
+            m.close()
+        res["speedup"] = round(res["single_step_ms"] / res["on_chip_ms"], 2)
+        out[f"{n}x{n}"] = res
+    return {"nt": nt, "runs": out}
+
+
 def replica_rate(ms_local, units_local, world, dist=None, device="cpu"):
     """Whole-job timing of N independent replicas: the step time is the maximum over
     ranks, the rate the units all ranks processed per second of that time.  Returns
@@ -619,11 +663,13 @@ def main():
 
     # the other two workloads of the metric, measured after the timed region
     model.close()
-    serving = batched = layered = None
+    serving = batched = layered = onchip = None
     if rank == 0 and not args.no_layered and args.workload == "salt_3d_512":
         k1 = kern["fwd_step_3d"]
         layered = layered_section(dev, args.layered_nt, args.snap_budget_gb, peak,
                                   (k1["avg_ms"], pts * w.nshots) if k1["launches"] else None)
+    if rank == 0 and not args.no_serving:
+        onchip = onchip_section(dev)
     if rank == 0 and not args.no_serving:
         serving = serving_section(dev, args.serving_requests,
                                   rates=tuple(float(x) for x in args.serving_rates.split(",")))
@@ -646,7 +692,8 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "clocks": ck, "e2e": e2e, "gpu_launches": launches,
                 "roofline": roof, "cpu_baseline": cpu, "misfit": float(phi.item()),
-                "layered_3d_256": layered, "serving": serving, "batched_2d": batched}
+                "layered_3d_256": layered, "serving": serving, "onchip_2d": onchip,
+                "batched_2d": batched}
         print(json.dumps(line), flush=True)
     model.close()
     if world > 1:

@@ -72,7 +72,12 @@ typedef struct {
                                    two time steps per pass (same results bit for bit;
                                    measured on GB300 within 3 % of single steps: the
                                    2-D step is latency-bound, so halving its DRAM bytes
-                                   buys nothing); default 0                             */
+                                   buys nothing); 2: one-shot 2-D forward calls on grids
+                                   whose two states fit in the shared memory of one
+                                   cluster of CTAs, with node receivers on one row,
+                                   advance up to 64 steps per launch with the states on
+                                   chip (same results bit for bit); other calls run
+                                   single steps; default 0                              */
 } fwi_opts;
 
 /* Acquisition geometry of one call: shot s has one source and nrec receivers, each a
@@ -256,7 +261,9 @@ int fwi_model_info(const fwi_model *m, fwi_info *out);
  * receivers share one launch instead: each tick, one captured graph of persistent
  * multi-request step and sampling kernels advances all of them by steps_per_turn
  * (rounded up to even) steps from a device table of request descriptors updated in
- * place.  Finished requests are retired and release their memory.  max_active = 1
+ * place; requests small enough to keep both states in the shared memory of one cluster
+ * of CTAs are advanced by a single launch per tick that runs all those steps on chip.
+ * Finished requests are retired and release their memory.  max_active = 1
  * serves one request at a time on the same kernels. */
 #define FWI_REQ_FORWARD  0
 #define FWI_REQ_GRADIENT 1
@@ -284,7 +291,9 @@ typedef struct {
 
 typedef struct {
     int32_t status;             /* FWI_OK or the request's error code                   */
-    int32_t shared_launch;      /* 1: its steps ran in the shared launch                */
+    int32_t shared_launch;      /* 0: own stream; 1: shared launch of multi-request
+                                   step kernels; 2: shared cluster launch, k steps per
+                                   launch with the states in shared memory            */
     double  misfit;             /* gradient requests (Eq. 1)                            */
     double  t_admit, t_start, t_done;   /* seconds after the start of fwi_serve         */
     int64_t device_bytes;       /* device memory the request's model held at admission  */

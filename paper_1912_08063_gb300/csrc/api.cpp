@@ -4,7 +4,9 @@
 // validates arguments, owns device memory and orders launches on the caller's stream.
 #include "fwi.h"
 
+#include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -192,6 +194,10 @@ struct fwi_model {
         CUtensorMap map;
     };
     std::vector<MapEntry> maps;
+    DevBuf cl_tab;                 // one-entry table of the on-chip 2-D forward launch
+    Batch2d *cl_host = nullptr;    // its pinned staging
+    cudaEvent_t cl_up = nullptr;   // the staging's last upload finished
+    int cl_rec_z = -1, cl_rec_x0 = 0;
     int resident[3] = {0, 0, 0};   // resident CTAs of the 3-D step kernel, per mode
     int resident_query[3] = {0, 0, 0};   // what the occupancy query returned (-e: error e)
     int64_t t_fwd_n = 0, t_adj_n = 0, t_st_n = 0;
@@ -721,6 +727,7 @@ struct FwdJob {
     float *uc = nullptr, *up = nullptr;   // u^n and u^{n-1}
     int n = 0;
     int tb_chunks = 0;      // z-chunks of the two-step pass (0: single steps only)
+    int cl_size = 0;        // temporal blocking on chip: cluster size (0: off)
     // CUDA graph of one turn: g_units steps from the state buffers (g_uc, g_up), replayed
     // with the device step counter m->step_ctr (dev_n: its value as the host last set it)
     cudaGraphExec_t gexec = nullptr;
@@ -757,7 +764,35 @@ int fwd_setup(FwdJob &j, fwi_model *m, int ns, int nr, const float *wav, float *
     j.n = 0;
     // 2-D batches wide enough to fill the GPU advance two steps per pass when the source
     // is a node (off-grid source taps are added between steps)
-    j.tb_chunks = (m->og_src || !m->opts.temporal_blocking) ? 0 : step2d_tb2_chunks(m->g, ns);
+    j.tb_chunks = (m->og_src || m->opts.temporal_blocking != 1) ? 0 : step2d_tb2_chunks(m->g, ns);
+    j.cl_size = 0;
+    if (m->opts.temporal_blocking == 2 && m->ndim == 2 && ns == 1 && !m->og_src && !m->og_rec &&
+        tr && !m->opts.timing) {
+        // receivers on one row (sampled in the step's epilogue) and states that fit on chip
+        const int C = cluster2d_size(m->M);
+        bool ok = C > 0 && nr > 0 && m->g.nz / C > m->M &&
+                  2LL * ((m->g.nz + C - 1) / C) * m->g.px * 4 <= cluster2d_max_smem();
+        int64_t o0 = 0;
+        if (ok) {
+            o0 = node_offset(m, m->geo_rec.data());
+            const int x0 = (int)(o0 % m->g.plane);
+            ok = x0 + nr <= m->g.nx;
+            for (int r = 1; ok && r < nr; ++r) ok = node_offset(m, m->geo_rec.data() + 3 * r) == o0 + r;
+        }
+        if (ok && m->cl_tab.ensure(sizeof(Batch2d)) == FWI_OK) {
+            if (!m->cl_host) {
+                if (cudaMallocHost((void **)&m->cl_host, sizeof(Batch2d)) != cudaSuccess) {
+                    cudaGetLastError();
+                    m->cl_host = nullptr;
+                }
+            }
+            if (m->cl_host) {
+                j.cl_size = C;
+                m->cl_rec_z = (int)(o0 / m->g.plane);
+                m->cl_rec_x0 = (int)(o0 % m->g.plane);
+            }
+        }
+    }
     if (j.tb_chunks > 0) {
         const size_t fbytes = (size_t)ns * m->g.field * sizeof(float);
         if (m->ut[0].ensure(fbytes) != FWI_OK || m->ut[1].ensure(fbytes) != FWI_OK) {
@@ -842,9 +877,49 @@ int fwd_capture(FwdJob &j, int units)
     return FWI_OK;
 }
 
+// Temporal blocking on chip: up to 64 steps per cluster launch (k_step2d_cluster) from a
+// one-entry table; the steps' arithmetic is the single step's.
+int fwd_advance_onchip(FwdJob &j, int64_t units, bool *done)
+{
+    fwi_model *m = j.m;
+    for (int64_t u = 0; u < units && j.n < m->nt;) {
+        const int k = (int)std::min<int64_t>({units - u, (int64_t)(m->nt - j.n), 64});
+        if (!m->cl_up) FWI_CU(cudaEventCreateWithFlags(&m->cl_up, cudaEventDisableTiming));
+        FWI_CU(cudaEventSynchronize(m->cl_up));   // the staging is free again
+        Batch2d *h = m->cl_host;
+        h->count = 1;
+        h->total_work = h->total_rec = 0;
+        Batch2dEntry &e = h->e[0];
+        e = Batch2dEntry{};
+        e.p = j.p;
+        e.p.n_dev = nullptr;
+        e.u0 = j.uc;
+        e.u1 = j.up;
+        e.n0 = j.n;
+        e.traces = j.tr;
+        e.nrec = j.nr;
+        e.rec_off = m->rec_off.as<int64_t>();
+        e.rec_z = m->cl_rec_z;
+        e.rec_x0 = m->cl_rec_x0;
+        const int C = j.cl_size;
+        const int smem = (int)((2LL * ((m->g.nz + C - 1) / C) * m->g.px * 4 + 1023) / 1024 * 1024);
+        FWI_CU(cudaMemcpyAsync(m->cl_tab.p, h, offsetof(Batch2d, e) + sizeof(Batch2dEntry),
+                               cudaMemcpyHostToDevice, j.s));
+        FWI_CU(cudaEventRecord(m->cl_up, j.s));
+        ++m->launches;
+        FWI_CU(launch_step2d_cluster(m->cl_tab.as<Batch2d>(), m->M, k, C, 1, smem, j.s));
+        if (k & 1) std::swap(j.uc, j.up);
+        j.n += k;
+        u += k;
+    }
+    *done = j.n >= m->nt;
+    return FWI_OK;
+}
+
 int fwd_advance(FwdJob &j, int64_t units, bool *done)
 {
     fwi_model *m = j.m;
+    if (j.cl_size > 0) return fwd_advance_onchip(j, units, done);
     // a turn of an even number of steps (the serving loop's unit of work) replays one
     // captured graph: the buffer parity repeats after it and the step index comes from
     // the device counter
@@ -1882,6 +1957,9 @@ void fwi_destroy(fwi_model *m)
     m->snaps.release();
     m->scales.release();
     if (m->h_flag) cudaFreeHost(m->h_flag);
+    m->cl_tab.release();
+    if (m->cl_host) cudaFreeHost(m->cl_host);
+    if (m->cl_up) cudaEventDestroy(m->cl_up);
     for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
     delete m;
 }

@@ -136,6 +136,15 @@ struct Batch2d {
 int multi2d_grid(int M);
 cudaError_t launch_step2d_multi(const Batch2d *tab, int M, int t, int grid, cudaStream_t s);
 cudaError_t launch_sample_multi(const Batch2d *tab, int t, int grid, cudaStream_t s);
+// Temporal blocking on chip: k steps of every request of the table in one launch, one
+// cluster of C CTAs per request, each CTA holding a band of rows of both states in shared
+// memory (smem bytes per CTA: 2 ceil(nz / C) px floats of the largest request).  For
+// requests with receivers on one row (rec_z >= 0) and nz / C > M.
+// cluster2d_size: the cluster size to use (16, else 8; 0 if clusters cannot be launched).
+int cluster2d_size(int M);
+int cluster2d_max_smem();
+cudaError_t launch_step2d_cluster(const Batch2d *tab, int M, int k, int C, int nreq, int smem,
+                                  cudaStream_t s);
 // Two forward steps in one pass (2-D): from (p.cur = u^n, p.prev = u^{n-1}) write u^{n+1}
 // to out1 and u^{n+2} to out2 (neither may alias cur or prev); sources at steps n and
 // n + 1.  step2d_tb2_chunks is 0 when the batch is too small to fill the GPU (then use

@@ -12,6 +12,8 @@
 // the Laplacian it computes for the step (u^m read pointwise, from an FP32 field or in
 // place from a 16-bit checkpoint; g read and written: 26-28 bytes per point), and at the
 // source point g -= dt^2 w[m] mu^{m+1} / W.  Shots run on grid.z.
+#include <cooperative_groups.h>
+
 #include "code16.cuh"
 #include "fwi_internal.h"
 
@@ -570,6 +572,162 @@ cudaError_t launch_step2d_tb2(const StepParams &p, int nshots, float *out1, floa
     // 283 against 292 Gpts/s on the 64-shot batch
     if (p.g.M == 4) return launch_tb2x<4, false>(p, nshots, out1, out2, s);
     if (p.g.M == 8) return launch_tb2x<8, false>(p, nshots, out1, out2, s);
+    return cudaErrorInvalidValue;
+}
+
+// ---- temporal blocking on chip: one thread-block cluster per request ----
+//
+// A small 2-D request is advanced by k steps in one launch.  Its C CTAs (one cluster)
+// split the nz rows into bands [r0, r1); each CTA holds its band of u^n and u^{n-1} in
+// shared memory for the whole launch, reads the M halo rows above and below from its
+// neighbours' shared memory (distributed shared memory of the cluster), and writes
+// u^{n+1} over its u^{n-1} band; a cluster barrier separates the steps (hardware, no
+// polling).  W, the sponge tables and the wavelet are read from global memory (L2).
+// Receivers that form one row are sampled in the epilogue; the source is added by the
+// thread owning its node.  The arithmetic of a point is the single step's (lap4,
+// update4 on the same operands), so k steps here equal k single steps bit for bit.  The
+// states return to global memory at the end of the launch (buffer 0 to u0, 1 to u1, the
+// same parity the single steps leave).
+constexpr int kClThreads = 512;
+
+template <int M>
+__global__ void __launch_bounds__(kClThreads, 1) k_step2d_cluster(const Batch2d *__restrict__ tab, int k)
+{
+    namespace cg = cooperative_groups;
+    constexpr int Q = 2 * M + 1, W4 = M / 4;
+    extern __shared__ __align__(16) float smc[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int req = blockIdx.x / C;   // one cluster per request (uniform per cluster)
+    if (req >= tab->count) return;
+    const Batch2dEntry &E = tab->e[req];
+    const StepParams &p = E.p;
+    const int nz = p.g.nz, nx = p.g.nx, px = p.g.px;
+    const int r0 = (int)((int64_t)rank * nz / C), r1 = (int)((int64_t)(rank + 1) * nz / C);
+    const int rup = rank > 0 ? (int)((int64_t)(rank - 1) * nz / C) : 0;   // first row above
+    const int R = r1 - r0, band = (nz + C - 1) / C * px;   // floats per band buffer
+    float *b0 = smc, *b1 = smc + band;
+    const int G = px / 4;
+    for (int i = threadIdx.x; i < R * G; i += blockDim.x) {
+        *(float4 *)(b0 + 4 * i) = __ldg((const float4 *)(E.u0 + (int64_t)r0 * px) + i);
+        *(float4 *)(b1 + 4 * i) = __ldg((const float4 *)(E.u1 + (int64_t)r0 * px) + i);
+    }
+    // source node
+    int src_z = -1, src_x = -1;
+    if (p.src_off) {
+        const int64_t so = p.src_off[0];
+        src_z = (int)(so / px);
+        src_x = (int)(so - (int64_t)src_z * px);
+    }
+    cl.sync();
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int s = 0; s < k; ++s) {
+        const int n = E.n0 + s;
+        if (n >= p.nt) break;   // the same for every CTA of the cluster
+        const float *cur = (s & 1) ? b1 : b0;
+        float *prv = (s & 1) ? b0 : b1;
+        const float *up = rank > 0 ? cl.map_shared_rank(cur, rank - 1) : nullptr;
+        const float *dn = rank < C - 1 ? cl.map_shared_rank(cur, rank + 1) : nullptr;
+        const float srcv = p.dt2 * p.wavelet[n];
+        float *row_tr = E.rec_z >= r0 && E.rec_z < r1 ? E.traces + (int64_t)n * E.nrec : nullptr;
+        for (int it = threadIdx.x; it < R * G; it += blockDim.x) {
+            const int lr = it / G, g = it - lr * G;
+            const int z = r0 + lr, x0 = 4 * g;
+            if (x0 >= nx) continue;
+            float4 q[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int zz = z - M + i;
+                const float *src = zz < 0 || zz >= nz ? nullptr
+                                   : zz < r0          ? up + (int64_t)(zz - rup) * px
+                                   : zz >= r1         ? dn + (int64_t)(zz - r1) * px
+                                                      : cur + (int64_t)(zz - r0) * px;
+                q[i] = src ? *(const float4 *)(src + x0) : zero4;
+            }
+            float w[4 + 2 * M];
+            const float *rowc = cur + (int64_t)lr * px;
+#pragma unroll
+            for (int g4 = 0; g4 < 2 * W4 + 1; ++g4) {
+                const int xg = x0 + 4 * (g4 - W4);
+                const float4 v = g4 == W4 ? q[M] : (xg < 0 || xg >= px ? zero4 : *(const float4 *)(rowc + xg));
+                w[4 * g4] = v.x, w[4 * g4 + 1] = v.y, w[4 * g4 + 2] = v.z, w[4 * g4 + 3] = v.w;
+            }
+            float2 l0, l1;
+            lap4<M>(w, q, p.c, l0, l1);
+            float sx[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) sx[e] = (x0 + e < nx) ? p.sig_x[x0 + e] : 0.0f;
+            const float4 pv = *(const float4 *)(prv + (int64_t)lr * px + x0);
+            const float4 Wv = __ldg((const float4 *)(p.W + (int64_t)z * px + x0));
+            const int se = (z == src_z && src_x >= x0 && src_x < x0 + 4) ? src_x - x0 : -1;
+            const float4 o = update4(q[M], l0, l1, pv, Wv, sx, p.sig_z[z], se, srcv);
+            *(float4 *)(prv + (int64_t)lr * px + x0) = o;
+            if (row_tr && z == E.rec_z) {
+                const float rhs[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int r = x0 + e - E.rec_x0;
+                    if (r >= 0 && r < E.nrec) row_tr[r] = rhs[e];
+                }
+            }
+        }
+        // every band's u^{n+1} is written and every read of u^n is done
+        cl.sync();
+    }
+    for (int i = threadIdx.x; i < R * G; i += blockDim.x) {
+        ((float4 *)(E.u0 + (int64_t)r0 * px))[i] = *(const float4 *)(b0 + 4 * i);
+        ((float4 *)(E.u1 + (int64_t)r0 * px))[i] = *(const float4 *)(b1 + 4 * i);
+    }
+}
+
+int cluster2d_max_smem() { return 220 * 1024; }
+
+int cluster2d_size(int M)
+{
+    // the largest cluster (16, else 8) of which at least one fits with full shared memory
+    const void *fn = M == 8 ? (const void *)k_step2d_cluster<8> : (const void *)k_step2d_cluster<4>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, cluster2d_max_smem()) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    for (int C : {16, 8}) {
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(C, 1, 1);
+        cfg.blockDim = dim3(kClThreads, 1, 1);
+        cfg.dynamicSmemBytes = cluster2d_max_smem();
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) == cudaSuccess && nc > 0) return C;
+        cudaGetLastError();
+    }
+    return 0;
+}
+
+cudaError_t launch_step2d_cluster(const Batch2d *tab, int M, int k, int C, int nreq, int smem,
+                                  cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C * (nreq > 0 ? nreq : 1), 1, 1);
+    cfg.blockDim = dim3(kClThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (M == 4) return cudaLaunchKernelEx(&cfg, k_step2d_cluster<4>, tab, k);
+    if (M == 8) return cudaLaunchKernelEx(&cfg, k_step2d_cluster<8>, tab, k);
     return cudaErrorInvalidValue;
 }
 

@@ -21,7 +21,9 @@
 // advance every pooled request by k steps.  The graph reads the table at run time, so
 // admissions and retirements change only the table, never the graph.  A request that
 // reaches its last step leaves the pool: its own stream waits for that tick before the
-// result copies.
+// result copies.  Small requests (both states fit in the shared memory of one cluster
+// of CTAs) go to cluster pools instead, whose tick is a single launch that advances each
+// request by k steps with its states on chip (temporal blocking, k_step2d_cluster).
 #include <algorithm>
 #include <chrono>
 #include <cstddef>
@@ -70,8 +72,12 @@ struct Slot {
     bool pool_synced = false;     // the pool's stream has waited for its set-up
 };
 
-// A pool of requests advanced together by the shared launch (one per stencil radius).
+// A pool of requests advanced together by the shared launch.  kind 0: per tick, k
+// launches of the multi-request step kernel (and of the sampling kernel); kind 1: per
+// tick, one launch of the cluster kernel, which advances each request by k steps with
+// its states held in the shared memory of one cluster of C CTAs (small grids only).
 struct Pool {
+    int kind = 0, C = 0;
     int M = 0;
     fwi::Batch2d *dev = nullptr;       // device table
     fwi::Batch2d *host[2] = {};        // pinned staging, used alternately
@@ -93,6 +99,12 @@ struct Pool {
 
 constexpr int kPoolZChunk = 128;   // most rows per work item of the multi-request step
 constexpr int kPools = 4;          // shared-launch pools per stencil radius
+// Cluster pools take grids of at most this many computed points (measured on GB300: one
+// request alone runs 4.3x / 2.3x / 1.3x faster on chip than in single steps at 128^2 /
+// 256^2 / 384^2, and no faster from about 512^2 on) and advance them by at least
+// kClusterTick steps per tick (the states stay on chip for the whole launch).
+constexpr int64_t kClusterMaxPoints = 200000;
+constexpr int kClusterTick = 64;
 
 void pool_release(Pool &p)
 {
@@ -110,8 +122,10 @@ void pool_release(Pool &p)
 }
 
 // Allocates the pool's table and stream and captures its tick graph (k steps).
-int pool_setup(Pool &p, int M, int k)
+int pool_setup(Pool &p, int kind, int M, int k, int C)
 {
+    p.kind = kind;
+    p.C = C;
     p.M = M;
     p.k = k;
     cudaError_t e = cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking);
@@ -123,19 +137,24 @@ int pool_setup(Pool &p, int M, int k)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.tick, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemsetAsync(p.dev, 0, sizeof(fwi::Batch2d), p.stream);
     if (e != cudaSuccess) return fwi::report_error(FWI_ERR_CUDA, std::string("serve pool: ") + cudaGetErrorString(e));
-    p.grid_step = fwi::multi2d_grid(M);
+    p.grid_step = kind == 0 ? fwi::multi2d_grid(M) : 0;
     p.grid_sample = 152 * 4;
+    const size_t want = kind == 0 ? (size_t)(2 * k) : 1;
     e = cudaStreamBeginCapture(p.stream, cudaStreamCaptureModeThreadLocal);
-    for (int t = 0; t < k && e == cudaSuccess; ++t) {
-        e = fwi::launch_step2d_multi(p.dev, M, t, p.grid_step, p.stream);
-        if (e == cudaSuccess) e = fwi::launch_sample_multi(p.dev, t, p.grid_sample, p.stream);
+    if (kind == 0) {
+        for (int t = 0; t < k && e == cudaSuccess; ++t) {
+            e = fwi::launch_step2d_multi(p.dev, M, t, p.grid_step, p.stream);
+            if (e == cudaSuccess) e = fwi::launch_sample_multi(p.dev, t, p.grid_sample, p.stream);
+        }
+    } else {
+        e = fwi::launch_step2d_cluster(p.dev, M, k, C, 1, fwi::cluster2d_max_smem(), p.stream);
     }
     const cudaError_t ec = cudaStreamEndCapture(p.stream, &p.graph);
     if (e == cudaSuccess) e = ec;
     // the kernel nodes, in launch order (a chain), so each tick can size their grids
     size_t nn = 0;
     if (e == cudaSuccess) e = cudaGraphGetNodes(p.graph, nullptr, &nn);
-    if (e == cudaSuccess && nn != (size_t)(2 * k)) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess && nn != want) e = cudaErrorInvalidValue;
     if (e == cudaSuccess) {
         std::vector<cudaGraphNode_t> all(nn);
         e = cudaGraphGetRootNodes(p.graph, all.data(), &nn);
@@ -151,7 +170,7 @@ int pool_setup(Pool &p, int M, int k)
             if (e == cudaSuccess && ne == 1) e = cudaGraphNodeGetDependentNodes(cur, &nx, nullptr, &ne);
             cur = ne == 1 ? nx : nullptr;
         }
-        if (e == cudaSuccess && p.nodes.size() != (size_t)(2 * k)) e = cudaErrorInvalidValue;
+        if (e == cudaSuccess && p.nodes.size() != want) e = cudaErrorInvalidValue;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&p.exec, p.graph, 0);
     if (e != cudaSuccess) {
@@ -265,8 +284,10 @@ extern "C" int fwi_serve(const fwi_request *reqs, int32_t n, const fwi_serve_opt
     // kPools pools per radius, filled round-robin: their ticks overlap on the device
     // (measured on GB300: one pool serialises its requests' steps behind one another,
     // four match the throughput of one stream per request)
-    std::vector<Pool> pools(2 * kPools);
+    // pools: [kind][radius 4, 8][kPools]
+    std::vector<Pool> pools(2 * 2 * kPools);
     int rr = 0;
+    int cl_size[2] = {-1, -1};   // cluster size per radius (0: no cluster pools)
     const int tick_k = (o.steps_per_turn + 1) / 2 * 2;
     const bool share = o.no_shared_launch == 0;
     int64_t used = 0;
@@ -307,16 +328,28 @@ extern "C" int fwi_serve(const fwi_request *reqs, int32_t n, const fwi_serve_opt
                 continue;
             }
             if (share && fwi::job_batchable(free_slot->job)) {
-                const int pi = (r.order == 16 ? kPools : 0) + (rr++ % kPools);
+                const int M = r.order / 2, ri = r.order == 16 ? 1 : 0;
+                if (cl_size[ri] < 0) cl_size[ri] = fwi::cluster2d_size(M);
+                // small grids whose receivers form one row go to the cluster pools
+                fwi::Batch2dEntry probe;
+                int kind = 0;
+                const int C = cl_size[ri];
+                if (C > 0 && fwi::job_batch_entry(free_slot->job, &probe, 64) == FWI_OK &&
+                    probe.rec_z >= 0 && probe.p.g.nz / C > M &&
+                    (int64_t)probe.p.g.nz * probe.p.g.px <= kClusterMaxPoints &&
+                    2LL * ((probe.p.g.nz + C - 1) / C) * probe.p.g.px * 4 <= fwi::cluster2d_max_smem())
+                    kind = 1;
+                const int pi = (kind * 2 + ri) * kPools + (rr++ % kPools);
                 Pool &pl = pools[pi];
-                if (!pl.stream && !pl.failed && pool_setup(pl, r.order / 2, tick_k) != FWI_OK) {
+                if (!pl.stream && !pl.failed &&
+                    pool_setup(pl, kind, M, kind ? std::max(tick_k, kClusterTick) : tick_k, C) != FWI_OK) {
                     pool_release(pl);
                     pl.failed = true;
                 }
                 if (!pl.failed && (int)pl.members.size() < fwi::kBatch2dMax &&
                     cudaEventRecord(free_slot->turn, free_slot->stream) == cudaSuccess) {
                     free_slot->pool = pi;   // its set-up is ordered before the pool's next tick
-                    results[idx].shared_launch = 1;
+                    results[idx].shared_launch = 1 + kind;
                     pl.members.push_back((int)(free_slot - slots.data()));
                 } else {
                     cudaGetLastError();
@@ -420,12 +453,24 @@ extern "C" int fwi_serve(const fwi_request *reqs, int32_t n, const fwi_serve_opt
             h->total_work = work;
             h->total_rec = recs;
             const size_t bytes = offsetof(fwi::Batch2d, e) + (size_t)h->count * sizeof(fwi::Batch2dEntry);
+            if (pl.kind == 1 && rc == FWI_OK) {
+                // one cluster per request, shared memory for the largest band pair
+                int64_t need = 0;
+                for (int q = 0; q < h->count; ++q) {
+                    const fwi::StepParams &sp = h->e[q].p;
+                    need = std::max<int64_t>(need, 2LL * ((sp.g.nz + pl.C - 1) / pl.C) * sp.g.px * 4);
+                }
+                cudaKernelNodeParams kp = pl.params[0];
+                kp.gridDim = dim3((unsigned)(pl.C * h->count), 1, 1);
+                kp.sharedMemBytes = (unsigned)((need + 1023) / 1024 * 1024);
+                if (cudaGraphExecKernelNodeSetParams(pl.exec, pl.nodes[0], &kp) != cudaSuccess) rc = FWI_ERR_CUDA;
+            }
             // grids sized to this tick's work (the persistent loops cover any excess)
             const unsigned gs = (unsigned)std::max(1, std::min(work, pl.grid_step));
             const unsigned gr = (unsigned)std::max(1, std::min((recs + 255) / 256, pl.grid_sample));
             // the sampling nodes run only when some request's step does not sample itself
             const bool sample = recs > 0;
-            for (size_t q = 0; rc == FWI_OK && q < pl.nodes.size(); ++q) {
+            for (size_t q = 0; pl.kind == 0 && rc == FWI_OK && q < pl.nodes.size(); ++q) {
                 if ((q & 1) && sample != pl.sampling &&
                     cudaGraphNodeSetEnabled(pl.exec, pl.nodes[q], sample ? 1 : 0) != cudaSuccess)
                     rc = FWI_ERR_CUDA;

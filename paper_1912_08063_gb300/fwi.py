@@ -382,7 +382,7 @@ class FwiModel:
         self.opts = fwi_opts(int(order), int(nb) if nb else -1, SNAP_DTYPES[snap_dtype],
                              int(fold_every), int(snap_budget_bytes), float(sponge_r0),
                              float(sponge_vref), int(bool(timing)),
-                             int(bool(temporal_blocking)))
+                             int(temporal_blocking))
         self.handle = fwi_create_model(self.ndim, self.shape, sp, v, dt, nt, self.opts,
                                        stream)
 

@@ -90,7 +90,7 @@ def test_graph_replayed_forward_equals_direct_call(shared):
     res, out = fwi.fwi_serve(reqs, max_active=4, steps_per_turn=6, snap_slots=4,
                              shared_launch=shared)
     n2d = sum(1 for r in reqs if r["v"].ndim == 2)
-    assert sum(x["shared_launch"] for x in res) == (n2d if shared else 0)
+    assert sum(1 for x in res if x["shared_launch"]) == (n2d if shared else 0)
     for r, x, o in zip(reqs, res, out):
         assert x["status"] == 0
         m = fwi.FwiModel(torch.from_numpy(r["v"]).cuda(), r["h"], r["dt"], r["nt"])
@@ -151,7 +151,7 @@ def test_served_results_match_the_oracle():
         r["arrival"] = 0.001 * i
     res, out = fwi.fwi_serve(reqs, max_active=8, steps_per_turn=4, snap_slots=6)
     assert all(x["status"] == 0 for x in res), res
-    assert res[fwd]["shared_launch"] == 1 and res[grd]["shared_launch"] == 0
+    assert res[fwd]["shared_launch"] > 0 and res[grd]["shared_launch"] == 0
     rf = reqs[fwd]
     ref = problem(rf, rf["v"]).forward()[0]
     e = _rel(np.asarray(out[fwd]).reshape(ref.shape), ref)
@@ -171,8 +171,8 @@ def test_shared_launch_equals_own_streams():
     requests ran in the shared launch, and several of them were in it at once."""
     from paper_1912_08063_gb300 import fwi
     reqs = _requests(12, seed=7)
-    for i, r in enumerate(reqs):
-        r["arrival"] = 0.001 * i
+    for r in reqs:
+        r["arrival"] = 0.0
     a, oa = fwi.fwi_serve(reqs, max_active=12, steps_per_turn=4, snap_slots=6)
     b, ob = fwi.fwi_serve(reqs, max_active=12, steps_per_turn=4, snap_slots=6,
                           shared_launch=False)
@@ -186,3 +186,39 @@ def test_shared_launch_equals_own_streams():
         assert a[i]["misfit"] == b[i]["misfit"]
     iv = sorted((a[i]["t_start"], a[i]["t_done"]) for i in pooled)
     assert any(y[0] < x[1] for x, y in zip(iv, iv[1:]))
+
+
+def test_cluster_launch_small_and_large_requests():
+    """Small 2-D forward requests run in the cluster launch (k steps per launch, both
+    states in the shared memory of one cluster), larger ones in the multi-request step
+    launch; both equal direct forward calls bit for bit, and one of each matches the
+    oracle."""
+    import oracle
+    from paper_1912_08063_gb300 import fwi
+
+    def dt_for(ndim, h):
+        lim = 1.0 / fwi.fwi_cfl_number(ndim, 8, (h, h, h), 4500.0, 1.0)
+        return math.floor(0.8 * lim * 1e4) / 1e4
+
+    reqs = synth.serving_requests(40, dt_for, seed=9, size2d=(40, 900), size3d=(20, 24),
+                                  nt_range=(30, 90), frac_grad=0.0, frac_2d=1.0)
+    for r in reqs:
+        r["arrival"] = 0.0
+    res, out = fwi.fwi_serve(reqs, max_active=16, steps_per_turn=8, snap_slots=4)
+    kinds = [x["shared_launch"] for x in res]
+    assert all(x["status"] == 0 for x in res) and 1 in kinds and 2 in kinds, kinds
+    for r, x, o in zip(reqs, res, out):
+        m = fwi.FwiModel(torch.from_numpy(r["v"]).cuda(), r["h"], r["dt"], r["nt"])
+        acq = fwi.Acquisition([r["src"]], r["rec"])
+        direct = m.forward(acq, torch.from_numpy(r["wavelet"][None]).cuda())[0].cpu().numpy()
+        m.close()
+        assert np.array_equal(np.asarray(o).reshape(direct.shape), direct), x["shared_launch"]
+    for kind in (1, 2):
+        i = min((j for j, k in enumerate(kinds) if k == kind), key=lambda j: reqs[j]["v"].size)
+        r = reqs[i]
+        ref = oracle.Problem(r["v"], r["h"], r["dt"], r["nt"], order=8, nb=20,
+                             src=np.asarray(r["src"])[None], rec=r["rec"],
+                             wavelet=r["wavelet"][None]).forward()[0]
+        e = _rel(np.asarray(out[i]).reshape(ref.shape), ref)
+        print(f"shared launch kind {kind}, {r['v'].shape}: traces rel-L2 {e:.2e}")
+        assert e <= 1e-4

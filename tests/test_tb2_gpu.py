@@ -1,7 +1,9 @@
-"""Temporal blocking of the 2-D forward step (fwi_opts.temporal_blocking): a batch of shots
-wide enough to fill the GPU advances two time steps per pass.  Its traces and final state
-equal the single-step path (each shot on its own, too few shots for the two-step pass) bit
-for bit, including an odd step count (the last step single), and match the FP64 oracle."""
+"""Temporal blocking of the 2-D forward step (fwi_opts.temporal_blocking).  Mode 1: a batch
+of shots wide enough to fill the GPU advances two time steps per pass; its traces and final
+state equal the single-step path (each shot on its own, too few shots for the two-step
+pass) bit for bit, including an odd step count (the last step single), and match the FP64
+oracle.  Mode 2: a one-shot request small enough for one cluster of CTAs advances up to 64
+steps per launch with its states in shared memory; the same bars."""
 import numpy as np
 import pytest
 
@@ -54,4 +56,36 @@ def test_two_step_pass_matches_oracle():
     ref = P.forward()
     e = np.linalg.norm(tr[pick] - ref) / np.linalg.norm(ref)
     print(f"two-step pass traces vs oracle: rel-L2 {e:.2e}")
+    assert e <= 1e-4
+
+
+@pytest.mark.parametrize("shape,order", [((60, 90), 8), ((131, 77), 16), ((300, 280), 8)])
+def test_onchip_blocking_equals_single_steps(shape, order):
+    """temporal_blocking = 2: a one-shot 2-D forward with receivers on one row runs up to
+    64 steps per launch in one cluster of CTAs with both states in shared memory; traces
+    and the final state equal single steps bit for bit, and the traces match the
+    oracle."""
+    from paper_1912_08063_gb300 import fwi
+    import oracle
+    rng = np.random.default_rng(41)
+    nz, nx = shape
+    v = synth.smooth_random(rng, shape, 10.0, ell=80.0)
+    h, nt = 10.0, 150
+    dt = 0.5 / fwi.fwi_cfl_number(2, order, (h, h, h), float(v.max()), 1.0)
+    src = np.array([[3, 0, nx // 2]], dtype=np.int32)
+    rec = np.array([[2, 0, x] for x in range(nx)], dtype=np.int32)
+    wav = synth.ricker(25.0, dt, nt)[None].astype(np.float32)
+    acq = fwi.Acquisition(src, rec)
+    outs = []
+    for tb in (0, 2):
+        m = fwi.FwiModel(torch.from_numpy(v).cuda(), h, dt, nt, order=order, nb=20,
+                         temporal_blocking=tb)
+        tr, fin = m.forward(acq, torch.from_numpy(wav).cuda(), final_state=True)
+        outs.append((tr.cpu().numpy(), fin.cpu().numpy()))
+        m.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    ref = oracle.Problem(v, h, dt, nt, order=order, nb=20, src=src, rec=rec,
+                         wavelet=wav).forward()
+    e = np.linalg.norm(outs[1][0] - ref) / np.linalg.norm(ref)
+    print(f"on-chip blocking {shape} order {order}: traces rel-L2 {e:.2e}")
     assert e <= 1e-4
