@@ -589,47 +589,18 @@ __device__ __forceinline__ void run_segment(Ctx<C, MODE> &c, int col, int z0, in
     c.pbase += c.nout;
 }
 
-// Walks this CTA's share of the persistent schedule (plan_persistent): in each of the
-// p.rounds rounds CTA k < p.round_ctas takes unit u = r p.round_ctas + k (z-part
-// h = u / columns, planes [h nz / zparts, (h + 1) nz / zparts), of tile column
-// u mod columns); the leftover units, all in the last z-part,
-// are cut along z into p.rem_ctas equal pieces, one per CTA (a piece may end one column
-// and start the next).  seg(col, z0, z1) streams one segment; the walk stops when the
-// CTA's abort flag is raised.
+// Walks this CTA's share of the persistent schedule (plan_persistent, schedule_segment):
+// seg(col, z0, z1) streams one segment; the walk stops when the CTA's abort flag is
+// raised.  Every thread of the CTA takes the same segments.
 template <class Seg>
 __device__ __forceinline__ void walk_schedule(const Step3dParams &p, int columns, const int *abort_flag,
                                               Seg &&seg)
 {
-    const int k = blockIdx.x;
-    bool go = true;
-    for (int i = 0; go && i < p.rounds; ++i) {
-        if (k < p.round_ctas) {
-            const int u = i * p.round_ctas + k;
-            const int h = u / columns;
-            seg(u - h * columns, (int)((int64_t)h * p.nz / p.zparts),
-                (int)((int64_t)(h + 1) * p.nz / p.zparts));
-        }
+    int col, z0, z1;
+    for (int i = 0; schedule_segment(p, columns, (int)blockIdx.x, i, &col, &z0, &z1); ++i) {
+        seg(col, z0, z1);
         __syncthreads();
-        go = !*(volatile const int *)abort_flag;
-    }
-    const int first = p.rounds * p.round_ctas;
-    const int rem = columns * p.zparts - first;
-    if (go && rem > 0 && k < p.rem_ctas) {
-        const int zb = (int)((int64_t)(p.zparts - 1) * p.nz / p.zparts);   // last part: zb .. nz - 1
-        const int len_u = p.nz - zb;
-        const int64_t total = (int64_t)rem * len_u;
-        const int64_t len = (total + p.rem_ctas - 1) / p.rem_ctas;
-        int64_t s0 = (int64_t)k * len;
-        const int64_t s1 = s0 + len < total ? s0 + len : total;
-        while (go && s0 < s1) {
-            const int u = first + (int)(s0 / len_u);
-            const int z0 = zb + (int)(s0 % len_u);
-            const int z1 = (int)(z0 + (s1 - s0) < p.nz ? z0 + (s1 - s0) : p.nz);
-            seg(u % columns, z0, z1);
-            s0 += z1 - z0;
-            __syncthreads();
-            go = !*(volatile const int *)abort_flag;
-        }
+        if (*(volatile const int *)abort_flag) break;
     }
 }
 

@@ -24,9 +24,13 @@ struct Step3dParams {
     int nshots;
     int rounds, round_ctas;       // whole-unit rounds and the CTAs each round uses
     int rem_ctas;                 // CTAs sharing the leftover units along z
-    int zparts;                   // a unit is z-part h, planes [h nz / zparts,
-                                  // (h + 1) nz / zparts), of a tile column; units are
-                                  // numbered part-major
+    int zparts, zfirst;           // a unit is z-part h of a tile column: planes
+                                  // [h zfirst, (h + 1) zfirst), the last part up to nz;
+                                  // units are numbered part-major
+    int rem_first, rem_ppu;       // leftover units go to CTAs rem_first ..
+                                  // rem_first + rem_ctas - 1: cut into rem_ppu aligned
+                                  // pieces each (rem_ppu > 0), or as one run cut into
+                                  // equal pieces that may cross units (rem_ppu = 0)
     float cx[kMaxM + 1], cy[kMaxM + 1], cz[kMaxM + 1], c0;
     float2 cy2[kMaxM + 1], cz2[kMaxM + 1], c02;   // the same weights as packed pairs
     int iso;                      // hx = hy = hz: the isotropic instantiation may run
@@ -102,14 +106,66 @@ Step3dKernelInfo step3d_kernel_tm8(int mode, bool iso);
 int encode_field_map(CUtensorMap *map, const void *base, const Geom &g, int nshots, int bx,
                      int by, int elem_bytes, int64_t shot_stride);
 
+// Segment idx (0, 1, ...) of CTA k in the persistent schedule of p over `columns` tile
+// columns: tile column *col, output planes [*z0, *z1).  Returns false past its last
+// segment.  The kernels walk it (k = blockIdx.x) and the planner evaluates it, so both
+// read the same schedule.
+__host__ __device__ inline bool schedule_segment(const Step3dParams &p, int columns, int k, int idx,
+                                                 int *col, int *z0, int *z1)
+{
+    const int S = p.zparts;
+    if (k < p.round_ctas) {
+        if (idx < p.rounds) {
+            const int u = idx * p.round_ctas + k;
+            const int h = u / columns;
+            *col = u - h * columns;
+            *z0 = h * p.zfirst;
+            *z1 = h == S - 1 ? p.nz : *z0 + p.zfirst;
+            return true;
+        }
+        idx -= p.rounds;
+    }
+    const int first = p.rounds * p.round_ctas;   // first leftover unit
+    const int rem = columns * S - first;
+    const int kk = k - p.rem_first;
+    if (rem <= 0 || kk < 0 || kk >= p.rem_ctas) return false;
+    const int zb = (S - 1) * p.zfirst;            // the leftover units lie in the last part
+    const int len_u = p.nz - zb;
+    if (p.rem_ppu > 0) {                          // aligned pieces, one per CTA
+        if (idx > 0) return false;
+        const int u = first + kk / p.rem_ppu, piece = kk % p.rem_ppu;
+        const int plen = (len_u + p.rem_ppu - 1) / p.rem_ppu;
+        *col = u % columns;
+        *z0 = zb + piece * plen;
+        *z1 = *z0 + plen < p.nz ? *z0 + plen : p.nz;
+        return *z0 < *z1;
+    }
+    const int64_t total = (int64_t)rem * len_u;
+    const int64_t len = (total + p.rem_ctas - 1) / p.rem_ctas;
+    const int64_t s0 = (int64_t)kk * len;
+    const int64_t s1 = s0 + len < total ? s0 + len : total;
+    const int64_t start = idx == 0 ? s0 : (s0 / len_u + idx) * len_u;
+    if (start >= s1) return false;
+    const int64_t end = (start / len_u + 1) * len_u < s1 ? (start / len_u + 1) * len_u : s1;
+    const int u = first + (int)(start / len_u);
+    *col = u % columns;
+    *z0 = zb + (int)(start % len_u);
+    *z1 = *z0 + (int)(end - start);
+    return true;
+}
+
 // Persistent schedule of one launch over `columns` tile columns of nz planes on
 // `resident` CTAs: rounds of whole units, then the leftover units cut along z into
 // pieces of at least 4M planes (each piece streams 2M warm-up planes).  A unit is a whole
 // column, or, with `in_step` and fewer columns than CTAs, one of S = ceil(resident /
 // columns) z-parts of a column that begin at the same z in every column: the CTAs of a
 // round then stream z in step part by part, so a tile's halo planes are still in L2 when
-// its neighbours read them (a field larger than L2 needs this).  Fills p.rounds,
-// p.round_ctas, p.rem_ctas, p.zparts and returns the grid size.
+// its neighbours read them (a field larger than L2 needs this).  With z-parts the planner
+// compares equal parts (leftovers cut over all CTAs, as one run or in pieces aligned to
+// the leftover units) with longer first parts whose leftover last parts go, in aligned
+// pieces, to the CTAs that ran a last part, and keeps the one whose busiest CTA streams
+// the fewest planes (warm-up planes included).  Fills the schedule fields of p and
+// returns the grid size.
 int plan_persistent(Step3dParams &p, int columns, int resident, bool in_step = false);
 
 }  // namespace fwi
