@@ -101,7 +101,7 @@ def workload(name, nt_override, n=0):
 
 
 STEP3D_SOURCES = ["k_step3d.cuh", "k_step3d_m8.cu", "k_step3d_m4.cu", "k_step3d.cu", "step3d.h",
-                  "code16.cuh", "k_step3d_tm.cuh", "k_step3d_tm8.cu", "tmap.cpp"]
+                  "code16.cuh", "k_step3d_tm.cuh", "k_step3d_tm8.cu", "k_step3d_tm4.cu", "tmap.cpp"]
 
 
 def kernel_source_hash():

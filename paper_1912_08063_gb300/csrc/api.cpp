@@ -587,7 +587,8 @@ int step3d_launch(fwi_model *m, const StepParams &p, int ns, int mode, cudaStrea
     q.sig_y = sig_y(m);
     q.sig_z = sig_z(m);
     q.err = m->d_flag;
-    const int TY = step3d_variant(g.M).ty;
+    if (mode == kModeStep && p.st_code) mode = kModeStepStore;
+    const int TY = step3d_variant(g.M, mode).ty;
     CUtensorMap mc, ma, mb, md, me;
     FWI_TRY(field_map(m, p.cur, ns, 64 + 2 * g.M, TY + 2 * g.M, &mc));
     FWI_TRY(field_map(m, p.prev, ns, 64, TY, &ma));

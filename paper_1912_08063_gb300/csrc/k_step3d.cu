@@ -11,34 +11,38 @@
 
 namespace fwi {
 
-// Configuration per radius; FWI_STEP3D_VARIANT=<ty>,<ry>,<pf>,<u>,<opt>[,<opt_rev>]
-// overrides it for tuning runs (only the instantiated combinations are accepted), and
-// FWI_STEP3D_TMEM=0/1 turns the tensor-memory kernel off/on at radius 8 (on by default:
-// measured faster in every mode on GB300).  At
-// radius 8 the queue shifts every 2 planes and all modes take the packed x-sums, as
-// measured fastest on GB300 (against U = 3 and scalar x-sums).
-Step3dVariant step3d_variant(int M)
+// Configuration per radius and mode; FWI_STEP3D_VARIANT=<ty>,<ry>,<pf>,<u>,<opt>[,<opt_rev>]
+// overrides the register-queue kernel's configuration for tuning runs (only the
+// instantiated combinations are accepted), and FWI_STEP3D_TMEM=0/1 turns the
+// tensor-memory kernel off/on in every mode.  By default, as measured on GB300: the
+// tensor-memory kernel in every mode at radius 8, and at radius 4 in the forward modes
+// (forward 0.090 -> 0.087 ms, forward + store 0.108 -> 0.085 ms at 296^3) but not in the
+// reverse mode (0.1165 against 0.1194 ms).  The register-queue kernel at radius 8 shifts
+// its queue every 2 planes and takes the packed x-sums in all modes (measured fastest
+// against U = 3 and scalar x-sums).
+Step3dVariant step3d_variant(int M, int mode)
 {
     Step3dVariant v = M == 8 ? Step3dVariant{32, 2, 2, 2, 1, 1, 1} : Step3dVariant{16, 2, 3, 2, 0, 0, 0};
-    if (M == 8)
-        if (const char *e = std::getenv("FWI_STEP3D_TMEM")) v.tm = std::atoi(e) != 0;
+    if (M == 4) v.tm = mode != kModeAdj;
+    if (const char *e = std::getenv("FWI_STEP3D_TMEM")) v.tm = std::atoi(e) != 0;
     if (const char *e = std::getenv("FWI_STEP3D_VARIANT")) {
         int ty, ry, pf, un, opt, optr;
         const int n = std::sscanf(e, "%d,%d,%d,%d,%d,%d", &ty, &ry, &pf, &un, &opt, &optr);
         if (n == 5 || n == 6) {
             Step3dVariant w{ty, ry, pf, un, opt, n == 6 ? optr : opt, 0};
             bool ok = true;
-            for (int mode = 0; mode < 3; ++mode)
-                ok = ok && (M == 8 ? step3d_kernel_m8(w, mode) : step3d_kernel_m4(w, mode)).fn;
+            for (int md = 0; md < 3; ++md)
+                ok = ok && (M == 8 ? step3d_kernel_m8(w, md) : step3d_kernel_m4(w, md)).fn;
             if (ok) v = w;
         }
     }
+    if (v.tm) v.ty = 32;
     return v;
 }
 
 static Step3dKernelInfo kernel_info(int M, int mode, bool iso = false)
 {
-    const Step3dVariant v = step3d_variant(M);
+    const Step3dVariant v = step3d_variant(M, mode);
     if (M == 8) return step3d_kernel_m8(v, mode, iso);
     if (M == 4) return step3d_kernel_m4(v, mode, iso);
     return Step3dKernelInfo{nullptr, 0, 0};

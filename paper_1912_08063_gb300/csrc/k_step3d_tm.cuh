@@ -1,4 +1,4 @@
-// 3-D time step on GB300 (sm_103a), radius 8: the z-stream held in tensor memory.
+// 3-D time step on GB300 (sm_103a), radius 8 and 4: the z-stream held in tensor memory.
 //
 // Same three modes and the same arithmetic contract as k_step3d.cuh (kModeStep,
 // kModeStepStore, kModeAdj; Eq. 3 with the sponge, the W-weighted reverse step and the
@@ -12,7 +12,7 @@
 //     from the planes already streamed, and the output plane j = i - M is finished as
 //     L(j) = P(j) + sum_k c_k u(j + k)  (the future half, planes j + 1 .. i);
 //   * the planes i - M .. i - 1 of u and the partials P(i - M) .. P(i - 1) live in two
-//     rings of M slots in tensor memory (TMEM, 256 columns per CTA, 128 per thread:
+//     rings of M slots in tensor memory (TMEM, 32 M columns per CTA, 16 M per thread:
 //     each thread owns one TMEM lane and 8 values per slot), read with tcgen05.ld and
 //     written with tcgen05.st at addresses computed from the plane index, so the queue
 //     never moves between registers;
@@ -25,12 +25,13 @@
 // checkpoint store, 26 or 28 in kModeAdj.
 //
 // TMEM: warp w reads and writes lanes 32 (w mod 4) .. 32 (w mod 4) + 31 (the lane
-// quarter the hardware gives it) and columns 128 (w / 4) .. 128 (w / 4) + 127 of its
-// CTA's allocation: raw ring at columns 0 .. 63 (slot s = plane mod 8 at 8 s), partial
-// ring at 64 .. 127.  Allocation is made by warp 0 at the start and released by warp 0
-// at the end, on every path (including a bounded wait that gave up).  An SM holds at most
-// two CTAs of these kernels (their shared memory sees to that), and two allocations of
-// 256 columns fit its 512, so an allocation never waits.
+// quarter the hardware gives it) and columns 16 M (w / 4) .. 16 M (w / 4) + 16 M - 1 of
+// its CTA's allocation: raw ring at the first 8 M of those (slot s = plane mod M at 8 s),
+// partial ring at the next 8 M.  Allocation is made by warp 0 at the start and released
+// by warp 0 at the end, on every path (including a bounded wait that gave up).  An SM
+// holds at most two CTAs of these kernels (their shared memory sees to that), and their
+// allocations (256 columns each at radius 8, 128 at radius 4) fit its 512, so an
+// allocation never waits.
 #pragma once
 
 #include "k_step3d.cuh"
@@ -54,20 +55,23 @@ using s3d::tma_load4;
 constexpr int kPackX = s3d::kPackX, kIso = s3d::kIso;
 
 // ---- tensor memory (tcgen05) ----
-constexpr uint32_t kTmemCols = 256;
+// Columns per CTA at radius M: two rings of M slots of 8 columns for each of the two warps
+// that share a lane quarter.
+template <int M>
+__host__ __device__ constexpr uint32_t tmem_cols() { return 32u * M; }
 
-__device__ __forceinline__ void tmem_alloc(uint32_t *dst)
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t cols)
 {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(dst)),
-                 "r"(kTmemCols)
+                 "r"(cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr)
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols)
 {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTmemCols)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols)
                  : "memory");
 }
 
@@ -162,7 +166,8 @@ struct Cfg {
     static constexpr int NTX = TX / RX, NTY = TY / RY, NT = NTX * NTY;
     static constexpr int SX = TX + 2 * M, SY = TY + 2 * M;
     static constexpr int SH = P + 1, SP = PP + 1;
-    static_assert(M == 8, "the TMEM rings hold M = 8 slots (plane mod 8)");
+    static_assert(M == 8 || M == 4, "the TMEM rings hold M slots (plane mod M)");
+    static constexpr uint32_t RING = 8u * M;   // columns of one ring
     static_assert(NT == 256 && RX * RY == 8, "8 values per TMEM slot, 8 warps");
     static constexpr int HALO_BYTES = SX * SY * 4;
     static constexpr int TILE_BYTES = TX * TY * 4;
@@ -170,8 +175,9 @@ struct Cfg {
     static constexpr int PW_STRIDE = (NPW * TILE_BYTES + 127) / 128 * 128;
     static constexpr int MISC = 256;   // barriers, flags, scales, sponge groups, TMEM base
     static constexpr int SMEM = SH * HALO_STRIDE + SP * PW_STRIDE + MISC + 1024;
-    // at most two CTAs per SM: the TMEM of two (2 x 256 columns) is all an SM has
-    static_assert(3 * (SMEM + 1024) > 233472, "a third CTA per SM would wait for TMEM");
+    // the CTAs that shared memory admits per SM never need more TMEM than the SM's 512
+    // columns, so an allocation never waits
+    static_assert((233472 / (SMEM + 1024)) * tmem_cols<M>() <= 512, "a CTA would wait for TMEM");
     static_assert(2 * (SMEM + 1024) <= 233472, "two CTAs per SM");
 };
 
@@ -358,11 +364,12 @@ struct Ctx {
         } else {
             // the previous iteration's TMEM stores must have landed before these loads
             tmem_wait_st();
-            // planes i-1 .. i-4 and the partial P(j) (the slot P(i) will take), then planes
-            // i-5 .. i-8 (i - 8 = j)
+            // planes i-1 .. i-4 and the partial P(j) (the slot P(i) will take), then, at
+            // radius 8, planes i-5 .. i-8 (i - M = j)
+            constexpr uint32_t RM = C::RING - 1;
             Slot8 q1, q2, q3, q4, pj;
-            tmem_ld5x8(traw + ((slot - 8u) & 63u), traw + ((slot - 16u) & 63u),
-                       traw + ((slot - 24u) & 63u), traw + ((slot - 32u) & 63u), tpart + slot, q1,
+            tmem_ld5x8(traw + ((slot - 8u) & RM), traw + ((slot - 16u) & RM),
+                       traw + ((slot - 24u) & RM), traw + ((slot - 32u) & RM), tpart + slot, q1,
                        q2, q3, q4, pj);
             float2 lacc[RY][2];
             // plane i - m enters P(i) with c_m and L(j) (j = i - M) with c_{M-m}
@@ -391,12 +398,14 @@ struct Ctx {
             add(q2, 2);
             add(q3, 3);
             add(q4, 4);
-            tmem_ld4x8(traw + ((slot - 40u) & 63u), traw + ((slot - 48u) & 63u),
-                       traw + ((slot - 56u) & 63u), traw + slot, q1, q2, q3, q4);
-            add(q1, 5);
-            add(q2, 6);
-            add(q3, 7);
-            add(q4, 8);
+            if constexpr (M == 8) {
+                tmem_ld4x8(traw + ((slot - 40u) & RM), traw + ((slot - 48u) & RM),
+                           traw + ((slot - 56u) & RM), traw + slot, q1, q2, q3, q4);
+                add(q1, 5);
+                add(q2, 6);
+                add(q3, 7);
+                add(q4, 8);
+            }
             const Slot8 uj = q4;
             // the raw slot of plane i - M = j and the partial slot of P(j) are read: refill
             tmem_st8(traw + slot, ctr[0], ctr[1]);
@@ -628,7 +637,7 @@ k_step3d_tm(const __grid_constant__ Step3dParams p, const __grid_constant__ CUte
     c.mxa = c.mxd = 0.0f;
 
     const int warp = c.tid >> 5;
-    if (warp == 0) tmem_alloc(tbase);
+    if (warp == 0) tmem_alloc(tbase, tmem_cols<M>());
     if (c.tid == 0) {
         for (int i = 0; i < C::SH; ++i) mbar_init(c.bar_h + i, 1);
         for (int i = 0; i < C::SP; ++i) mbar_init(c.bar_p + i, 1);
@@ -641,8 +650,8 @@ k_step3d_tm(const __grid_constant__ Step3dParams p, const __grid_constant__ CUte
     {
         const uint32_t t = *(volatile uint32_t *)tbase;
         const uint32_t lane = (uint32_t)(32 * (warp & 3)) << 16;
-        c.traw = t + lane + (uint32_t)(128 * (warp >> 2));
-        c.tpart = c.traw + 64u;
+        c.traw = t + lane + (uint32_t)(2 * C::RING * (warp >> 2));
+        c.tpart = c.traw + C::RING;
     }
 
     const int tiles_x = (p.nx + C::TX - 1) / C::TX;
@@ -654,7 +663,7 @@ k_step3d_tm(const __grid_constant__ Step3dParams p, const __grid_constant__ CUte
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
-    if (warp == 0) tmem_dealloc(*(volatile uint32_t *)tbase);
+    if (warp == 0) tmem_dealloc(*(volatile uint32_t *)tbase, tmem_cols<M>());
     if (*(volatile int *)c.abort_flag && c.tid == 0) {
         atomicOr(p.err, 2u);
         for (int q = c.h_issued - C::SH > 0 ? c.h_issued - C::SH : 0; q < c.h_issued; ++q)
@@ -680,7 +689,7 @@ Step3dKernelInfo kernel_info(int mode)
         k.threads = C::NT;
         k.smem = C::SMEM;
     }
-    k.tmem_cols = (int)kTmemCols;
+    k.tmem_cols = (int)tmem_cols<M>();
     return k;
 }
 

@@ -62,13 +62,13 @@ struct Step3dParams {
 // used for radius M.
 // Tile height, rows per thread, prefetch depth, queue shift interval, and the option bits
 // (Cfg::F) of the plain forward step (opt) and of the store and reverse modes (opt_rev);
-// tm = 1 selects the radius-8 kernel whose z-stream lives in tensor memory
-// (k_step3d_tm.cuh: 64 x 32 tiles, two CTAs per SM; the other fields then do not apply).
+// tm = 1 selects the kernel whose z-stream lives in tensor memory (k_step3d_tm.cuh:
+// 64 x 32 tiles, two CTAs per SM; ty is then 32 and the other fields do not apply).
 struct Step3dVariant {
     int ty, ry, pf, u, opt, opt_rev;
     int tm;
 };
-Step3dVariant step3d_variant(int M);
+Step3dVariant step3d_variant(int M, int mode);
 int step3d_smem_bytes(int M);
 int step3d_threads(int M);
 // Resident CTAs of the 3-D step kernel of `mode` on the current device (SMs x CTAs per
@@ -97,8 +97,9 @@ struct Step3dKernelInfo {
 // (scaled by 1 / h^2 once per point) may be returned.
 Step3dKernelInfo step3d_kernel_m4(const Step3dVariant &v, int mode, bool iso = false);
 Step3dKernelInfo step3d_kernel_m8(const Step3dVariant &v, int mode, bool iso = false);
-// The tensor-memory radius-8 kernel (k_step3d_tm8.cu).
+// The tensor-memory kernels (k_step3d_tm8.cu, k_step3d_tm4.cu).
 Step3dKernelInfo step3d_kernel_tm8(int mode, bool iso);
+Step3dKernelInfo step3d_kernel_tm4(int mode, bool iso);
 
 // Encodes a 4-D tensor map over shots of a field laid out as in Geom (elements of
 // `elem_bytes` = 4 or 2, shots `shot_stride` elements apart), with box (bx, by, 1, 1) and

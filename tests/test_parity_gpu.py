@@ -415,15 +415,17 @@ def test_model_reuse_across_checkpoint_layouts():
     assert torch.equal(g1a, fresh(acq1, 1)) and torch.equal(g2, fresh(acq2, 2))
 
 
+@pytest.mark.parametrize("order", [16, 8])
 @pytest.mark.parametrize("tmem", ["1", "0"])
-def test_radius8_step_kernels_both_variants(tmem, monkeypatch):
-    """The radius-8 3-D steps run either the tensor-memory kernel (the default: z-stream
-    in TMEM, two CTAs per SM) or the register-queue kernel (FWI_STEP3D_TMEM=0); both
-    match the oracle in every mode: forward, forward with checkpoint stores, reverse
-    step with imaging (FP16 checkpoints, recomputation)."""
+def test_step_kernels_both_variants(tmem, order, monkeypatch):
+    """The 3-D steps run either the tensor-memory kernel (z-stream in TMEM, two CTAs per
+    SM; FWI_STEP3D_TMEM=1) or the register-queue kernel (FWI_STEP3D_TMEM=0), at radius 8
+    and radius 4; every combination matches the oracle in every mode: forward, forward
+    with checkpoint stores, reverse step with imaging (FP16 checkpoints,
+    recomputation)."""
     monkeypatch.setenv("FWI_STEP3D_TMEM", tmem)
     rng = np.random.default_rng(31)
-    w = synth.random_small(rng, 3, (22, 37, 70), nt=70, order=16, nb=4, nrec=9)
+    w = synth.random_small(rng, 3, (22, 37, 70), nt=70, order=order, nb=4, nrec=9)
     m, p, acq = make_pair(w, snap="fp16", budget=1)
     probe = m.info()
     field = probe["computed"][0] * probe["computed"][1] * probe["pitch_x"]
@@ -438,7 +440,7 @@ def test_radius8_step_kernels_both_variants(tmem, monkeypatch):
     info = m.info()
     rphi, rg = p.gradient(dobs.astype(np.float64))
     eg = rel(g.cpu().numpy(), rg)
-    print(f"radius 8, TMEM {tmem}: traces {et:.2e}, gradient {eg:.2e}, "
+    print(f"order {order}, TMEM {tmem}: traces {et:.2e}, gradient {eg:.2e}, "
           f"slots {info['snap_slots']}, forward steps {info['last_forward_steps']}")
     assert 0 < info["snap_slots"] < w.nt
     assert et <= TOL_FWD and eg <= TOL_GRAD16
