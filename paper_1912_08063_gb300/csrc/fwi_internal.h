@@ -72,6 +72,8 @@ struct StepParams {
     unsigned *maxbits;        // nullable, forward step only: per shot, raise [2s] / [2s+1]
                               // to the bits of max|out| / max|out - cur| (the checkpoint
                               // codec's scales of the new state pair)
+    unsigned *err;            // TMA-staged kernels: status word, bit 1 (value 2) = a
+                              // bounded wait gave up
 };
 
 // An off-grid source or receiver (Kaiser-windowed sinc point): taps at the computed-grid

@@ -155,6 +155,17 @@ __host__ __device__ inline bool schedule_segment(const Step3dParams &p, int colu
     return true;
 }
 
+// 3-D map [shot][z][x] of a 2-D field (elements of elem_bytes = 4 or 2, shots
+// `shot_stride` elements apart) with box (bx, 1, 1) and zero fill outside the grid.
+int encode_field_map2d(CUtensorMap *map, const void *base, const Geom &g, int nshots, int bx,
+                       int elem_bytes, int64_t shot_stride);
+
+// The TMA-staged 2-D step (k_step2d_tma.cu).  maps: the streamed field with boxes of 256
+// and of M columns, prev, W (one shot), and for the reverse step aux and g (each with a
+// 256-column box); the launcher picks the z-chunks.
+cudaError_t launch_step2d_tma(const StepParams &p, int nshots, bool imaging, const CUtensorMap *maps,
+                              cudaStream_t s);
+
 // Persistent schedule of one launch over `columns` tile columns of nz planes on
 // `resident` CTAs: rounds of whole units, then the leftover units cut along z into
 // pieces of at least 4M planes (each piece streams 2M warm-up planes).  A unit is a whole

@@ -39,6 +39,35 @@ int encode_field_map(CUtensorMap *map, const void *base, const Geom &g, int nsho
     return r == CUDA_SUCCESS ? 0 : -1;
 }
 
+int encode_field_map2d(CUtensorMap *map, const void *base, const Geom &g, int nshots, int bx,
+                       int elem_bytes, int64_t shot_stride)
+{
+    if (elem_bytes != 4 && elem_bytes != 2) return -1;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !f) {
+            cudaGetLastError();
+            return -1;
+        }
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }
+    const cuuint64_t eb = (cuuint64_t)elem_bytes;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.nz, (cuuint64_t)nshots};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.px * eb, (cuuint64_t)shot_stride * eb};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, 1, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt =
+        elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    CUresult r = encode(map, dt, 3, const_cast<void *>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -1;
+}
+
 // Planes (with warm-up) the busiest CTA streams under schedule p.
 static int64_t schedule_cost(const Step3dParams &p, int columns, int grid)
 {

@@ -445,3 +445,24 @@ def test_step_kernels_both_variants(tmem, order, monkeypatch):
     assert 0 < info["snap_slots"] < w.nt
     assert et <= TOL_FWD and eg <= TOL_GRAD16
     assert abs(phi.item() - rphi) <= TOL_GRAD32 * rphi
+
+
+@pytest.mark.parametrize("tma", ["1", "0"])
+def test_2d_step_kernels_both_variants(tma, monkeypatch):
+    """The 2-D step runs either the register-streaming kernel (default) or the TMA-staged
+    one (FWI_STEP2D_TMA=1); traces and FP32-checkpoint gradients equal each other bit for
+    bit and match the oracle, for a batch of shots at orders 8 and 16."""
+    monkeypatch.setenv("FWI_STEP2D_TMA", tma)
+    rng = np.random.default_rng(33)
+    for order in (8, 16):
+        w = synth.random_small(rng, 2, (61, 300), nt=90, order=order, nb=6, nrec=11)
+        m, p, acq = make_pair(w, snap="fp32")
+        wav = torch.from_numpy(w.wavelets()).cuda()
+        tr = m.forward(acq, wav).cpu().numpy()
+        ref = p.forward()
+        dobs = (ref * 0.8).astype(np.float32)
+        phi, g = m.gradient(acq, wav, torch.from_numpy(dobs).cuda())
+        rphi, rg = p.gradient(dobs.astype(np.float64))
+        et, eg = rel(tr, ref), rel(g.cpu().numpy(), rg)
+        print(f"2-D order {order}, TMA {tma}: traces {et:.2e}, gradient {eg:.2e}")
+        assert et <= TOL_FWD and eg <= TOL_GRAD32
