@@ -195,6 +195,11 @@ struct fwi_model {
     };
     std::vector<MapEntry> maps;
     std::vector<MapEntry> maps2;   // 3-D maps of 2-D fields
+    // 3-D: every receiver a node of computed plane rec_fuse_z, distinct per shot: the step
+    // kernels sample and inject at them from rec_map ([shot][y][x] receiver index or -1);
+    // -1 otherwise
+    DevBuf rec_map;
+    int rec_fuse_z = -1;
     DevBuf cl_tab;                 // one-entry table of the on-chip 2-D forward launch
     Batch2d *cl_host = nullptr;    // its pinned staging
     cudaEvent_t cl_up = nullptr;   // the staging's last upload finished
@@ -208,7 +213,7 @@ struct fwi_model {
     {
         size_t b = v.bytes + W.bytes + sig.bytes + g32.bytes + g64.bytes + traces.bytes +
                    src_off.bytes + rec_off.bytes + inj.bytes + src_scale.bytes + maxbits.bytes +
-                   partials.bytes + phi.bytes + snaps.bytes + scales.bytes;
+                   partials.bytes + phi.bytes + snaps.bytes + scales.bytes + rec_map.bytes;
         for (int i = 0; i < 2; ++i) b += u[i].bytes + mu[i].bytes + stage_out[i].bytes;
         for (int i = 0; i < 3; ++i) b += stage_in[i].bytes;
         return (int64_t)b;
@@ -491,6 +496,30 @@ int ensure_workspace(fwi_model *m, const fwi_acq *a, bool grad, cudaStream_t s)
         if (og_r)
             FWI_CU(cudaMemcpyAsync(m->rec_pts.p, rp.data(), rp.size() * sizeof(PointTaps),
                                    cudaMemcpyHostToDevice, s));
+        // receivers on one plane at distinct nodes: map them for the step kernels
+        m->rec_fuse_z = -1;
+        std::vector<int32_t> rmap;
+        const char *fz = std::getenv("FWI_STEP3D_REC_FUSE");   // 0: separate kernels
+        if (m->ndim == 3 && !og_r && nr > 0 && !(fz && std::atoi(fz) == 0)) {
+            const int64_t plane = m->g.plane;
+            const int z0 = (int)(ro[0] / plane);
+            bool ok = true;
+            for (size_t i = 0; ok && i < ro.size(); ++i) ok = ro[i] / plane == z0;
+            if (ok) {
+                rmap.assign((size_t)ns * plane, -1);
+                for (int sh = 0; ok && sh < ns; ++sh)
+                    for (int r = 0; ok && r < nr; ++r) {
+                        int32_t &slot = rmap[(size_t)sh * plane + (size_t)(ro[(size_t)sh * nr + r] % plane)];
+                        ok = slot < 0;
+                        slot = r;
+                    }
+            }
+            if (ok && m->rec_map.ensure(rmap.size() * sizeof(int32_t)) == FWI_OK) {
+                FWI_CU(cudaMemcpyAsync(m->rec_map.p, rmap.data(), rmap.size() * sizeof(int32_t),
+                                       cudaMemcpyHostToDevice, s));
+                m->rec_fuse_z = z0;
+            }
+        }
         FWI_CU(cudaStreamSynchronize(s));   // host temporaries
         if (og_s) { m->geo_src.clear(); m->geo_src_pos.assign(a->src_pos, a->src_pos + nsrc); }
         else { m->geo_src_pos.clear(); m->geo_src.assign(a->src, a->src + nsrc); }
@@ -617,6 +646,19 @@ int step3d_launch(fwi_model *m, const StepParams &p, int ns, int mode, cudaStrea
         q.g = p.gacc;
         q.aux_fmt = p.aux_fmt;
         q.aux_scale = p.aux_scale;
+    }
+    // receivers handled in the epilogue: samples of a forward step that records traces
+    // (node source: off-grid source taps are added after the step, before sampling), the
+    // residual injection of a reverse step with imaging
+    if (m->rec_fuse_z >= 0 &&
+        (mode == kModeAdj ? p.inj_q != nullptr : (p.rec_tr != nullptr && !m->og_src))) {
+        q.rec_map = m->rec_map.as<int>();
+        q.rec_z = m->rec_fuse_z;
+        q.nrec = m->geo_nrec;
+        q.rec_tr = p.rec_tr;
+        q.inj_q = p.inj_q;
+        q.inj_scale = p.inj_scale;
+        q.inj_n = p.inj_n;
     }
     ensure_resident(m);
     const int tiles = ((g.nx + 63) / 64) * ((g.ny + TY - 1) / TY);
@@ -868,6 +910,8 @@ int after_forward_step(fwi_model *m, const StepParams &p, float *next, int ns, i
                                         m->W.as<float>(), sig_z(m), sig_y(m), sig_x(m),
                                         p.wavelet, m->nt, n, p.dt2, 0.0f, 0, s, p.n_dev));
     if (!traces) return FWI_OK;
+    // the 3-D step sampled the receivers itself
+    if (use_step3d(m) && m->rec_fuse_z >= 0 && !m->og_src && p.rec_tr == traces) return FWI_OK;
     if (m->og_rec)
         FWI_LAUNCH(m, launch_sample_pts(g, next, m->rec_pts.as<PointTaps>(), ns, nr, m->nt, n,
                                         traces, s, p.n_dev));
@@ -905,6 +949,7 @@ int fwd_capture(FwdJob &j, int units)
         p.cur = uc;
         p.prev = up;
         p.n = i;
+        p.rec_tr = j.tr;
         ++m->launches;
         rc = raw_step(m, p, j.ns, false, j.s);
         if (rc == FWI_OK) rc = after_forward_step(m, p, p.prev, j.ns, j.nr, i, j.tr, j.s);
@@ -1014,6 +1059,7 @@ int fwd_advance(FwdJob &j, int64_t units, bool *done)
             u += 2;
             continue;
         }
+        j.p.rec_tr = j.tr;
         FWI_TRY(step_launch(m, j.p, j.ns, false, 0, j.s));
         FWI_TRY(after_forward_step(m, j.p, j.p.prev, j.ns, j.nr, j.n, j.tr, j.s));
         std::swap(j.uc, j.up);
@@ -1089,6 +1135,7 @@ int grad_capture(GradJob &j, int par, bool rec)
         p.cur = m->u[cur].as<float>();
         p.prev = m->u[1 - cur].as<float>();
         p.n = i;
+        p.rec_tr = rec ? j.tr : nullptr;
         ++m->launches;
         rc = raw_step(m, p, j.ns, false, j.s);
         if (rc == FWI_OK)
@@ -1327,8 +1374,9 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
                     FWI_CU(cudaMemsetAsync(m->maxbits.p, 0, 2 * ns * sizeof(unsigned), s));
                     j.pf.maxbits = m->maxbits.as<unsigned>();
                 }
-                FWI_TRY(step_launch(m, j.pf, ns, false, j.pf.st_code ? 2 : 0, s));
                 const bool rec_now = j.step >= j.recorded;
+                j.pf.rec_tr = rec_now ? j.tr : nullptr;
+                FWI_TRY(step_launch(m, j.pf, ns, false, j.pf.st_code ? 2 : 0, s));
                 FWI_TRY(after_forward_step(m, j.pf, j.pf.prev, ns, nr, (int)j.step,
                                            rec_now ? j.tr : nullptr, s));
                 if (rec_now) j.recorded = j.step + 1;
@@ -1428,6 +1476,12 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
             j.pa.gacc = m->g32.as<float>();
             j.pa.src_off = (img && !m->og_src) ? m->src_off.as<int64_t>() : nullptr;
             j.pa.n = mm;
+            // node receivers on one plane: the reverse step with imaging injects the
+            // residual itself
+            const bool inj_fused = img && use_step3d(m) && m->rec_fuse_z >= 0 && !m->og_rec;
+            j.pa.inj_q = inj_fused ? j.res : nullptr;
+            j.pa.inj_scale = m->inj.as<float>();
+            j.pa.inj_n = mm - 1;
             FWI_TRY(step_launch(m, j.pa, ns, img, 1, s));
             if (img && m->og_src)   // source term of the imaging sum at the source taps
                 FWI_LAUNCH(m, launch_image_pts(g, m->g32.as<float>(), j.pa.cur, 0, g.field,
@@ -1445,7 +1499,7 @@ int grad_advance(GradJob &j, int64_t units, bool *done)
                                                 ns * nr, nr, m->W.as<float>(), sig_z(m),
                                                 sig_y(m), sig_x(m), j.res, nt, mm - 1,
                                                 j.pa.dt2, 2.0f, 1, s));
-            } else {
+            } else if (!inj_fused) {
                 FWI_LAUNCH(m, launch_inject(g, j.pa.prev, m->rec_off.as<int64_t>(),
                                             m->inj.as<float>(), j.res, ns, nr, nt, mm - 1, s));
             }
@@ -2012,6 +2066,7 @@ void fwi_destroy(fwi_model *m)
     m->scales.release();
     if (m->h_flag) cudaFreeHost(m->h_flag);
     m->cl_tab.release();
+    m->rec_map.release();
     if (m->cl_host) cudaFreeHost(m->cl_host);
     if (m->cl_up) cudaEventDestroy(m->cl_up);
     for (cudaEvent_t e : m->ev) cudaEventDestroy(e);

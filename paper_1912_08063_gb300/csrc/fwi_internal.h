@@ -74,6 +74,13 @@ struct StepParams {
                               // codec's scales of the new state pair)
     unsigned *err;            // TMA-staged kernels: status word, bit 1 (value 2) = a
                               // bounded wait gave up
+    // 3-D receivers sampled / residuals injected in the step's epilogue (set by the
+    // library when every receiver is a node of one plane): forward steps write
+    // rec_tr[s][n][r] = u^{n+1}(rec_r); reverse steps add inj_scale[s][r] inj_q[s][inj_n][r]
+    // to mu^m at the receivers (nullptr: the separate kernels do it)
+    float *rec_tr;
+    const float *inj_q, *inj_scale;
+    int inj_n;
 };
 
 // An off-grid source or receiver (Kaiser-windowed sinc point): taps at the computed-grid

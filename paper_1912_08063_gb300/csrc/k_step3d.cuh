@@ -142,6 +142,29 @@ __device__ __forceinline__ void src_image(float2 &g0, float2 &g1, float4 c, floa
     else g1.y = fmaf(-srcv, q, g1.y);
 }
 
+// Receivers at output row y, points x0 .. x0 + 3 of plane p.rec_z (p.rec_map set): a
+// forward mode writes their samples, the reverse mode adds the residual injection
+// inj_scale * q (rounded as the separate injection kernel's atomic add: product, then
+// sum) to the new values o before they are stored.
+template <int MODE>
+__device__ __forceinline__ void rec_epilogue(const Step3dParams &p, int shot, int y, int x0, int nrow,
+                                             float (&o)[4])
+{
+    const int4 ri = __ldg((const int4 *)(p.rec_map + ((int64_t)shot * p.ny + y) * p.px + x0));
+    const int idx[4] = {ri.x, ri.y, ri.z, ri.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (idx[e] < 0) continue;
+        if (MODE != kModeAdj) {
+            p.rec_tr[((int64_t)shot * p.nt + nrow) * p.nrec + idx[e]] = o[e];
+        } else {
+            const float a = p.inj_scale[(int64_t)shot * p.nrec + idx[e]];
+            const float q = p.inj_q[((int64_t)shot * p.nt + p.inj_n) * p.nrec + idx[e]];
+            o[e] = __fadd_rn(o[e], __fmul_rn(a, q));
+        }
+    }
+}
+
 // Options of the plane loop (bits of Cfg::F):
 //   kPackX     x-sums as packed FP32x2 on register pairs that are 64-bit aligned (even
 //              offsets pair points (0,1) and (2,3) and add into the y accumulators, odd
@@ -231,6 +254,7 @@ struct Ctx {
     int64_t sb;
     int src_j, src_r, src_e;   // source node in this thread's block (src_j < 0: none)
     float srcv;
+    int nrow;                  // step index (the trace row of a forward step)
     float mxa, mxd;            // max|out| and max|out - c| up to sign (p->maxbits set)
     float4 q[C::L][C::RY];
 
@@ -454,7 +478,8 @@ struct Ctx {
                 o0 = __fadd2_rn(t0, lo2(A));   // s = 0
                 o1 = __fadd2_rn(t1, hi2(A));
             }
-            const float rhs[4] = {o0.x, o0.y, o1.x, o1.y};
+            float rhs[4] = {o0.x, o0.y, o1.x, o1.y};
+            if (p->rec_map && j == p->rec_z && store) rec_epilogue<MODE>(*p, shot, y, x0, nrow, rhs);
             if (MODE != kModeAdj && p->maxbits) {
                 const float cz[4] = {cz4.x, cz4.y, cz4.z, cz4.w};
 #pragma unroll
@@ -537,6 +562,7 @@ __device__ __forceinline__ void run_segment(Ctx<C, MODE> &c, int col, int z0, in
     c.src_j = -1;
     c.src_r = c.src_e = 0;
     c.srcv = 0.0f;
+    c.nrow = (p.n_dev ? *p.n_dev : 0) + p.n;
     if (p.src_off) {
         const int64_t s = p.src_off[c.shot];
         const int sz = (int)(s / p.plane), rem = (int)(s - (int64_t)sz * p.plane);

@@ -205,6 +205,7 @@ struct Ctx {
     float *codef;               // kModeStepStore with FP32: the same
     int src_j, src_r, src_e;   // source node in this thread's block (src_j < 0: none)
     float srcv;
+    int nrow;                  // step index (the trace row of a forward step)
     bool domax;                 // raise the checkpoint maxima (p->maxbits set)
     float mxa, mxd;
 
@@ -465,8 +466,14 @@ struct Ctx {
             const float syz = syr[r] + sz;
             const float2 d0 = __fadd2_rn(make_float2(sx1[0], sx1[1]), make_float2(syz, syz));
             const float2 d1 = __fadd2_rn(make_float2(sx1[2], sx1[3]), make_float2(syz, syz));
-            const float2 o0 = __ffma2_rn(t0, make_float2(rcp_fast(d0.x), rcp_fast(d0.y)), lo2(A));
-            const float2 o1 = __ffma2_rn(t1, make_float2(rcp_fast(d1.x), rcp_fast(d1.y)), hi2(A));
+            float2 o0 = __ffma2_rn(t0, make_float2(rcp_fast(d0.x), rcp_fast(d0.y)), lo2(A));
+            float2 o1 = __ffma2_rn(t1, make_float2(rcp_fast(d1.x), rcp_fast(d1.y)), hi2(A));
+            if (p->rec_map && j == p->rec_z && rowok[r]) {
+                float ov[4] = {o0.x, o0.y, o1.x, o1.y};
+                s3d::rec_epilogue<MODE>(*p, shot, y0 + r, x0, nrow, ov);
+                o0 = make_float2(ov[0], ov[1]);
+                o1 = make_float2(ov[2], ov[3]);
+            }
             if (MODE != kModeAdj && domax) {
                 mxa = absmax_nan(mxa, o0.x);
                 mxa = absmax_nan(mxa, o0.y);
@@ -548,6 +555,7 @@ __device__ __forceinline__ void run_segment(Ctx<C, MODE> &c, int col, int z0, in
     c.src_j = -1;
     c.src_r = c.src_e = 0;
     c.srcv = 0.0f;
+    c.nrow = (p.n_dev ? *p.n_dev : 0) + p.n;
     if (p.src_off) {
         const int64_t s = p.src_off[c.shot];
         const int sz = (int)(s / p.plane), rem = (int)(s - (int64_t)sz * p.plane);

@@ -54,6 +54,16 @@ struct Step3dParams {
     unsigned *maxbits;            // kModeStep, nullable: per shot, raise [2s] to the bits of
                                   // max|out| and [2s+1] to max|out - c| (the checkpoint
                                   // codec's scales of the new state pair)
+    // receivers handled in the epilogue (rec_map nullable): every receiver is the node
+    // (rec_z, y, x) with rec_map[shot][y][x] = its index (-1 elsewhere); forward modes
+    // write rec_tr[shot][n][r] = out, the reverse mode adds
+    // inj_scale[shot][r] * inj_q[shot][inj_n][r] to out (the same two roundings as the
+    // separate injection kernel)
+    const int *rec_map;
+    int rec_z, nrec;
+    float *rec_tr;
+    const float *inj_q, *inj_scale;
+    int inj_n;
 };
 
 // Kernel configurations of the 3-D step: tile height, points per thread along y,

@@ -466,3 +466,43 @@ def test_2d_step_kernels_both_variants(tma, monkeypatch):
         et, eg = rel(tr, ref), rel(g.cpu().numpy(), rg)
         print(f"2-D order {order}, TMA {tma}: traces {et:.2e}, gradient {eg:.2e}")
         assert et <= TOL_FWD and eg <= TOL_GRAD32
+
+
+@pytest.mark.parametrize("order", [8, 16])
+def test_receivers_fused_into_the_3d_steps(order, monkeypatch):
+    """Node receivers on one plane: the 3-D forward steps sample them and the reverse
+    steps inject the residual in their epilogues (no separate launches).  Traces, misfit
+    and gradient equal the separate-kernel path (FWI_STEP3D_REC_FUSE=0) bit for bit and
+    match the oracle; two shots with different receiver lines, FP16 checkpoints with
+    recomputation."""
+    rng = np.random.default_rng(35 + order)
+    w = synth.random_small(rng, 3, (26, 33, 47), nt=60, order=order, nb=4, nrec=1)
+    w.src = np.array([[3, 10, 20], [4, 25, 30]], dtype=np.int32)
+    w.rec = np.array([[[2, y, x] for y in range(1, 33, 3) for x in range(0, 47, 2)],
+                      [[2, y, x] for y in range(0, 33, 3) for x in range(0, 47, 2)]],
+                     dtype=np.int32)
+    outs = []
+    for fuse in ("1", "0"):
+        monkeypatch.setenv("FWI_STEP3D_REC_FUSE", fuse)
+        m, p, acq = make_pair(w, snap="fp16", budget=1)
+        probe = m.info()
+        field = probe["computed"][0] * probe["computed"][1] * probe["pitch_x"]
+        m.close()
+        m, p, acq = make_pair(w, snap="fp16", budget=2 * 5 * 2 * 2 * (-(-field // 64) * 64))
+        wav = torch.from_numpy(w.wavelets()).cuda()
+        tr = m.forward(acq, wav).cpu().numpy()
+        dobs = (p.forward() * 0.7).astype(np.float32)
+        phi, g = m.gradient(acq, wav, torch.from_numpy(dobs).cuda())
+        info = m.info()
+        m.close()
+        outs.append((tr, phi.item(), g.cpu().numpy(), info))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1] and np.array_equal(outs[0][2], outs[1][2])
+    assert 0 < outs[0][3]["snap_slots"] < w.nt
+    # the fused run launched fewer kernels (no per-step sampling or injection)
+    assert outs[0][3]["kernel_launches"] < outs[1][3]["kernel_launches"]
+    ref = p.forward()
+    rphi, rg = p.gradient(dobs.astype(np.float64))
+    et, eg = rel(outs[0][0], ref), rel(outs[0][2], rg)
+    print(f"fused receivers order {order}: traces {et:.2e}, gradient {eg:.2e}")
+    assert et <= TOL_FWD and eg <= TOL_GRAD16
