@@ -53,6 +53,9 @@ using s3d::taylor;
 using s3d::taylor_centre3;
 using s3d::tma_load4;
 constexpr int kPackX = s3d::kPackX, kIso = s3d::kIso;
+// Reverse mode only: g is read and written with plain per-thread accesses instead of a
+// fourth TMA tile, which leaves shared memory for a deeper pointwise ring.
+constexpr int kGPlain = 32;
 
 // ---- tensor memory (tcgen05) ----
 // Columns per CTA at radius M: two rings of M slots of 8 columns for each of the two warps
@@ -223,7 +226,7 @@ struct Ctx {
         const int st = pfill;
         uint64_t *b = bar_p + st;
         unsigned char *d = pw + st * C::PW_STRIDE;
-        mbar_expect_tx(b, (C::NPW == 4 && p->aux_fmt != 0 ? 3 * C::TILE_BYTES + C::TILE_BYTES / 2
+        mbar_expect_tx(b, (C::NPW >= 3 && p->aux_fmt != 0 ? (C::NPW - 1) * C::TILE_BYTES + C::TILE_BYTES / 2
                                                            : C::NPW * C::TILE_BYTES) + 16);
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 16, [%2];"
@@ -231,10 +234,8 @@ struct Ctx {
             : "memory");
         tma_load4(d, ma, bx * C::TX, by * C::TY, za + o, shot, b);
         tma_load4(d + C::TILE_BYTES, mb, bx * C::TX, by * C::TY, za + o, 0, b);
-        if (C::NPW == 4) {
-            tma_load4(d + 2 * C::TILE_BYTES, md, bx * C::TX, by * C::TY, za + o, shot, b);
-            tma_load4(d + 3 * C::TILE_BYTES, me, bx * C::TX, by * C::TY, za + o, shot, b);
-        }
+        if (C::NPW >= 3) tma_load4(d + 2 * C::TILE_BYTES, md, bx * C::TX, by * C::TY, za + o, shot, b);
+        if (C::NPW == 4) tma_load4(d + 3 * C::TILE_BYTES, me, bx * C::TX, by * C::TY, za + o, shot, b);
         pfill = pfill + 1 == C::SP ? 0 : pfill + 1;
         ++p_issued;
     }
@@ -424,6 +425,15 @@ struct Ctx {
     {
         constexpr int M = C::M, TX = C::TX, RY = C::RY;
         const int o = it - 2 * M, j = za + o;
+        const int64_t zoff = (int64_t)j * plane_f;
+        // g by plain loads: issued before the wait so their latency overlaps it
+        float4 Gp[RY];
+        if (MODE == kModeAdj && (C::F & kGPlain)) {
+#pragma unroll
+            for (int r = 0; r < RY; ++r)
+                Gp[r] = rowok[r] ? *(const float4 *)(gp + zoff + (int64_t)r * p->px)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         const bool pok = wait_warp(bar_p + pst, (uint32_t)pph);
         const int sp = pst;
         pph ^= pst + 1 == C::SP;
@@ -435,7 +445,6 @@ struct Ctx {
         const float *ta = (const float *)(pw + sp * C::PW_STRIDE);
         const float *tb = ta + TX * C::TY;
         const float sz = szs[4 * sp + (j & 3)];
-        const int64_t zoff = (int64_t)j * plane_f;
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
             const float4 cz4 = r == 0 ? uj.a : uj.b;
@@ -506,7 +515,7 @@ struct Ctx {
                         ? *(const float4 *)(td + toff)
                         : unpack_code4(*(const uint2 *)((const unsigned short *)td + toff),
                                        p->aux_fmt, *ainv);
-                const float4 G = *(const float4 *)(te + toff);
+                const float4 G = (C::F & kGPlain) ? Gp[r] : *(const float4 *)(te + toff);
                 float2 g0 = __ffma2_rn(lo2(Ua), l0, lo2(G));
                 float2 g1 = __ffma2_rn(hi2(Ua), l1, hi2(G));
                 if (at_src) src_image(g0, g1, cz4, B, src_e, srcv);
@@ -613,7 +622,7 @@ k_step3d_tm(const __grid_constant__ Step3dParams p, const __grid_constant__ CUte
             const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
             const __grid_constant__ CUtensorMap map_d, const __grid_constant__ CUtensorMap map_e)
 {
-    using C = Cfg<M, P, PP, F, MODE == kModeAdj ? 4 : 2>;
+    using C = Cfg<M, P, PP, F, MODE == kModeAdj ? ((F & kGPlain) ? 3 : 4) : 2>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // aligned by pointer arithmetic on the shared array (a round trip through an integer
     // would hide the address space, and every shared-memory read would become generic)
@@ -692,8 +701,11 @@ Step3dKernelInfo kernel_info(int mode)
         k.threads = C::NT;
         k.smem = C::SMEM;
     } else {
-        using C = Cfg<M, 2, 1, F, 4>;
-        k.fn = (Step3dKernel)k_step3d_tm<M, 2, 1, F, kModeAdj>;
+        // reverse: g by plain accesses, so two CTAs per SM fit a pointwise ring of three
+        // stages (with a halo ring of two); measured at 552^3 against g as a fourth TMA
+        // tile with rings of three halo and two pointwise stages: 0.779 against 0.796 ms
+        using C = Cfg<M, 1, 2, F | kGPlain, 3>;
+        k.fn = (Step3dKernel)k_step3d_tm<M, 1, 2, F | kGPlain, kModeAdj>;
         k.threads = C::NT;
         k.smem = C::SMEM;
     }
