@@ -14,7 +14,9 @@ namespace fwi {
 // Configuration per radius and mode; FWI_STEP3D_VARIANT=<ty>,<ry>,<pf>,<u>,<opt>[,<opt_rev>]
 // overrides the register-queue kernel's configuration for tuning runs (only the
 // instantiated combinations are accepted), and FWI_STEP3D_TMEM=0/1 turns the
-// tensor-memory kernel off/on in every mode.  By default, as measured on GB300: the
+// tensor-memory kernel off/on in every mode, and FWI_STEP3D_TILE_G=0/1 fixes the form of
+// its reverse step (g staged per thread / g as a TMA tile; unset: by the launch's CTAs
+// per tile column, kTileGParts).  By default, as measured on GB300: the
 // tensor-memory kernel in every mode at radius 8, and at radius 4 in the forward modes
 // (forward 0.090 -> 0.087 ms, forward + store 0.108 -> 0.085 ms at 296^3) but not in the
 // reverse mode (0.1165 against 0.1194 ms).  The register-queue kernel at radius 8 shifts
@@ -40,9 +42,10 @@ Step3dVariant step3d_variant(int M, int mode)
     return v;
 }
 
-static Step3dKernelInfo kernel_info(int M, int mode, bool iso = false)
+static Step3dKernelInfo kernel_info(int M, int mode, bool iso = false, bool tile_g = false)
 {
-    const Step3dVariant v = step3d_variant(M, mode);
+    Step3dVariant v = step3d_variant(M, mode);
+    v.tile_g = tile_g;
     if (M == 8) return step3d_kernel_m8(v, mode, iso);
     if (M == 4) return step3d_kernel_m4(v, mode, iso);
     return Step3dKernelInfo{nullptr, 0, 0};
@@ -65,9 +68,8 @@ static cudaError_t prepare_kernel(const Step3dKernelInfo &k)
                                 (int)cudaSharedmemCarveoutMaxShared);
 }
 
-int step3d_resident_ctas(int M, int mode, bool iso)
+static int resident_ctas(const Step3dKernelInfo &k)
 {
-    const Step3dKernelInfo k = kernel_info(M, mode, iso);
     if (!k.fn) return -(int)cudaErrorInvalidDeviceFunction;
     cudaError_t e = prepare_kernel(k);
     int dev = 0, sms = 0, per = 0;
@@ -102,12 +104,25 @@ int step3d_resident_ctas(int M, int mode, bool iso)
     return sms * per;
 }
 
+// The reverse step's two forms (g staged per thread or as a TMA tile) are planned with
+// one count: the smaller of theirs.
+int step3d_resident_ctas(int M, int mode, bool iso)
+{
+    const int a = resident_ctas(kernel_info(M, mode, iso));
+    if (mode != kModeAdj || a < 0) return a;
+    const int b = resident_ctas(kernel_info(M, mode, iso, true));
+    return b < 0 ? b : std::min(a, b);
+}
+
 cudaError_t launch_step3d_tma(const Step3dParams &p, int mode, int ctas,
                               const CUtensorMap &mc, const CUtensorMap &ma,
                               const CUtensorMap &mb, const CUtensorMap &md,
                               const CUtensorMap &me, cudaStream_t s)
 {
-    const Step3dKernelInfo k = kernel_info(p.M, mode, p.iso != 0);
+    const int64_t columns = (int64_t)((p.nx + 63) / 64) * ((p.ny + 31) / 32) * p.nshots;
+    bool tile_g = (int64_t)ctas > (int64_t)(kTileGParts - 1) * columns;   // ctas/columns >= 5
+    if (const char *e = std::getenv("FWI_STEP3D_TILE_G")) tile_g = std::atoi(e) != 0;
+    const Step3dKernelInfo k = kernel_info(p.M, mode, p.iso != 0, mode == kModeAdj && tile_g);
     if (!k.fn) return cudaErrorInvalidValue;
     const cudaError_t e = prepare_kernel(k);
     if (e != cudaSuccess) return e;

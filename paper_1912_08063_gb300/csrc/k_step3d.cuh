@@ -107,6 +107,15 @@ __device__ __forceinline__ void tma_load4(void *dst, const CUtensorMap *map, int
         : "memory");
 }
 
+// Starts bringing the tile of a 4-D tensor map at (x, y, z, w) into L2 (no shared memory,
+// no barrier; parts outside the tensor are skipped).
+__device__ __forceinline__ void tma_prefetch4(const CUtensorMap *map, int x, int y, int z, int w)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];"
+                 ::"l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(w)
+                 : "memory");
+}
+
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 

@@ -49,13 +49,15 @@ using s3d::mbar_wait;
 using s3d::rcp_fast;
 using s3d::smem_u32;
 using s3d::src_image;
+using s3d::tma_prefetch4;
 using s3d::taylor;
 using s3d::taylor_centre3;
 using s3d::tma_load4;
 constexpr int kPackX = s3d::kPackX, kIso = s3d::kIso;
-// Reverse mode only: g is read and written with plain per-thread accesses instead of a
-// fourth TMA tile, which leaves shared memory for a deeper pointwise ring.
-constexpr int kGPlain = 32;
+// Reverse step: each thread copies its own g values of the plane into a shared buffer
+// with cp.async at the top of the plane (the tile itself brought into L2 one plane
+// earlier), instead of g as a fourth TMA pointwise tile
+constexpr int kGAsync = 32;
 
 // ---- tensor memory (tcgen05) ----
 // Columns per CTA at radius M: two rings of M slots of 8 columns for each of the two warps
@@ -177,7 +179,8 @@ struct Cfg {
     static constexpr int HALO_STRIDE = (HALO_BYTES + 127) / 128 * 128;
     static constexpr int PW_STRIDE = (NPW * TILE_BYTES + 127) / 128 * 128;
     static constexpr int MISC = 256;   // barriers, flags, scales, sponge groups, TMEM base
-    static constexpr int SMEM = SH * HALO_STRIDE + SP * PW_STRIDE + MISC + 1024;
+    static constexpr int GS = (F & kGAsync) ? 1 : 0;   // g staging buffer
+    static constexpr int SMEM = SH * HALO_STRIDE + SP * PW_STRIDE + GS * TILE_BYTES + MISC + 1024;
     // the CTAs that shared memory admits per SM never need more TMEM than the SM's 512
     // columns, so an allocation never waits
     static_assert((233472 / (SMEM + 1024)) * tmem_cols<M>() <= 512, "a CTA would wait for TMEM");
@@ -189,6 +192,7 @@ struct Ctx {
     const Step3dParams *p;
     const CUtensorMap *mc, *ma, *mb, *md, *me;
     unsigned char *halo, *pw;
+    float *gbuf;
     uint64_t *bar_h, *bar_p;
     int *abort_flag;
     const float *ainv;
@@ -341,6 +345,28 @@ struct Ctx {
             if (it + C::P < niter) issue_halo(it + C::P);
             const int op = it - 2 * M + C::PP;
             if (op >= 0 && op < nout) issue_pw(op);
+            if (MODE == kModeAdj && C::GS) {   // g of the next output plane into L2
+                const int og = it - 2 * M + 1;
+                if (og >= 0 && og < nout) tma_prefetch4(me, bx * C::TX, by * C::TY, za + og, shot);
+            }
+        }
+        if (MODE == kModeAdj && C::GS) {
+            // this thread's g values of output plane j (if any) into the staging buffer,
+            // whose previous contents this thread has read (in program order) already;
+            // rows outside the grid copy nothing and read as zero
+            const int og = it - 2 * M;
+            if (og >= 0) {
+                const int64_t zoff = (int64_t)(za + og) * plane_f;
+#pragma unroll
+                for (int r = 0; r < RY; ++r) {
+                    const float *src = rowok[r] ? gp + zoff + (int64_t)r * p->px : gp;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                                 ::"r"(smem_u32(gbuf + (ty * RY + r) * C::TX + tx * 4)), "l"(src),
+                                 "r"(rowok[r] ? 16 : 0)
+                                 : "memory");
+                }
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
         }
         const int i = za - M + it;
         const uint32_t slot = (uint32_t)(i & (M - 1)) * 8u;   // same slot for i and i - M
@@ -426,14 +452,6 @@ struct Ctx {
         constexpr int M = C::M, TX = C::TX, RY = C::RY;
         const int o = it - 2 * M, j = za + o;
         const int64_t zoff = (int64_t)j * plane_f;
-        // g by plain loads: issued before the wait so their latency overlaps it
-        float4 Gp[RY];
-        if (MODE == kModeAdj && (C::F & kGPlain)) {
-#pragma unroll
-            for (int r = 0; r < RY; ++r)
-                Gp[r] = rowok[r] ? *(const float4 *)(gp + zoff + (int64_t)r * p->px)
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
         const bool pok = wait_warp(bar_p + pst, (uint32_t)pph);
         const int sp = pst;
         pph ^= pst + 1 == C::SP;
@@ -444,6 +462,7 @@ struct Ctx {
         }
         const float *ta = (const float *)(pw + sp * C::PW_STRIDE);
         const float *tb = ta + TX * C::TY;
+        if (MODE == kModeAdj && C::GS) asm volatile("cp.async.wait_group 0;" ::: "memory");
         const float sz = szs[4 * sp + (j & 3)];
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
@@ -515,7 +534,7 @@ struct Ctx {
                         ? *(const float4 *)(td + toff)
                         : unpack_code4(*(const uint2 *)((const unsigned short *)td + toff),
                                        p->aux_fmt, *ainv);
-                const float4 G = (C::F & kGPlain) ? Gp[r] : *(const float4 *)(te + toff);
+                const float4 G = *(const float4 *)((C::GS ? gbuf : te) + toff);
                 float2 g0 = __ffma2_rn(lo2(Ua), l0, lo2(G));
                 float2 g1 = __ffma2_rn(hi2(Ua), l1, hi2(G));
                 if (at_src) src_image(g0, g1, cz4, B, src_e, srcv);
@@ -622,7 +641,7 @@ k_step3d_tm(const __grid_constant__ Step3dParams p, const __grid_constant__ CUte
             const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
             const __grid_constant__ CUtensorMap map_d, const __grid_constant__ CUtensorMap map_e)
 {
-    using C = Cfg<M, P, PP, F, MODE == kModeAdj ? ((F & kGPlain) ? 3 : 4) : 2>;
+    using C = Cfg<M, P, PP, F, MODE == kModeAdj ? ((F & kGAsync) ? 3 : 4) : 2>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // aligned by pointer arithmetic on the shared array (a round trip through an integer
     // would hide the address space, and every shared-memory read would become generic)
@@ -637,7 +656,8 @@ k_step3d_tm(const __grid_constant__ Step3dParams p, const __grid_constant__ CUte
     c.me = &map_e;
     c.halo = smem;
     c.pw = smem + C::SH * C::HALO_STRIDE;
-    unsigned char *misc = c.pw + C::SP * C::PW_STRIDE;
+    c.gbuf = (float *)(c.pw + C::SP * C::PW_STRIDE);
+    unsigned char *misc = (unsigned char *)c.gbuf + C::GS * C::TILE_BYTES;
     c.bar_h = (uint64_t *)misc;                      // SH + SP <= 8 barriers: bytes 0..63
     c.bar_p = c.bar_h + C::SH;
     c.abort_flag = (int *)(misc + 64);
@@ -675,6 +695,7 @@ k_step3d_tm(const __grid_constant__ Step3dParams p, const __grid_constant__ CUte
     const int tiles = tiles_x * ((p.ny + C::TY - 1) / C::TY);
     s3d::walk_schedule(p, tiles * p.nshots, c.abort_flag,
                        [&](int col, int z0, int z1) { run_segment(c, col, z0, z1, tiles_x, tiles); });
+    if (MODE == kModeAdj && C::GS) asm volatile("cp.async.wait_all;" ::: "memory");
     // every TMEM access of the CTA is complete before warp 0 releases the columns
     tmem_wait_st();
     tmem_fence_before();
@@ -691,7 +712,7 @@ k_step3d_tm(const __grid_constant__ Step3dParams p, const __grid_constant__ CUte
 }
 
 template <int M, int F>
-Step3dKernelInfo kernel_info(int mode)
+Step3dKernelInfo kernel_info(int mode, bool tile_g)
 {
     Step3dKernelInfo k;
     if (mode == kModeStep || mode == kModeStepStore) {
@@ -700,12 +721,16 @@ Step3dKernelInfo kernel_info(int mode)
                                  : (Step3dKernel)k_step3d_tm<M, 2, 2, F, kModeStepStore>;
         k.threads = C::NT;
         k.smem = C::SMEM;
+    } else if (tile_g) {
+        // g as a fourth TMA pointwise tile: rings of three halo and two pointwise stages
+        using C = Cfg<M, 2, 1, F, 4>;
+        k.fn = (Step3dKernel)k_step3d_tm<M, 2, 1, F, kModeAdj>;
+        k.threads = C::NT;
+        k.smem = C::SMEM;
     } else {
-        // reverse: g by plain accesses, so two CTAs per SM fit a pointwise ring of three
-        // stages (with a halo ring of two); measured at 552^3 against g as a fourth TMA
-        // tile with rings of three halo and two pointwise stages: 0.779 against 0.796 ms
-        using C = Cfg<M, 1, 2, F | kGPlain, 3>;
-        k.fn = (Step3dKernel)k_step3d_tm<M, 1, 2, F | kGPlain, kModeAdj>;
+        // g staged by cp.async: rings of two halo and three pointwise stages
+        using C = Cfg<M, 1, 2, F | kGAsync, 3>;
+        k.fn = (Step3dKernel)k_step3d_tm<M, 1, 2, F | kGAsync, kModeAdj>;
         k.threads = C::NT;
         k.smem = C::SMEM;
     }

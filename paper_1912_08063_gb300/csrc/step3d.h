@@ -73,11 +73,19 @@ struct Step3dParams {
 // Tile height, rows per thread, prefetch depth, queue shift interval, and the option bits
 // (Cfg::F) of the plain forward step (opt) and of the store and reverse modes (opt_rev);
 // tm = 1 selects the kernel whose z-stream lives in tensor memory (k_step3d_tm.cuh:
-// 64 x 32 tiles, two CTAs per SM; ty is then 32 and the other fields do not apply).
+// 64 x 32 tiles, two CTAs per SM; ty is then 32 and the other fields do not apply);
+// tile_g = 1 makes its reverse step read g as a TMA pointwise tile instead of staging it
+// with per-thread asynchronous copies.
 struct Step3dVariant {
     int ty, ry, pf, u, opt, opt_rev;
     int tm;
+    int tile_g = 0;
 };
+// The tensor-memory reverse step takes g as a TMA tile when a launch has at least this
+// many CTAs per 64 x 32 tile column, so that its columns are cut along z into as many
+// short parts or pieces (23 to 72 planes on the 232^3 to 360^3 grids measured, 3-6 %
+// faster there), and stages g per thread otherwise (424^3 and up, 4-15 % faster).
+constexpr int kTileGParts = 5;
 Step3dVariant step3d_variant(int M, int mode);
 int step3d_smem_bytes(int M);
 int step3d_threads(int M);
@@ -108,8 +116,8 @@ struct Step3dKernelInfo {
 Step3dKernelInfo step3d_kernel_m4(const Step3dVariant &v, int mode, bool iso = false);
 Step3dKernelInfo step3d_kernel_m8(const Step3dVariant &v, int mode, bool iso = false);
 // The tensor-memory kernels (k_step3d_tm8.cu, k_step3d_tm4.cu).
-Step3dKernelInfo step3d_kernel_tm8(int mode, bool iso);
-Step3dKernelInfo step3d_kernel_tm4(int mode, bool iso);
+Step3dKernelInfo step3d_kernel_tm8(int mode, bool iso, bool tile_g);
+Step3dKernelInfo step3d_kernel_tm4(int mode, bool iso, bool tile_g);
 
 // Encodes a 4-D tensor map over shots of a field laid out as in Geom (elements of
 // `elem_bytes` = 4 or 2, shots `shot_stride` elements apart), with box (bx, by, 1, 1) and

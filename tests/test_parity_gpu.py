@@ -416,14 +416,16 @@ def test_model_reuse_across_checkpoint_layouts():
 
 
 @pytest.mark.parametrize("order", [16, 8])
-@pytest.mark.parametrize("tmem", ["1", "0"])
-def test_step_kernels_both_variants(tmem, order, monkeypatch):
+@pytest.mark.parametrize("tmem,tile_g", [("1", "0"), ("1", "1"), ("0", "0")])
+def test_step_kernels_both_variants(tmem, tile_g, order, monkeypatch):
     """The 3-D steps run either the tensor-memory kernel (z-stream in TMEM, two CTAs per
-    SM; FWI_STEP3D_TMEM=1) or the register-queue kernel (FWI_STEP3D_TMEM=0), at radius 8
-    and radius 4; every combination matches the oracle in every mode: forward, forward
-    with checkpoint stores, reverse step with imaging (FP16 checkpoints,
+    SM; FWI_STEP3D_TMEM=1), with its reverse step staging g per thread or reading it as a
+    TMA tile (FWI_STEP3D_TILE_G=0/1), or the register-queue kernel (FWI_STEP3D_TMEM=0), at
+    radius 8 and radius 4; every combination matches the oracle in every mode: forward,
+    forward with checkpoint stores, reverse step with imaging (FP16 checkpoints,
     recomputation)."""
     monkeypatch.setenv("FWI_STEP3D_TMEM", tmem)
+    monkeypatch.setenv("FWI_STEP3D_TILE_G", tile_g)
     rng = np.random.default_rng(31)
     w = synth.random_small(rng, 3, (22, 37, 70), nt=70, order=order, nb=4, nrec=9)
     m, p, acq = make_pair(w, snap="fp16", budget=1)
@@ -440,11 +442,31 @@ def test_step_kernels_both_variants(tmem, order, monkeypatch):
     info = m.info()
     rphi, rg = p.gradient(dobs.astype(np.float64))
     eg = rel(g.cpu().numpy(), rg)
-    print(f"order {order}, TMEM {tmem}: traces {et:.2e}, gradient {eg:.2e}, "
+    print(f"order {order}, TMEM {tmem}, tile g {tile_g}: traces {et:.2e}, gradient {eg:.2e}, "
           f"slots {info['snap_slots']}, forward steps {info['last_forward_steps']}")
     assert 0 < info["snap_slots"] < w.nt
     assert et <= TOL_FWD and eg <= TOL_GRAD16
     assert abs(phi.item() - rphi) <= TOL_GRAD32 * rphi
+
+
+@pytest.mark.parametrize("order", [16, 8])
+def test_reverse_step_forms_are_bit_equal(order, monkeypatch):
+    """The tensor-memory reverse step's two ways of reading g (per-thread asynchronous
+    copies into a staging buffer, or a TMA pointwise tile) do the same arithmetic in the
+    same order: gradients equal bit for bit, on a grid whose ragged tiles leave rows and
+    columns outside the field."""
+    monkeypatch.setenv("FWI_STEP3D_TMEM", "1")
+    rng = np.random.default_rng(35)
+    w = synth.random_small(rng, 3, (29, 41, 67), nt=40, order=order, nb=4, nrec=7)
+    wav = torch.from_numpy(w.wavelets()).cuda()
+    m, p, acq = make_pair(w, snap="fp16")
+    dobs = torch.from_numpy((p.forward() * 0.8).astype(np.float32)).cuda()
+    out = {}
+    for tg in ("0", "1"):
+        monkeypatch.setenv("FWI_STEP3D_TILE_G", tg)
+        out[tg] = m.gradient(acq, wav, dobs)
+    assert torch.equal(out["0"][1], out["1"][1])
+    assert out["0"][0].item() == out["1"][0].item()
 
 
 @pytest.mark.parametrize("tma", ["1", "0"])
