@@ -1785,7 +1785,7 @@ int fwi_create_model(fwi_model **out, int32_t ndim, const int64_t shape[3],
     g.M = m->M;
     const int64_t nz = shape[0] + 2 * o.nb, ny = ndim == 3 ? shape[1] + 2 * o.nb : 1,
                   nx = shape[2] + 2 * o.nb;
-    if (nz > (1 << 30) || ny > (1 << 30) || nx > (1 << 30)) {
+    if (nz > (1 << 30) || ny > (1 << 30) || nx > (1 << 30) || nz * ny >= ((int64_t)1 << 31)) {
         delete m;
         return fail(FWI_ERR_ARG, "grid too large");
     }

@@ -23,24 +23,26 @@ int blocks_for(int64_t n, int cap = 148 * 16)
 // ---------------------------------------------------------------- set-up
 
 // W[c] = (v[clamp(c - nb)] dt)^2 on the computed grid, zero in the row padding.
-__global__ void k_build_W(Geom g, int nb, int64_t npz, int64_t npy, int64_t npx,
-                          const float *__restrict__ v, double dt, float *__restrict__ W)
+// One CTA per computed row (z, y) at a time, threads along x (the row split is one 32-bit
+// division per row, not two 64-bit ones per point).
+__global__ void k_build_W(Geom g, int nb, int npz, int npy, int npx, const float *__restrict__ v,
+                          double dt, float *__restrict__ W)
 {
-    const int64_t total = (int64_t)g.nz * g.plane;
     const int nby = (g.ndim == 3) ? nb : 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t z = i / g.plane, r = i - z * g.plane;
-        const int64_t y = r / g.px, x = r - y * g.px;
-        float w = 0.0f;
-        if (x < g.nx) {
-            int64_t pz = min(max(z - nb, (int64_t)0), npz - 1);
-            int64_t py = min(max(y - nby, (int64_t)0), npy - 1);
-            int64_t pxx = min(max(x - nb, (int64_t)0), npx - 1);
-            double vv = v[(pz * npy + py) * npx + pxx];
-            w = (float)(vv * vv * dt * dt);
+    const int rows = g.nz * g.ny;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int z = row / g.ny, y = row - z * g.ny;
+        const int pz = min(max(z - nb, 0), npz - 1), py = min(max(y - nby, 0), npy - 1);
+        const float *vr = v + ((int64_t)pz * npy + py) * npx;
+        float *wr = W + (int64_t)row * g.px;
+        for (int x = threadIdx.x; x < g.px; x += blockDim.x) {
+            float w = 0.0f;
+            if (x < g.nx) {
+                const double vv = vr[min(max(x - nb, 0), npx - 1)];
+                w = (float)(vv * vv * dt * dt);
+            }
+            wr[x] = w;
         }
-        W[i] = w;
     }
 }
 
@@ -390,30 +392,32 @@ __global__ void k_fold(float *__restrict__ g32, double *__restrict__ g64, int64_
 // grad(p) = (2 / v(p)) * sum_shots sum_{computed cells c replicated from p} g_mu(c),
 // where g_mu = sum_m mu^{m+1} L u^m and mu = W nu (so dphi/dW = g_mu / W and
 // dphi/dv = 2 v dt^2 dphi/dW = 2 g_mu / v).
-__global__ void k_finish(Geom g, int nb, int64_t npz, int64_t npy, int64_t npx, int nshots,
+// One CTA per physical row (pz, py) at a time, threads along x.
+__global__ void k_finish(Geom g, int nb, int npz, int npy, int npx, int nshots,
                          const double *__restrict__ g64, const float *__restrict__ v,
                          float *__restrict__ grad32, double *__restrict__ grad64)
 {
-    const int64_t nphys = npz * npy * npx;
     const int nby = (g.ndim == 3) ? nb : 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nphys;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t pz = i / (npy * npx), r = i - pz * npy * npx;
-        const int64_t py = r / npx, pxx = r - py * npx;
-        const int64_t z0 = pz == 0 ? 0 : pz + nb, z1 = pz == npz - 1 ? pz + 2 * nb : pz + nb;
-        const int64_t y0 = py == 0 ? 0 : py + nby, y1 = py == npy - 1 ? py + 2 * nby : py + nby;
-        const int64_t x0 = pxx == 0 ? 0 : pxx + nb, x1 = pxx == npx - 1 ? pxx + 2 * nb : pxx + nb;
-        double acc = 0.0;
-        for (int s = 0; s < nshots; ++s) {
-            const double *gs = g64 + (int64_t)s * g.field;
-            for (int64_t cz = z0; cz <= z1; ++cz)
-                for (int64_t cy = y0; cy <= y1; ++cy)
-                    for (int64_t cx = x0; cx <= x1; ++cx)
-                        acc += gs[cz * g.plane + cy * g.px + cx];
+    const int rows = npz * npy;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int pz = row / npy, py = row - pz * npy;
+        const int z0 = pz == 0 ? 0 : pz + nb, z1 = pz == npz - 1 ? pz + 2 * nb : pz + nb;
+        const int y0 = py == 0 ? 0 : py + nby, y1 = py == npy - 1 ? py + 2 * nby : py + nby;
+        for (int pxx = threadIdx.x; pxx < npx; pxx += blockDim.x) {
+            const int x0 = pxx == 0 ? 0 : pxx + nb, x1 = pxx == npx - 1 ? pxx + 2 * nb : pxx + nb;
+            double acc = 0.0;
+            for (int s = 0; s < nshots; ++s) {
+                const double *gs = g64 + (int64_t)s * g.field;
+                for (int cz = z0; cz <= z1; ++cz)
+                    for (int cy = y0; cy <= y1; ++cy)
+                        for (int cx = x0; cx <= x1; ++cx)
+                            acc += gs[(int64_t)cz * g.plane + (int64_t)cy * g.px + cx];
+            }
+            const int64_t i = (int64_t)row * npx + pxx;
+            const double out = acc * 2.0 / (double)v[i];
+            if (grad32) grad32[i] = (float)out;
+            if (grad64) grad64[i] = out;
         }
-        const double out = acc * 2.0 / (double)v[i];
-        if (grad32) grad32[i] = (float)out;
-        if (grad64) grad64[i] = out;
     }
 }
 
@@ -424,8 +428,9 @@ __global__ void k_finish(Geom g, int nb, int64_t npz, int64_t npy, int64_t npx, 
 cudaError_t launch_build_W(const Geom &g, int nb, const int64_t np[3], const float *v,
                            float dt, float *W, cudaStream_t s)
 {
-    k_build_W<<<blocks_for((int64_t)g.nz * g.plane), kThreads, 0, s>>>(g, nb, np[0], np[1],
-                                                                      np[2], v, dt, W);
+    const int rows = g.nz * g.ny;
+    k_build_W<<<rows < 152 * 16 ? rows : 152 * 16, kThreads, 0, s>>>(g, nb, (int)np[0], (int)np[1],
+                                                                     (int)np[2], v, dt, W);
     return cudaGetLastError();
 }
 
@@ -588,8 +593,9 @@ cudaError_t launch_finish(const Geom &g, int nb, const int64_t np[3], int nshots
                           const double *g64, const float *v, float *grad32, double *grad64,
                           cudaStream_t s)
 {
-    k_finish<<<blocks_for(np[0] * np[1] * np[2], 152 * 8), kThreads, 0, s>>>(
-        g, nb, np[0], np[1], np[2], nshots, g64, v, grad32, grad64);
+    const int rows = (int)(np[0] * np[1]);
+    k_finish<<<rows < 152 * 16 ? rows : 152 * 16, kThreads, 0, s>>>(
+        g, nb, (int)np[0], (int)np[1], (int)np[2], nshots, g64, v, grad32, grad64);
     return cudaGetLastError();
 }
 
