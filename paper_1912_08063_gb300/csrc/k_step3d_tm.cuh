@@ -58,6 +58,7 @@ constexpr int kPackX = s3d::kPackX, kIso = s3d::kIso;
 // with cp.async at the top of the plane (the tile itself brought into L2 one plane
 // earlier), instead of g as a fourth TMA pointwise tile
 constexpr int kGAsync = 32;
+template <bool B> struct BoolC { static constexpr bool value = B; };
 
 // ---- tensor memory (tcgen05) ----
 // Columns per CTA at radius M: two rings of M slots of 8 columns for each of the two warps
@@ -211,6 +212,7 @@ struct Ctx {
     unsigned short *codep;      // kModeStepStore with 16-bit codes: code at the same place
     float *codef;               // kModeStepStore with FP32: the same
     int src_j, src_r, src_e;   // source node in this thread's block (src_j < 0: none)
+    int src_z;                  // the source node's plane in this shot (-1: none)
     float srcv;
     int nrow;                  // step index (the trace row of a forward step)
     bool domax;                 // raise the checkpoint maxima (p->maxbits set)
@@ -246,8 +248,11 @@ struct Ctx {
 
     // A bounded wait whose outcome every lane of the warp shares (the TMEM instructions
     // that follow are warp-collective, so no lane may skip them alone).
+    // Forward modes probe once before the polling loop (552^3: forward 0.535 -> 0.521 ms,
+    // forward + store 0.600 -> 0.579 ms; no gain for the reverse step).
     __device__ __forceinline__ bool wait_warp(uint64_t *bar, uint32_t parity)
     {
+        if (MODE != kModeAdj && __all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
         return __all_sync(0xffffffffu, mbar_wait(bar, parity));
     }
 
@@ -464,83 +469,95 @@ struct Ctx {
         const float *tb = ta + TX * C::TY;
         if (MODE == kModeAdj && C::GS) asm volatile("cp.async.wait_group 0;" ::: "memory");
         const float sz = szs[4 * sp + (j & 3)];
-#pragma unroll
-        for (int r = 0; r < RY; ++r) {
-            const float4 cz4 = r == 0 ? uj.a : uj.b;
-            float2 l0 = lacc[r][0], l1 = lacc[r][1];
-            if (C::ISO) {
-                const float2 ih = make_float2(p->inv_h2, p->inv_h2);
-                l0 = __fmul2_rn(l0, ih);
-                l1 = __fmul2_rn(l1, ih);
-            }
-            const int toff = (ty * RY + r) * TX + tx * 4;
-            const int64_t off = zoff + (int64_t)r * p->px;
-            const float4 A = *(const float4 *)(ta + toff);   // prev
-            const float4 B = *(const float4 *)(tb + toff);   // W
-            // (2c + W lap - (1 - s) prev [+ dt^2 w at the source]) / (1 + s), evaluated as
-            // prev + (2 (c - prev) + W lap [+ dt^2 w]) / (1 + s)
-            const float2 m1 = make_float2(-1.0f, -1.0f), two = make_float2(2.0f, 2.0f);
-            const float2 dc0 = __ffma2_rn(lo2(A), m1, lo2(cz4));
-            const float2 dc1 = __ffma2_rn(hi2(A), m1, hi2(cz4));
-            float2 t0 = __ffma2_rn(lo2(B), l0, __fmul2_rn(two, dc0));
-            float2 t1 = __ffma2_rn(hi2(B), l1, __fmul2_rn(two, dc1));
-            const bool at_src = j == src_j && r == src_r;
-            if (MODE != kModeAdj && at_src) {
-                if (src_e == 0) t0.x += srcv;
-                else if (src_e == 1) t0.y += srcv;
-                else if (src_e == 2) t1.x += srcv;
-                else t1.y += srcv;
-            }
-            const float syz = syr[r] + sz;
-            const float2 d0 = __fadd2_rn(make_float2(sx1[0], sx1[1]), make_float2(syz, syz));
-            const float2 d1 = __fadd2_rn(make_float2(sx1[2], sx1[3]), make_float2(syz, syz));
-            float2 o0 = __ffma2_rn(t0, make_float2(rcp_fast(d0.x), rcp_fast(d0.y)), lo2(A));
-            float2 o1 = __ffma2_rn(t1, make_float2(rcp_fast(d1.x), rcp_fast(d1.y)), hi2(A));
-            if (p->rec_map && j == p->rec_z && rowok[r]) {
-                float ov[4] = {o0.x, o0.y, o1.x, o1.y};
-                s3d::rec_epilogue<MODE>(*p, shot, y0 + r, x0, nrow, ov);
-                o0 = make_float2(ov[0], ov[1]);
-                o1 = make_float2(ov[2], ov[3]);
-            }
-            if (MODE != kModeAdj && domax) {
-                mxa = absmax_nan(mxa, o0.x);
-                mxa = absmax_nan(mxa, o0.y);
-                mxa = absmax_nan(mxa, o1.x);
-                mxa = absmax_nan(mxa, o1.y);
-                mxd = absmax_nan(mxd, o0.x - cz4.x);
-                mxd = absmax_nan(mxd, o0.y - cz4.y);
-                mxd = absmax_nan(mxd, o1.x - cz4.z);
-                mxd = absmax_nan(mxd, o1.y - cz4.w);
-            }
-            if (rowok[r]) *(float4 *)(outp + off) = make_float4(o0.x, o0.y, o1.x, o1.y);
-            if (MODE == kModeStepStore && rowok[r]) {
-                // checkpoint of the input pair (c = u^n, prev = u^{n-1}) in the encode
-                // kernel's format: FP32 pair, or 16-bit a = c s_a and d = (c - prev) s_d
-                if (p->st_dtype == 0) {
-                    *(float4 *)(codef + off) = cz4;
-                    if (p->st_comps == 2) *(float4 *)(codef + off + p->field) = A;
-                } else {
-                    *(uint2 *)(codep + off) = pack_code4(cz4, p->st_dtype, sts[0]);
-                    if (p->st_comps == 2)
-                        *(uint2 *)(codep + off + p->field) =
-                            pack_code4(make_float4(dc0.x, dc0.y, dc1.x, dc1.y), p->st_dtype, sts[1]);
+        // the rows' epilogue.  Forward modes run the source and receiver checks only in the
+        // planes that hold the source node or the receivers (one uniform test per plane;
+        // 552^3: forward 0.561 -> 0.535 ms, forward + store 0.617 -> 0.599 ms); the
+        // reverse step keeps them in every plane (hoisted, it needs 128 registers and ran
+        // 0.715 -> 0.731 ms)
+        auto rows = [&](auto spec_c) {
+            constexpr bool SPEC = decltype(spec_c)::value;
+    #pragma unroll
+            for (int r = 0; r < RY; ++r) {
+                const float4 cz4 = r == 0 ? uj.a : uj.b;
+                float2 l0 = lacc[r][0], l1 = lacc[r][1];
+                if (C::ISO) {
+                    const float2 ih = make_float2(p->inv_h2, p->inv_h2);
+                    l0 = __fmul2_rn(l0, ih);
+                    l1 = __fmul2_rn(l1, ih);
+                }
+                const int toff = (ty * RY + r) * TX + tx * 4;
+                const int64_t off = zoff + (int64_t)r * p->px;
+                const float4 A = *(const float4 *)(ta + toff);   // prev
+                const float4 B = *(const float4 *)(tb + toff);   // W
+                // (2c + W lap - (1 - s) prev [+ dt^2 w at the source]) / (1 + s), evaluated as
+                // prev + (2 (c - prev) + W lap [+ dt^2 w]) / (1 + s)
+                const float2 m1 = make_float2(-1.0f, -1.0f), two = make_float2(2.0f, 2.0f);
+                const float2 dc0 = __ffma2_rn(lo2(A), m1, lo2(cz4));
+                const float2 dc1 = __ffma2_rn(hi2(A), m1, hi2(cz4));
+                float2 t0 = __ffma2_rn(lo2(B), l0, __fmul2_rn(two, dc0));
+                float2 t1 = __ffma2_rn(hi2(B), l1, __fmul2_rn(two, dc1));
+                const bool at_src = SPEC && j == src_j && r == src_r;
+                if (MODE != kModeAdj && at_src) {
+                    if (src_e == 0) t0.x += srcv;
+                    else if (src_e == 1) t0.y += srcv;
+                    else if (src_e == 2) t1.x += srcv;
+                    else t1.y += srcv;
+                }
+                const float syz = syr[r] + sz;
+                const float2 d0 = __fadd2_rn(make_float2(sx1[0], sx1[1]), make_float2(syz, syz));
+                const float2 d1 = __fadd2_rn(make_float2(sx1[2], sx1[3]), make_float2(syz, syz));
+                float2 o0 = __ffma2_rn(t0, make_float2(rcp_fast(d0.x), rcp_fast(d0.y)), lo2(A));
+                float2 o1 = __ffma2_rn(t1, make_float2(rcp_fast(d1.x), rcp_fast(d1.y)), hi2(A));
+                if (SPEC && p->rec_map && j == p->rec_z && rowok[r]) {
+                    float ov[4] = {o0.x, o0.y, o1.x, o1.y};
+                    s3d::rec_epilogue<MODE>(*p, shot, y0 + r, x0, nrow, ov);
+                    o0 = make_float2(ov[0], ov[1]);
+                    o1 = make_float2(ov[2], ov[3]);
+                }
+                if (MODE != kModeAdj && domax) {
+                    mxa = absmax_nan(mxa, o0.x);
+                    mxa = absmax_nan(mxa, o0.y);
+                    mxa = absmax_nan(mxa, o1.x);
+                    mxa = absmax_nan(mxa, o1.y);
+                    mxd = absmax_nan(mxd, o0.x - cz4.x);
+                    mxd = absmax_nan(mxd, o0.y - cz4.y);
+                    mxd = absmax_nan(mxd, o1.x - cz4.z);
+                    mxd = absmax_nan(mxd, o1.y - cz4.w);
+                }
+                if (rowok[r]) *(float4 *)(outp + off) = make_float4(o0.x, o0.y, o1.x, o1.y);
+                if (MODE == kModeStepStore && rowok[r]) {
+                    // checkpoint of the input pair (c = u^n, prev = u^{n-1}) in the encode
+                    // kernel's format: FP32 pair, or 16-bit a = c s_a and d = (c - prev) s_d
+                    if (p->st_dtype == 0) {
+                        *(float4 *)(codef + off) = cz4;
+                        if (p->st_comps == 2) *(float4 *)(codef + off + p->field) = A;
+                    } else {
+                        *(uint2 *)(codep + off) = pack_code4(cz4, p->st_dtype, sts[0]);
+                        if (p->st_comps == 2)
+                            *(uint2 *)(codep + off + p->field) =
+                                pack_code4(make_float4(dc0.x, dc0.y, dc1.x, dc1.y), p->st_dtype, sts[1]);
+                    }
+                }
+                if (MODE == kModeAdj) {
+                    // g += u^m * (L mu^{m+1});  at the source point g -= dt^2 w[m] mu^{m+1} / W
+                    const float *td = ta + 2 * TX * C::TY, *te = ta + 3 * TX * C::TY;
+                    const float4 Ua =
+                        p->aux_fmt == 0
+                            ? *(const float4 *)(td + toff)
+                            : unpack_code4(*(const uint2 *)((const unsigned short *)td + toff),
+                                           p->aux_fmt, *ainv);
+                    const float4 G = *(const float4 *)((C::GS ? gbuf : te) + toff);
+                    float2 g0 = __ffma2_rn(lo2(Ua), l0, lo2(G));
+                    float2 g1 = __ffma2_rn(hi2(Ua), l1, hi2(G));
+                    if (at_src) src_image(g0, g1, cz4, B, src_e, srcv);
+                    if (rowok[r]) *(float4 *)(gp + off) = make_float4(g0.x, g0.y, g1.x, g1.y);
                 }
             }
-            if (MODE == kModeAdj) {
-                // g += u^m * (L mu^{m+1});  at the source point g -= dt^2 w[m] mu^{m+1} / W
-                const float *td = ta + 2 * TX * C::TY, *te = ta + 3 * TX * C::TY;
-                const float4 Ua =
-                    p->aux_fmt == 0
-                        ? *(const float4 *)(td + toff)
-                        : unpack_code4(*(const uint2 *)((const unsigned short *)td + toff),
-                                       p->aux_fmt, *ainv);
-                const float4 G = *(const float4 *)((C::GS ? gbuf : te) + toff);
-                float2 g0 = __ffma2_rn(lo2(Ua), l0, lo2(G));
-                float2 g1 = __ffma2_rn(hi2(Ua), l1, hi2(G));
-                if (at_src) src_image(g0, g1, cz4, B, src_e, srcv);
-                if (rowok[r]) *(float4 *)(gp + off) = make_float4(g0.x, g0.y, g1.x, g1.y);
-            }
-        }
+        };
+        if (MODE == kModeAdj || j == src_z || (p->rec_map && j == p->rec_z))
+            rows(BoolC<true>{});
+        else
+            rows(BoolC<false>{});
         return true;
     }
 };
@@ -581,6 +598,7 @@ __device__ __forceinline__ void run_segment(Ctx<C, MODE> &c, int col, int z0, in
         c.domax = MODE != kModeAdj && p.maxbits != nullptr;
     }
     c.src_j = -1;
+    c.src_z = -1;
     c.src_r = c.src_e = 0;
     c.srcv = 0.0f;
     c.nrow = (p.n_dev ? *p.n_dev : 0) + p.n;
@@ -588,6 +606,7 @@ __device__ __forceinline__ void run_segment(Ctx<C, MODE> &c, int col, int z0, in
         const int64_t s = p.src_off[c.shot];
         const int sz = (int)(s / p.plane), rem = (int)(s - (int64_t)sz * p.plane);
         const int sy = rem / p.px, sx = rem - sy * p.px;
+        c.src_z = sz;
         if (sy >= c.y0 && sy < c.y0 + RY && sx >= c.x0 && sx < c.x0 + 4) {
             c.src_j = sz;
             c.src_r = sy - c.y0;
