@@ -1643,7 +1643,6 @@ int job_batch_entry(Job *j, Batch2dEntry *e, int zchunk)
     }
     e->p = f.p;
     e->p.zchunk = zchunk;
-    e->p.l2pf = 0;   // requests of the shared launch are small (their fields stay in L2)
     e->p.nzchunks = (m->g.nz + zchunk - 1) / zchunk;
     e->p.n_dev = nullptr;
     e->u0 = f.uc;

@@ -81,8 +81,6 @@ struct StepParams {
     float *rec_tr;
     const float *inj_q, *inj_scale;
     int inj_n;
-    int l2pf;                 // 2-D steps: rows ahead whose streamed fields are prefetched
-                              // into L2 (0: none)
 };
 
 // An off-grid source or receiver (Kaiser-windowed sinc point): taps at the computed-grid

@@ -52,7 +52,7 @@ struct RowIn {
 // (it may live in kernel parameters or in a device table).  With row_tr, the receivers
 // are the rn consecutive nodes of row rz from column rx0 on, and the epilogue writes
 // their samples u^{n+1} to row_tr[0 .. rn) (forward step only).
-template <int M, bool IMG, bool PFR, bool STORE>
+template <int M, bool IMG, bool PFR, bool STORE, int PF = 0>
 __device__ __forceinline__ void step2d_body(const StepParams &p, const float *cur_base,
                                             float *prev_base, int n, int bx, int shot, int zc,
                                             float *row_tr = nullptr, int rz = -1, int rx0 = 0,
@@ -124,9 +124,11 @@ __device__ __forceinline__ void step2d_body(const StepParams &p, const float *cu
     RowIn<M, IMG> nxt;
     if (PFR && z0 < z1) load_row(z0, nxt);
 
+    // PF > 0: the streamed rows PF iterations ahead into L2 (addresses formed from the row
+    // each time: pointers carried across iterations cost registers and occupancy)
     for (int z = z0; z < z1; ++z) {
-        if (p.l2pf > 0 && xin) {
-            const int zp = z + p.l2pf;
+        if (PF > 0 && xin) {
+            const int zp = z + PF;
             if (zp + M < nz)
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(cur + (int64_t)(zp + M) * plane + x0));
             if (zp < z1) {
@@ -225,11 +227,11 @@ __device__ __forceinline__ void step2d_body(const StepParams &p, const float *cu
     }
 }
 
-template <int M, bool IMG, bool PFR, bool STORE = false>
+template <int M, bool IMG, bool PFR, bool STORE = false, int PF = 0>
 __global__ void __launch_bounds__(kThreads2) k_step2d_reg(const StepParams p)
 {
     const int shot = blockIdx.z / p.nzchunks, zc = blockIdx.z - shot * p.nzchunks;
-    step2d_body<M, IMG, PFR, STORE>(p, p.cur, p.prev, (p.n_dev ? *p.n_dev : 0) + p.n, blockIdx.x,
+    step2d_body<M, IMG, PFR, STORE, PF>(p, p.cur, p.prev, (p.n_dev ? *p.n_dev : 0) + p.n, blockIdx.x,
                                     shot, zc);
 }
 
@@ -453,14 +455,14 @@ cudaError_t launch_tb2x(const StepParams &p0, int nshots, float *out1, float *ou
 }
 
 // Resident CTAs of one instantiation on the device (registers limit it).
-template <int M, bool IMG, bool PFR, bool STORE>
+template <int M, bool IMG, bool PFR, bool STORE, int PF>
 int resident2()
 {
     static const int resident = [] {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step2d_reg<M, IMG, PFR, STORE>,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step2d_reg<M, IMG, PFR, STORE, PF>,
                                                           kThreads2, 0) != cudaSuccess ||
             per < 1) {
             cudaGetLastError();
@@ -478,12 +480,16 @@ cudaError_t launch2(const StepParams &p0, int nshots, cudaStream_t s)
     const int bx = (p.g.nx + kTile2 - 1) / kTile2;
     const int64_t ctas = (int64_t)bx * nshots;
     bool store = false;
+    // fields larger than L2 (one field of the launch over 96 MB): the streamed rows are
+    // prefetched into L2 ahead of their loads (see below)
+    const bool big = (double)p.g.field * 4.0 * nshots > 96.0 * (1 << 20);
     int resident;
     if constexpr (IMG) {
-        resident = resident2<M, true, false, false>();
+        resident = big ? resident2<M, true, false, false, 1>() : resident2<M, true, false, false, 0>();
     } else {
         store = p.st_code != nullptr;
-        resident = store ? resident2<M, false, true, true>() : resident2<M, false, true, false>();
+        resident = store ? (big ? resident2<M, false, true, true, 2>() : resident2<M, false, true, true, 0>())
+                         : (big ? resident2<M, false, true, false, 2>() : resident2<M, false, true, false, 0>());
     }
     // z-chunks (at least 4M rows each) that best fill whole waves of resident CTAs; each
     // chunk streams 2M warm-up rows that cost about a third of an output row
@@ -505,20 +511,24 @@ cudaError_t launch2(const StepParams &p0, int nshots, cudaStream_t s)
     p.zchunk = (p.g.nz + nch - 1) / nch;
     p.nzchunks = (p.g.nz + p.zchunk - 1) / p.zchunk;
     dim3 grid(bx, 1, p.nzchunks * nshots);
-    // fields larger than L2 (one field of the launch over 96 MB): the streamed rows are
-    // prefetched into L2 ahead of their loads, 2 rows (forward modes) or 1 (reverse);
+    // prefetch into L2 for fields larger than L2: 2 rows ahead (forward modes) or 1 (reverse);
     // measured on 64 shots of 440 x 1064 (120 MB per field) against none: forward
     // 0.1017 -> 0.0985 ms, forward + store 0.1110 -> 0.108 ms, reverse 0.1582 -> 0.122 ms.
     // On grids that stay in L2 the prefetches only delay the loads (1500 steps of a
     // 128^2 to 384^2 request: 17.0 -> 21.6 ms), so they are off there.
-    const bool big = (double)p.g.field * 4.0 * nshots > 96.0 * (1 << 20);
-    p.l2pf = big ? (IMG ? 1 : 2) : 0;
     // forward: row z + 1's loads in flight during row z; reverse (imaging): all of row z's
     // loads first (its pipelined form needs too many registers; measured on 64 shots of
     // 440 x 1064: forward 0.121 -> 0.106 ms, reverse 0.190 -> 0.250 ms)
-    if constexpr (IMG) k_step2d_reg<M, true, false, false><<<grid, kThreads2, 0, s>>>(p);
-    else if (store) k_step2d_reg<M, false, true, true><<<grid, kThreads2, 0, s>>>(p);
-    else k_step2d_reg<M, false, true, false><<<grid, kThreads2, 0, s>>>(p);
+    if constexpr (IMG) {
+        if (big) k_step2d_reg<M, true, false, false, 1><<<grid, kThreads2, 0, s>>>(p);
+        else k_step2d_reg<M, true, false, false><<<grid, kThreads2, 0, s>>>(p);
+    } else if (store) {
+        if (big) k_step2d_reg<M, false, true, true, 2><<<grid, kThreads2, 0, s>>>(p);
+        else k_step2d_reg<M, false, true, true><<<grid, kThreads2, 0, s>>>(p);
+    } else {
+        if (big) k_step2d_reg<M, false, true, false, 2><<<grid, kThreads2, 0, s>>>(p);
+        else k_step2d_reg<M, false, true, false><<<grid, kThreads2, 0, s>>>(p);
+    }
     return cudaGetLastError();
 }
 
