@@ -476,7 +476,7 @@ struct Ctx {
         // 0.715 -> 0.731 ms)
         auto rows = [&](auto spec_c) {
             constexpr bool SPEC = decltype(spec_c)::value;
-    #pragma unroll
+#pragma unroll
             for (int r = 0; r < RY; ++r) {
                 const float4 cz4 = r == 0 ? uj.a : uj.b;
                 float2 l0 = lacc[r][0], l1 = lacc[r][1];
