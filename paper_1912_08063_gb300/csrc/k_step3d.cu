@@ -38,7 +38,17 @@ Step3dVariant step3d_variant(int M, int mode)
             if (ok) v = w;
         }
     }
-    if (v.tm) v.ty = 32;
+    if (v.tm) {
+        // radius-8 forward modes on 64 x 16 tiles, four CTAs of 4 warps per SM (measured
+        // at 552^3 against two CTAs of 8 warps: forward 0.522 -> 0.500 ms, forward + store
+        // 0.577 -> 0.545 ms; at 424^3 0.282 -> 0.245 and 0.306 -> 0.266 ms); not the
+        // reverse step, which fits only one halo and one pointwise stage then (552^3:
+        // 0.724 -> 0.851 ms), nor radius 4 (296^3 forward + store 0.084 -> 0.091 ms);
+        // FWI_STEP3D_HALF=0/1 overrides for the forward modes
+        v.half = M == 8 && mode != kModeAdj;
+        if (const char *e = std::getenv("FWI_STEP3D_HALF")) v.half = mode != kModeAdj && std::atoi(e) != 0;
+        v.ty = v.half ? 16 : 32;
+    }
     return v;
 }
 
@@ -119,7 +129,8 @@ cudaError_t launch_step3d_tma(const Step3dParams &p, int mode, int ctas,
                               const CUtensorMap &mb, const CUtensorMap &md,
                               const CUtensorMap &me, cudaStream_t s)
 {
-    const int64_t columns = (int64_t)((p.nx + 63) / 64) * ((p.ny + 31) / 32) * p.nshots;
+    const int ty = step3d_variant(p.M, mode).ty;
+    const int64_t columns = (int64_t)((p.nx + 63) / 64) * ((p.ny + ty - 1) / ty) * p.nshots;
     bool tile_g = (int64_t)ctas > (int64_t)(kTileGParts - 1) * columns;   // ctas/columns >= 5
     if (const char *e = std::getenv("FWI_STEP3D_TILE_G")) tile_g = std::atoi(e) != 0;
     const Step3dKernelInfo k = kernel_info(p.M, mode, p.iso != 0, mode == kModeAdj && tile_g);

@@ -58,13 +58,12 @@ constexpr int kPackX = s3d::kPackX, kIso = s3d::kIso;
 // with cp.async at the top of the plane (the tile itself brought into L2 one plane
 // earlier), instead of g as a fourth TMA pointwise tile
 constexpr int kGAsync = 32;
+// Forward modes: 64 x 16 tiles of 4 warps, four CTAs per SM (the same 16 warps and the
+// same 512 TMEM columns as two CTAs of 8 warps, with a barrier per 4 warps per plane)
+constexpr int kHalf = 64;
 template <bool B> struct BoolC { static constexpr bool value = B; };
 
 // ---- tensor memory (tcgen05) ----
-// Columns per CTA at radius M: two rings of M slots of 8 columns for each of the two warps
-// that share a lane quarter.
-template <int M>
-__host__ __device__ constexpr uint32_t tmem_cols() { return 32u * M; }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t cols)
 {
@@ -168,13 +167,15 @@ template <int M_, int P_, int PP_, int F_, int NPW_>
 struct Cfg {
     static constexpr int M = M_, P = P_, PP = PP_, F = F_, NPW = NPW_;
     static constexpr bool ISO = (F & kIso) != 0;
-    static constexpr int TX = 64, TY = 32, RX = 4, RY = 2;
+    static constexpr int TX = 64, TY = (F & kHalf) ? 16 : 32, RX = 4, RY = 2;
     static constexpr int NTX = TX / RX, NTY = TY / RY, NT = NTX * NTY;
     static constexpr int SX = TX + 2 * M, SY = TY + 2 * M;
     static constexpr int SH = P + 1, SP = PP + 1;
     static_assert(M == 8 || M == 4, "the TMEM rings hold M slots (plane mod M)");
     static constexpr uint32_t RING = 8u * M;   // columns of one ring
-    static_assert(NT == 256 && RX * RY == 8, "8 values per TMEM slot, 8 warps");
+    static_assert((NT == 256 || NT == 128) && RX * RY == 8, "8 values per TMEM slot, 4 or 8 warps");
+    // TMEM columns per CTA: the raw and partial rings of each warp that shares a lane quarter
+    static constexpr uint32_t TCOLS = 2u * RING * (uint32_t)(NT / 128);
     static constexpr int HALO_BYTES = SX * SY * 4;
     static constexpr int TILE_BYTES = TX * TY * 4;
     static constexpr int HALO_STRIDE = (HALO_BYTES + 127) / 128 * 128;
@@ -184,7 +185,7 @@ struct Cfg {
     static constexpr int SMEM = SH * HALO_STRIDE + SP * PW_STRIDE + GS * TILE_BYTES + MISC + 1024;
     // the CTAs that shared memory admits per SM never need more TMEM than the SM's 512
     // columns, so an allocation never waits
-    static_assert((233472 / (SMEM + 1024)) * tmem_cols<M>() <= 512, "a CTA would wait for TMEM");
+    static_assert((233472 / (SMEM + 1024)) * TCOLS <= 512, "a CTA would wait for TMEM");
     static_assert(2 * (SMEM + 1024) <= 233472, "two CTAs per SM");
 };
 
@@ -655,7 +656,7 @@ __device__ __forceinline__ void run_segment(Ctx<C, MODE> &c, int col, int z0, in
 // Persistent launch with the schedule of k_step3d.cuh (whole-column rounds, then the
 // leftover columns cut along z), two CTAs per SM.
 template <int M, int P, int PP, int F, int MODE>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__((F & kHalf) ? 128 : 256, (F & kHalf) ? 4 : 2)
 k_step3d_tm(const __grid_constant__ Step3dParams p, const __grid_constant__ CUtensorMap map_c,
             const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
             const __grid_constant__ CUtensorMap map_d, const __grid_constant__ CUtensorMap map_e)
@@ -693,7 +694,7 @@ k_step3d_tm(const __grid_constant__ Step3dParams p, const __grid_constant__ CUte
     c.mxa = c.mxd = 0.0f;
 
     const int warp = c.tid >> 5;
-    if (warp == 0) tmem_alloc(tbase, tmem_cols<M>());
+    if (warp == 0) tmem_alloc(tbase, C::TCOLS);
     if (c.tid == 0) {
         for (int i = 0; i < C::SH; ++i) mbar_init(c.bar_h + i, 1);
         for (int i = 0; i < C::SP; ++i) mbar_init(c.bar_p + i, 1);
@@ -720,7 +721,7 @@ k_step3d_tm(const __grid_constant__ Step3dParams p, const __grid_constant__ CUte
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
-    if (warp == 0) tmem_dealloc(*(volatile uint32_t *)tbase, tmem_cols<M>());
+    if (warp == 0) tmem_dealloc(*(volatile uint32_t *)tbase, C::TCOLS);
     if (*(volatile int *)c.abort_flag && c.tid == 0) {
         atomicOr(p.err, 2u);
         for (int q = c.h_issued - C::SH > 0 ? c.h_issued - C::SH : 0; q < c.h_issued; ++q)
@@ -731,29 +732,39 @@ k_step3d_tm(const __grid_constant__ Step3dParams p, const __grid_constant__ CUte
 }
 
 template <int M, int F>
-Step3dKernelInfo kernel_info(int mode, bool tile_g)
+Step3dKernelInfo kernel_info(int mode, bool tile_g, bool half)
 {
     Step3dKernelInfo k;
-    if (mode == kModeStep || mode == kModeStepStore) {
+    if ((mode == kModeStep || mode == kModeStepStore) && half) {
+        // 64 x 16 tiles, four CTAs of 4 warps per SM (the radius-8 forward modes)
+        using C = Cfg<M, 2, 2, F | kHalf, 2>;
+        k.fn = mode == kModeStep ? (Step3dKernel)k_step3d_tm<M, 2, 2, F | kHalf, kModeStep>
+                                 : (Step3dKernel)k_step3d_tm<M, 2, 2, F | kHalf, kModeStepStore>;
+        k.threads = C::NT;
+        k.smem = C::SMEM;
+        k.tmem_cols = (int)C::TCOLS;
+    } else if (mode == kModeStep || mode == kModeStepStore) {
         using C = Cfg<M, 2, 2, F, 2>;
         k.fn = mode == kModeStep ? (Step3dKernel)k_step3d_tm<M, 2, 2, F, kModeStep>
                                  : (Step3dKernel)k_step3d_tm<M, 2, 2, F, kModeStepStore>;
         k.threads = C::NT;
         k.smem = C::SMEM;
+        k.tmem_cols = (int)C::TCOLS;
     } else if (tile_g) {
         // g as a fourth TMA pointwise tile: rings of three halo and two pointwise stages
         using C = Cfg<M, 2, 1, F, 4>;
         k.fn = (Step3dKernel)k_step3d_tm<M, 2, 1, F, kModeAdj>;
         k.threads = C::NT;
         k.smem = C::SMEM;
+        k.tmem_cols = (int)C::TCOLS;
     } else {
         // g staged by cp.async: rings of two halo and three pointwise stages
         using C = Cfg<M, 1, 2, F | kGAsync, 3>;
         k.fn = (Step3dKernel)k_step3d_tm<M, 1, 2, F | kGAsync, kModeAdj>;
         k.threads = C::NT;
         k.smem = C::SMEM;
+        k.tmem_cols = (int)C::TCOLS;
     }
-    k.tmem_cols = (int)tmem_cols<M>();
     return k;
 }
 

@@ -3,10 +3,10 @@
 
 namespace fwi {
 
-Step3dKernelInfo step3d_kernel_tm4(int mode, bool iso, bool tile_g)
+Step3dKernelInfo step3d_kernel_tm4(int mode, bool iso, bool tile_g, bool half)
 {
-    if (iso) return s3tm::kernel_info<4, s3tm::kPackX | s3tm::kIso>(mode, tile_g);
-    return s3tm::kernel_info<4, s3tm::kPackX>(mode, tile_g);
+    if (iso) return s3tm::kernel_info<4, s3tm::kPackX | s3tm::kIso>(mode, tile_g, half);
+    return s3tm::kernel_info<4, s3tm::kPackX>(mode, tile_g, half);
 }
 
 }  // namespace fwi

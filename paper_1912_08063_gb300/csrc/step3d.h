@@ -80,6 +80,7 @@ struct Step3dVariant {
     int ty, ry, pf, u, opt, opt_rev;
     int tm;
     int tile_g = 0;
+    int half = 0;   // tensor-memory forward modes: 64 x 16 tiles, 4 warps, four CTAs per SM
 };
 // The tensor-memory reverse step takes g as a TMA tile when a launch has at least this
 // many CTAs per 64 x 32 tile column, so that its columns are cut along z into as many
@@ -116,8 +117,8 @@ struct Step3dKernelInfo {
 Step3dKernelInfo step3d_kernel_m4(const Step3dVariant &v, int mode, bool iso = false);
 Step3dKernelInfo step3d_kernel_m8(const Step3dVariant &v, int mode, bool iso = false);
 // The tensor-memory kernels (k_step3d_tm8.cu, k_step3d_tm4.cu).
-Step3dKernelInfo step3d_kernel_tm8(int mode, bool iso, bool tile_g);
-Step3dKernelInfo step3d_kernel_tm4(int mode, bool iso, bool tile_g);
+Step3dKernelInfo step3d_kernel_tm8(int mode, bool iso, bool tile_g, bool half);
+Step3dKernelInfo step3d_kernel_tm4(int mode, bool iso, bool tile_g, bool half);
 
 // Encodes a 4-D tensor map over shots of a field laid out as in Geom (elements of
 // `elem_bytes` = 4 or 2, shots `shot_stride` elements apart), with box (bx, by, 1, 1) and

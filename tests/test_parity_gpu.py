@@ -416,16 +416,19 @@ def test_model_reuse_across_checkpoint_layouts():
 
 
 @pytest.mark.parametrize("order", [16, 8])
-@pytest.mark.parametrize("tmem,tile_g", [("1", "0"), ("1", "1"), ("0", "0")])
-def test_step_kernels_both_variants(tmem, tile_g, order, monkeypatch):
-    """The 3-D steps run either the tensor-memory kernel (z-stream in TMEM, two CTAs per
-    SM; FWI_STEP3D_TMEM=1), with its reverse step staging g per thread or reading it as a
-    TMA tile (FWI_STEP3D_TILE_G=0/1), or the register-queue kernel (FWI_STEP3D_TMEM=0), at
+@pytest.mark.parametrize("tmem,tile_g,half",
+                         [("1", "0", "1"), ("1", "1", "0"), ("1", "0", "0"), ("0", "0", "0")])
+def test_step_kernels_both_variants(tmem, tile_g, half, order, monkeypatch):
+    """The 3-D steps run either the tensor-memory kernel (z-stream in TMEM; FWI_STEP3D_TMEM=1),
+    with its forward modes on 64 x 16 tiles of 4 warps or 64 x 32 tiles of 8 warps
+    (FWI_STEP3D_HALF=1/0) and its reverse step staging g per thread or reading it as a TMA
+    tile (FWI_STEP3D_TILE_G=0/1), or the register-queue kernel (FWI_STEP3D_TMEM=0), at
     radius 8 and radius 4; every combination matches the oracle in every mode: forward,
     forward with checkpoint stores, reverse step with imaging (FP16 checkpoints,
     recomputation)."""
     monkeypatch.setenv("FWI_STEP3D_TMEM", tmem)
     monkeypatch.setenv("FWI_STEP3D_TILE_G", tile_g)
+    monkeypatch.setenv("FWI_STEP3D_HALF", half)
     rng = np.random.default_rng(31)
     w = synth.random_small(rng, 3, (22, 37, 70), nt=70, order=order, nb=4, nrec=9)
     m, p, acq = make_pair(w, snap="fp16", budget=1)
@@ -442,7 +445,7 @@ def test_step_kernels_both_variants(tmem, tile_g, order, monkeypatch):
     info = m.info()
     rphi, rg = p.gradient(dobs.astype(np.float64))
     eg = rel(g.cpu().numpy(), rg)
-    print(f"order {order}, TMEM {tmem}, tile g {tile_g}: traces {et:.2e}, gradient {eg:.2e}, "
+    print(f"order {order}, TMEM {tmem}, tile g {tile_g}, half {half}: traces {et:.2e}, gradient {eg:.2e}, "
           f"slots {info['snap_slots']}, forward steps {info['last_forward_steps']}")
     assert 0 < info["snap_slots"] < w.nt
     assert et <= TOL_FWD and eg <= TOL_GRAD16
