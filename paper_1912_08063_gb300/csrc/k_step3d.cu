@@ -43,7 +43,8 @@ Step3dVariant step3d_variant(int M, int mode)
         // at 552^3 against two CTAs of 8 warps: forward 0.522 -> 0.500 ms, forward + store
         // 0.577 -> 0.545 ms; at 424^3 0.282 -> 0.245 and 0.306 -> 0.266 ms); not the
         // reverse step, which fits only one halo and one pointwise stage then (552^3:
-        // 0.724 -> 0.851 ms), nor radius 4 (296^3 forward + store 0.084 -> 0.091 ms);
+        // 0.724 -> 0.851 ms), nor radius 4 (552^3 forward 0.481 -> 0.515 ms, forward +
+        // store 0.579 -> 0.617 ms);
         // FWI_STEP3D_HALF=0/1 overrides for the forward modes
         v.half = M == 8 && mode != kModeAdj;
         if (const char *e = std::getenv("FWI_STEP3D_HALF")) v.half = mode != kModeAdj && std::atoi(e) != 0;
