@@ -58,7 +58,7 @@ typedef struct {
                                    a negative value means no sponge (closed box)        */
     int32_t snap_dtype;         /* FWI_SNAP_*: checkpoint storage type (default FP32)   */
     int32_t fold_every;         /* adjoint steps between FP32 -> FP64 gradient folds
-                                   (default 64)                                         */
+                                   (default 256)                                        */
     int64_t snap_budget_bytes;  /* device bytes for checkpoints over all shots; 0 = a
                                    quarter of the free memory at the first gradient call;
                                    sliced as fwi_checkpoint_plan describes              */

