@@ -514,8 +514,7 @@ cudaError_t launch2(const StepParams &p0, int nshots, cudaStream_t s)
     // prefetch into L2 for fields larger than L2: 2 rows ahead (forward modes) or 1 (reverse);
     // measured on 64 shots of 440 x 1064 (120 MB per field) against none: forward
     // 0.1017 -> 0.0985 ms, forward + store 0.1110 -> 0.108 ms, reverse 0.1582 -> 0.122 ms.
-    // On grids that stay in L2 the prefetches only delay the loads (1500 steps of a
-    // 128^2 to 384^2 request: 17.0 -> 21.6 ms), so they are off there.
+    // Grids that stay in L2 have no DRAM latency for them to hide, so they are off there.
     // forward: row z + 1's loads in flight during row z; reverse (imaging): all of row z's
     // loads first (its pipelined form needs too many registers; measured on 64 shots of
     // 440 x 1064: forward 0.121 -> 0.106 ms, reverse 0.190 -> 0.250 ms)
