@@ -85,8 +85,8 @@ int host_coeffs(int M, double *c)
 // largest magnitude of the 1-D stencil's symbol (at the Nyquist wavenumber)
 double host_symbol_max(int M)
 {
-    double c[kMaxM + 1];
-    host_coeffs(M, c);
+    double c[kMaxM + 1] = {};
+    if (host_coeffs(M, c) != FWI_OK) return 0.0;   // callers validate M first
     double s = c[0];
     for (int k = 1; k <= M; ++k) s += 2.0 * c[k] * ((k & 1) ? -1.0 : 1.0);
     return std::fabs(s);
